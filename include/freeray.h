@@ -1,0 +1,228 @@
+/*
+ * freeray — C ABI of the GB300 (sm_103a) differentiable freeform-lens tracer.
+ *
+ * Implements the hot path of de Koning, Heemels, Adam and Moeller, "Gradient
+ * descent-based freeform optics design using algorithmic differentiable
+ * non-sequential ray tracing" (2023): rays from a collimated beam, a point
+ * source or a grid of point sources are traced through a lens made of a flat
+ * entry face and a bicubic B-spline freeform exit face (Sec. 2.1) onto a screen,
+ * deposited with the smooth Gaussian reconstruction filter (Sec. 2.3), and the
+ * gradient of an irradiance loss is carried back to the control heights P^z
+ * (Sec. 2.5).
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented as "device" are CUDA device (or managed) memory owned
+ *    by the caller; the library never frees them. Pointers documented as
+ *    "host" are read during the call only.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *    enqueued on it asynchronously; nothing in this library synchronises the
+ *    host with the device, except fr_stream_wait (explicitly).
+ *  - Every call returns an fr_status. On failure nothing has been enqueued
+ *    (argument errors) or the CUDA error is reported (launch errors); a message
+ *    is kept in the handle (fr_last_error). No exception crosses the ABI and no
+ *    kernel traps: per-ray anomalies are counted in fr_stats.
+ *  - Calls taking an fr_handle allocate device scratch memory in the handle the
+ *    first time a larger problem is seen. That allocation is refused with
+ *    FR_ERR_WORKSPACE while `stream` is being captured into a CUDA graph, so a
+ *    call of the same size must run once before capture.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported;
+ *    control nets from 4x4 to 32x32; filter sizes nu_x = nu_y in {1, 3, 5}.
+ *
+ * Layouts:
+ *  - Control heights: float32, (n1+1) x (n2+1), row-major with the u index i
+ *    slow: ctrl_z[i*(n2+1) + j] = P^z_{i,j}; u runs along x, v along y.
+ *  - Irradiance and dL/dE: float32 on the extended grid with ghost pixels
+ *    (Sec. 2.3), (ny+nu_y-1) rows x (nx+nu_x-1) columns, row-major, row = y:
+ *    E[r*(nx+nu_x-1) + c]. Interior pixel (i, j) is column i+(nu_x-1)/2,
+ *    row j+(nu_y-1)/2. Units: flux per area, E = sum_k w_k F(x_k) / (w_x w_y).
+ *  - Target images for the loss: float32 on the interior ny x nx grid.
+ */
+#ifndef FREERAY_H
+#define FREERAY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_ABI_VERSION 1
+
+typedef enum fr_status {
+  FR_OK = 0,
+  FR_ERR_INVALID_ARG = 1,  /* a descriptor or size is out of range */
+  FR_ERR_UNSUPPORTED = 2,  /* valid, but outside what this build implements */
+  FR_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+  FR_ERR_WORKSPACE = 4,    /* scratch memory needed while a stream is capturing */
+  FR_ERR_TIMEOUT = 5       /* fr_stream_wait ran out of time */
+} fr_status;
+
+/* Source kinds (Sec. 2.2.1). */
+enum { FR_SOURCE_COLLIMATED = 0, FR_SOURCE_POINT = 1 };
+
+/* What happened to a ray; index into fr_stats.rays and fr_ray_record.status. */
+enum {
+  FR_RAY_ON_SCREEN = 0,     /* deposited */
+  FR_RAY_APERTURE_MISS = 1, /* point source: missed the entry face */
+  FR_RAY_OUT_OF_DOMAIN = 2, /* point source: left the side of the lens before the freeform */
+  FR_RAY_TIR = 3,           /* total internal reflection at the freeform (culled, Sec. 2.2) */
+  FR_RAY_OFF_SCREEN = 4,    /* missed the open interior screen |X|<R_x, |Y|<R_y */
+  FR_RAY_INVALID = 5,       /* freeform below the entry face where the ray enters */
+  FR_RAY_NEWTON_FAIL = 6,   /* point source: Newton did not meet the tolerance */
+  FR_RAY_NCAUSES = 8
+};
+
+/* Lens (Sec. 2.1): flat entry face z = z_in on [-rx,rx]x[-ry,ry] and the
+ * freeform z = Z(X^-1(x), Y^-1(y)), a B-spline of degrees (p, q) over clamped
+ * uniform knots whose X and Y are linear through the Greville construction. */
+typedef struct fr_lens_desc {
+  int32_t n1, n2;        /* control net (n1+1) x (n2+1); 3 <= n1, n2 <= 31 */
+  int32_t p, q;          /* degrees; must be 3 */
+  const float* ctrl_z;   /* device, (n1+1)*(n2+1) control heights P^z */
+  float rx, ry;          /* half-widths of the lens */
+  float z_in;            /* entry face; P^z > z_in keeps the lens valid (Sec. 2.1.2) */
+  float n_glass;         /* refractive index of the lens; air outside */
+} fr_lens_desc;
+
+/* Source (Sec. 2.2.1). Rays are numbered 0..n_rays-1; the initial weight of
+ * every ray is flux / n_rays. */
+typedef struct fr_source_desc {
+  int32_t kind;          /* FR_SOURCE_COLLIMATED or FR_SOURCE_POINT */
+  int32_t jitter;        /* collimated: 0 = cell centres, 1 = Philox jitter in each cell */
+  int32_t cols, rows;    /* collimated: square grid over (u,v) in [0,1]^2, n_rays = cols*rows,
+                            ray id = row*cols + col */
+  float pos[3];          /* point: source position (centre of the grid of sources) */
+  float half_angle;      /* point: cone half-angle phi_max in radians, (0, pi/2) */
+  int32_t grid_nx, grid_ny; /* point: grid of point sources (1,1 for one source);
+                               n_rays must be a multiple of grid_nx*grid_ny */
+  float grid_w, grid_h;  /* point: extent of the grid; centres equispaced including the ends */
+  float flux;            /* total flux of the source */
+} fr_source_desc;
+
+/* Screen and reconstruction filter (Sec. 2.3). */
+typedef struct fr_target_desc {
+  float z_screen;        /* screen plane, above the lens */
+  float Rx, Ry;          /* screen half-widths; pixel size w = 2R/n */
+  int32_t nx, ny;        /* interior pixels, 1..4096 */
+  int32_t nu_x, nu_y;    /* filter sizes (odd, equal, in {1,3,5}) */
+  float alpha;           /* Gaussian coefficient in pixel units: exp(-alpha ((x-c)/w)^2) */
+} fr_target_desc;
+
+/* Options. Zero-initialised options mean the defaults. */
+typedef struct fr_options {
+  int32_t deterministic;    /* 1: accumulate in int64 fixed point; results are bit-identical
+                               from run to run and independent of the launch schedule */
+  int32_t accumulate;       /* 1: add into E_out / dLdP_out instead of overwriting them */
+  int32_t newton_max_iter;  /* 0 -> 8 */
+  float newton_tol;         /* 0 -> 1e-6, absolute, on the ray parameter */
+  int32_t warps_per_cta;    /* 0 -> tuned; 1..32 */
+  int32_t rays_per_lane;    /* 0 -> tuned; 1..64 */
+  int32_t ctas_per_sm;      /* 0 -> tuned; 1..8 */
+  int32_t hist_mode;        /* 0 auto, 1 global atomics, 2 shared-memory privatised */
+  int32_t reserved[8];
+} fr_options;
+
+/* Per-cause ray counts (device, uint64). Kernels add to it; zero it first. */
+typedef struct fr_stats {
+  uint64_t rays[FR_RAY_NCAUSES];
+} fr_stats;
+
+/* One traced ray, for debugging and parity checks (fr_trace_debug). */
+typedef struct fr_ray_record {
+  int32_t status;        /* FR_RAY_* */
+  int32_t span_i, span_j;/* knot span index of the freeform hit (u_i0 <= u < u_i0+1) */
+  int32_t newton_iters;  /* point source: Newton iterations used */
+  float u, v;            /* freeform hit, parameter space */
+  float x, y, z;         /* freeform hit */
+  float dx, dy, dz;      /* direction inside the glass */
+  float tx, ty, tz;      /* direction after the freeform */
+  float X, Y;            /* screen hit */
+  float w;               /* final weight */
+  float t;               /* point source: ray parameter of the hit inside the glass */
+} fr_ray_record;
+
+/* One lens of a batched call: its own descriptors, rays and buffers. */
+typedef struct fr_batch_item {
+  fr_lens_desc lens;
+  fr_source_desc source;
+  fr_target_desc target;
+  uint64_t n_rays;
+  uint64_t seed;
+  float* E;              /* device: forward output, extended grid */
+  const float* dLdE;     /* device: adjoint input, extended grid */
+  float* dLdP;           /* device: adjoint output, (n1+1)*(n2+1) */
+  fr_stats* stats;       /* device or NULL */
+} fr_batch_item;
+
+typedef struct fr_handle fr_handle;
+
+/* Create / destroy a handle bound to the current CUDA device. */
+fr_status fr_create(fr_handle** out);
+fr_status fr_destroy(fr_handle* h);
+
+/* Message of the last failure on this handle ("" if none). Valid until the next call. */
+const char* fr_last_error(const fr_handle* h);
+
+/* ABI version (FR_ABI_VERSION) of the loaded library. */
+int32_t fr_abi_version(void);
+
+/* Forward trace (Secs. 2.2-2.3): rays [ray_begin, ray_begin+ray_count) of a
+ * source of n_rays rays through the lens onto the screen. Writes (or adds, with
+ * options->accumulate) the irradiance on the extended grid to E_out (device),
+ * and adds per-cause ray counts to stats_out (device, may be NULL).
+ * ray_count = UINT64_MAX means "to the end". `seed` keys the Philox stream of
+ * the point source and of collimated jitter. options may be NULL. */
+fr_status fr_trace_forward(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                           const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
+                           uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
+                           float* E_out, fr_stats* stats_out, void* stream);
+
+/* Adjoint (reverse mode of the forward trace, Sec. 2.5): given dL/dE on the
+ * extended grid (device), writes (or adds) dL/dP^z to dLdP_out (device,
+ * (n1+1)*(n2+1)). Each ray's path is recomputed from its id and seed, not read
+ * back; the arguments must equal those of the forward call. */
+fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                           const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
+                           uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
+                           const float* dLdE, float* dLdP_out, fr_stats* stats_out, void* stream);
+
+/* Per-ray records of rays [ray_begin, ray_begin+ray_count) (device array of
+ * ray_count records). Same path as fr_trace_forward. */
+fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                         const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
+                         uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
+                         fr_ray_record* out, void* stream);
+
+/* Squared L2 loss over the interior pixels, L = sum (E - E_ref)^2, into
+ * *loss_out (device double), and dL/dE = 2 (E - E_ref) on the interior and 0 on
+ * ghost pixels into dLdE_out (device, extended grid). E is on the extended
+ * grid, E_ref on the interior ny x nx grid. The sum is reduced in a fixed order
+ * (bit-identical run to run). */
+fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny,
+                     int32_t nu_x, int32_t nu_y, double* loss_out, float* dLdE_out, void* stream);
+
+/* Adam (Kingma & Ba, Algorithm 1) on n parameters in place (device P, m, v;
+ * gradient g). *step (device int32) is the number of steps taken so far: the
+ * update uses step+1 for the bias corrections and stores step+1, so a captured
+ * graph can be replayed. */
+fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* g, int64_t n,
+                       float lr, float beta1, float beta2, float eps, int32_t* step, void* stream);
+
+/* Batched forward / adjoint: every item (its own lens, source, screen, rays and
+ * buffers) in one launch of the trace kernel. Same semantics per item as
+ * fr_trace_forward / fr_trace_adjoint over all rays of the item. n_items <= 64. */
+fr_status fr_trace_batch_forward(fr_handle* h, const fr_batch_item* items, int32_t n_items,
+                                 const fr_options* options, void* stream);
+fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32_t n_items,
+                                 const fr_options* options, void* stream);
+
+/* Wait for `stream` on the host by polling, at most timeout_ms milliseconds.
+ * Returns FR_ERR_TIMEOUT if the work has not finished by then. */
+fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FREERAY_H */

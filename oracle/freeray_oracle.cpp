@@ -132,9 +132,9 @@ void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-// A 32-bit word to a uniform number in the open interval (0,1): the top 24
-// bits plus one half, times 2^-24.
-double word_to_unit(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }
+// A 32-bit word to a uniform number in the open interval (0,1): the top 23
+// bits plus one half, times 2^-23 (a value FP32 also holds exactly).
+double word_to_unit(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 // The two uniforms of ray `id`: counter (id_lo, id_hi, 0, 0), key = seed.
 void ray_uniforms(uint64_t seed, uint64_t id, double* xi1, double* xi2) {

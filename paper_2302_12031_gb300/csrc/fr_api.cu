@@ -1,0 +1,551 @@
+// The C ABI of include/freeray.h: argument checks, the device view of each
+// problem (fr::Item), the handle's scratch memory, the schedule, and the launch
+// sequence of every entry point. All arithmetic of the path runs in the kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fr_internal.h"
+
+namespace fr {
+cudaError_t configure_forward();
+cudaError_t configure_adjoint();
+cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);
+}  // namespace fr
+
+struct fr_handle {
+  int device = 0;
+  int sm_count = 0;
+  unsigned char* ws = nullptr;   // scratch memory owned by the handle
+  size_t ws_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+using fr::Item;
+
+constexpr size_t kAlign = 256;
+constexpr size_t kHeaderBytes = 2048;   // loss partials and counter at the start of the workspace
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+fr_status set_error(fr_handle* h, fr_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return s;
+}
+
+fr_status cuda_error(fr_handle* h, cudaError_t e, const char* what) {
+  return set_error(h, FR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FR_CUDA(h, call, what)                         \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_error(h, e_, what); \
+  } while (0)
+
+bool finite(float x) { return std::isfinite(x); }
+
+fr_options defaults(const fr_options* o) {
+  fr_options d;
+  std::memset(&d, 0, sizeof d);
+  if (o) d = *o;
+  if (d.newton_max_iter <= 0) d.newton_max_iter = 8;
+  if (!(d.newton_tol > 0.0f)) d.newton_tol = 1e-6f;
+  return d;
+}
+
+// Per-item offsets into the workspace.
+struct ItemWs {
+  size_t patch, basis_u, basis_v, zb, efix, pfix, gmax, end;
+};
+
+ItemWs plan(const Item& it, size_t at, bool det_fwd, bool det_adj) {
+  ItemWs w;
+  w.patch = at;
+  at = align_up(at + (size_t)it.nsu * it.nsv * 4 * sizeof(float4));
+  w.basis_u = at;
+  at = align_up(at + (size_t)it.nsu * 4 * sizeof(float4));
+  w.basis_v = at;
+  at = align_up(at + (size_t)it.nsv * 4 * sizeof(float4));
+  w.zb = at;
+  at = align_up(at + 2 * sizeof(float));
+  w.efix = at;
+  if (det_fwd) at = align_up(at + (size_t)it.ncol * it.nrow * sizeof(unsigned long long));
+  w.pfix = at;
+  if (det_adj) at = align_up(at + (size_t)it.ncu * it.ncv * sizeof(unsigned long long));
+  w.gmax = at;
+  at = align_up(at + sizeof(float));
+  w.end = at;
+  return w;
+}
+
+fr_status ensure_workspace(fr_handle* h, size_t bytes, cudaStream_t st) {
+  if (bytes <= h->ws_bytes) return FR_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FR_CUDA(h, cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_error(h, FR_ERR_WORKSPACE,
+                     "scratch memory must grow to %zu bytes while the stream is capturing; run the same call "
+                     "once before capture", bytes);
+  if (h->ws) {
+    FR_CUDA(h, cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    FR_CUDA(h, cudaFree(h->ws), "cudaFree");
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t want = std::max<size_t>(bytes, 1 << 20);
+  FR_CUDA(h, cudaMalloc(&h->ws, want), "cudaMalloc(workspace)");
+  h->ws_bytes = want;
+  FR_CUDA(h, cudaMemset(h->ws, 0, kHeaderBytes), "cudaMemset(workspace header)");
+  return FR_OK;
+}
+
+// Checks the public descriptors and fills the device view.
+fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S, const fr_target_desc* T,
+                    uint64_t n_rays, uint64_t seed, uint64_t begin, uint64_t count, const fr_options& o,
+                    Item* it) {
+  if (!L || !S || !T) return set_error(h, FR_ERR_INVALID_ARG, "null descriptor");
+  std::memset(it, 0, sizeof *it);
+  if (!L->ctrl_z) return set_error(h, FR_ERR_INVALID_ARG, "lens.ctrl_z is null");
+  if (L->p != 3 || L->q != 3) return set_error(h, FR_ERR_UNSUPPORTED, "only degrees p = q = 3 are implemented");
+  if (L->n1 < 3 || L->n2 < 3 || L->n1 + 1 > fr::kMaxCtrl || L->n2 + 1 > fr::kMaxCtrl)
+    return set_error(h, FR_ERR_UNSUPPORTED, "control net must be between 4x4 and %dx%d", fr::kMaxCtrl,
+                     fr::kMaxCtrl);
+  if (!(L->rx > 0.0f) || !(L->ry > 0.0f) || !finite(L->rx) || !finite(L->ry) || !finite(L->z_in) ||
+      !(L->n_glass > 0.0f) || !finite(L->n_glass))
+    return set_error(h, FR_ERR_INVALID_ARG, "lens geometry must be finite with rx, ry, n_glass > 0");
+  if (n_rays == 0) return set_error(h, FR_ERR_INVALID_ARG, "n_rays must be positive");
+  if (begin > n_rays) return set_error(h, FR_ERR_INVALID_ARG, "ray_begin beyond n_rays");
+  if (count == UINT64_MAX) count = n_rays - begin;
+  if (count > n_rays - begin) return set_error(h, FR_ERR_INVALID_ARG, "ray range beyond n_rays");
+  if (!(T->Rx > 0.0f) || !(T->Ry > 0.0f) || !finite(T->Rx) || !finite(T->Ry) || !finite(T->z_screen))
+    return set_error(h, FR_ERR_INVALID_ARG, "screen half-widths must be positive and finite");
+  if (T->nx < 1 || T->ny < 1 || T->nx > 4096 || T->ny > 4096)
+    return set_error(h, FR_ERR_INVALID_ARG, "screen pixels must be 1..4096 per axis");
+  if (T->nu_x != T->nu_y || (T->nu_x != 1 && T->nu_x != 3 && T->nu_x != 5))
+    return set_error(h, FR_ERR_UNSUPPORTED, "filter sizes must be equal and one of 1, 3, 5");
+  if (!(T->alpha > 0.0f) || !finite(T->alpha)) return set_error(h, FR_ERR_INVALID_ARG, "alpha must be positive");
+  if (!finite(S->flux)) return set_error(h, FR_ERR_INVALID_ARG, "flux must be finite");
+  // Lens.
+  it->ctrl = L->ctrl_z;
+  it->ncu = L->n1 + 1;
+  it->ncv = L->n2 + 1;
+  it->nsu = it->ncu - 3;
+  it->nsv = it->ncv - 3;
+  it->rx = L->rx;
+  it->ry = L->ry;
+  it->z_in = L->z_in;
+  it->n_glass = L->n_glass;
+  it->ku = (float)it->nsu / (2.0f * L->rx);
+  it->kv = (float)it->nsv / (2.0f * L->ry);
+  const double nr = (L->n_glass - 1.0) / (L->n_glass + 1.0);
+  it->R0 = (float)(nr * nr);
+  // Source.
+  it->kind = S->kind;
+  it->seed = seed;
+  it->n_rays = n_rays;
+  it->ray_begin = begin;
+  it->ray_end = begin + count;
+  it->omega0 = (float)((double)S->flux / (double)n_rays);
+  if (S->kind == FR_SOURCE_COLLIMATED) {
+    if (S->cols < 1 || S->rows < 1 || (uint64_t)S->cols * (uint64_t)S->rows != n_rays)
+      return set_error(h, FR_ERR_INVALID_ARG, "collimated source needs n_rays == cols * rows");
+    if (S->cols > (1 << 24) || S->rows > (1 << 24))
+      return set_error(h, FR_ERR_INVALID_ARG, "collimated grid side above 2^24");
+    it->cols = S->cols;
+    it->rows = S->rows;
+    it->jitter = S->jitter ? 1 : 0;
+    it->gnx = it->gny = 1;
+  } else if (S->kind == FR_SOURCE_POINT) {
+    if (!(S->half_angle > 0.0f) || !(S->half_angle < 1.5707963f))
+      return set_error(h, FR_ERR_INVALID_ARG, "half_angle must be in (0, pi/2)");
+    if (S->grid_nx < 1 || S->grid_ny < 1 || S->grid_nx > 4096 || S->grid_ny > 4096)
+      return set_error(h, FR_ERR_INVALID_ARG, "grid of sources must be 1..4096 per axis");
+    const uint64_t nsrc = (uint64_t)S->grid_nx * (uint64_t)S->grid_ny;
+    if (n_rays % nsrc != 0) return set_error(h, FR_ERR_INVALID_ARG, "n_rays must be a multiple of the sources");
+    if (n_rays / nsrc > 0xffffffffull) return set_error(h, FR_ERR_UNSUPPORTED, "more than 2^32 rays per source");
+    if (!(S->pos[2] < L->z_in) || !finite(S->pos[0]) || !finite(S->pos[1]))
+      return set_error(h, FR_ERR_INVALID_ARG, "the point source must lie before the entry face");
+    it->px = S->pos[0];
+    it->py = S->pos[1];
+    it->pz = S->pos[2];
+    it->omc_max = (float)(1.0 - std::cos((double)S->half_angle));
+    it->gnx = S->grid_nx;
+    it->gny = S->grid_ny;
+    it->gx0 = S->grid_nx > 1 ? -0.5f * S->grid_w : 0.0f;
+    it->gy0 = S->grid_ny > 1 ? -0.5f * S->grid_h : 0.0f;
+    it->gdx = S->grid_nx > 1 ? S->grid_w / (float)(S->grid_nx - 1) : 0.0f;
+    it->gdy = S->grid_ny > 1 ? S->grid_h / (float)(S->grid_ny - 1) : 0.0f;
+    it->per_src = (uint32_t)(n_rays / nsrc);
+  } else {
+    return set_error(h, FR_ERR_INVALID_ARG, "unknown source kind %d", S->kind);
+  }
+  // Screen.
+  it->z_screen = T->z_screen;
+  it->Rx = T->Rx;
+  it->Ry = T->Ry;
+  it->nx = T->nx;
+  it->ny = T->ny;
+  it->nu = T->nu_x;
+  it->ncol = T->nx + T->nu_x - 1;
+  it->nrow = T->ny + T->nu_y - 1;
+  const double wx = 2.0 * T->Rx / T->nx, wy = 2.0 * T->Ry / T->ny;
+  it->inv_wx = (float)(1.0 / wx);
+  it->inv_wy = (float)(1.0 / wy);
+  it->Rsx = (float)(T->Rx + 0.5 * (T->nu_x - 1) * wx);
+  it->Rsy = (float)(T->Ry + 0.5 * (T->nu_y - 1) * wy);
+  it->ax = (float)(T->alpha * 1.4426950408889634);
+  it->ay = it->ax;
+  it->cut = (float)std::exp(-(double)T->alpha * 0.25 * T->nu_x * T->nu_x);
+  it->inv_area = (float)(1.0 / (wx * wy));
+  // Fixed-point scale of E: a single contribution is at most omega0 / area.
+  {
+    const double cmax = std::fabs((double)S->flux) / (double)n_rays / (wx * wy);
+    int e = 0;
+    std::frexp(cmax > 0 ? cmax : 1.0, &e);
+    it->fixE = (float)std::ldexp(1.0, 32 - e);
+    it->fixP_unit = (float)(std::fabs((double)S->flux) / (wx * wy));
+  }
+  it->newton_max = o.newton_max_iter;
+  it->newton_tol = o.newton_tol;
+  return FR_OK;
+}
+
+
+// Tiles of an item for a CTA of `warps` warps.
+void schedule_item(Item* it, int warps, const fr_options& o) {
+  const uint64_t count = it->ray_end - it->ray_begin;
+  if (it->kind == FR_SOURCE_COLLIMATED) {
+    int R = o.rays_per_lane > 0 ? o.rays_per_lane : std::min(16, std::max(1, (it->cols + 31) / 32));
+    R = std::min(R, 64);
+    it->rays_per_lane = R;
+    if (count == 0) {
+      it->row_lo = it->row_hi = 0;
+      it->segs = 1;
+      it->tiles = 0;
+      return;
+    }
+    it->row_lo = (int)(it->ray_begin / (uint64_t)it->cols);
+    it->row_hi = (int)((it->ray_end - 1) / (uint64_t)it->cols) + 1;
+    const int groups = (it->row_hi - it->row_lo + warps - 1) / warps;
+    it->segs = (it->cols + 32 * R - 1) / (32 * R);
+    it->tiles = groups * it->segs;
+  } else {
+    int R = o.rays_per_lane > 0 ? o.rays_per_lane : 4;
+    R = std::min(R, 64);
+    it->rays_per_lane = R;
+    const uint64_t per_tile = (uint64_t)warps * 32 * (uint64_t)R;
+    it->tiles = (int)((count + per_tile - 1) / per_tile);
+  }
+}
+
+int pick_warps(const fr_options& o) { return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 8) : 8; }
+
+bool want_smem_hist(const Item& it, const fr_options& o, bool det) {
+  const size_t hist = (size_t)it.ncol * it.nrow * (det ? 8 : 4);
+  const size_t patches = (size_t)it.nsu * it.nsv * 4 * sizeof(float4);
+  if (hist + patches > 200 * 1024) return false;
+  if (o.hist_mode == 1) return false;
+  if (o.hist_mode == 2) return true;
+  return hist <= 100 * 1024;
+}
+
+// Splits `total_ctas` over the items in proportion to their estimated cost.
+void assign_ctas(std::vector<Item>& items, int total_ctas) {
+  double cost_sum = 0.0;
+  std::vector<double> cost(items.size());
+  for (size_t i = 0; i < items.size(); ++i) {
+    const double rays = (double)(items[i].ray_end - items[i].ray_begin);
+    cost[i] = rays * (items[i].kind == FR_SOURCE_POINT ? 3.0 : 1.0);
+    cost_sum += cost[i];
+  }
+  int at = 0;
+  for (size_t i = 0; i < items.size(); ++i) {
+    int g = items[i].tiles == 0 ? 0
+            : std::max(1, (int)std::lround(cost_sum > 0 ? total_ctas * cost[i] / cost_sum : 1.0));
+    g = std::min(g, items[i].tiles);
+    items[i].cta_begin = at;
+    items[i].cta_end = at + g;
+    at += g;
+  }
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Forward / adjoint over a list of items (one launch of the trace kernel).
+template <int CAP>
+fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o, bool adjoint,
+                    cudaStream_t st) {
+  const bool det = o.deterministic != 0;
+  const int warps = pick_warps(o);
+  // Workspace.
+  size_t at = kHeaderBytes;
+  std::vector<ItemWs> ws(items.size());
+  for (size_t i = 0; i < items.size(); ++i) {
+    ws[i] = plan(items[i], at, det && !adjoint, det && adjoint);
+    at = ws[i].end;
+  }
+  fr_status s = ensure_workspace(h, at, st);
+  if (s != FR_OK) return s;
+  size_t smem = 0;
+  for (size_t i = 0; i < items.size(); ++i) {
+    Item& it = items[i];
+    it.patch = reinterpret_cast<float4*>(h->ws + ws[i].patch);
+    it.basis_u = reinterpret_cast<float4*>(h->ws + ws[i].basis_u);
+    it.basis_v = reinterpret_cast<float4*>(h->ws + ws[i].basis_v);
+    it.zb = reinterpret_cast<float*>(h->ws + ws[i].zb);
+    it.Efix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].efix);
+    it.Pfix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].pfix);
+    it.gmax = reinterpret_cast<float*>(h->ws + ws[i].gmax);
+    schedule_item(&it, warps, o);
+    if (!adjoint) it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
+    smem = std::max(smem, adjoint ? fr::adj_smem_bytes(it, det) : fr::fwd_smem_bytes(it, det));
+  }
+  // Prep: power-form patches, basis tables and bounds of every lens.
+  {
+    cudaError_t e = fr::launch_prep(items.data(), (int)items.size(), st);
+    if (e != cudaSuccess) return cuda_error(h, e, "prep kernel");
+  }
+  // Outputs.
+  for (size_t i = 0; i < items.size(); ++i) {
+    Item& it = items[i];
+    if (!adjoint) {
+      if (det) FR_CUDA(h, cudaMemsetAsync(it.Efix, 0, (size_t)it.ncol * it.nrow * 8, st), "memset");
+      else if (!o.accumulate) FR_CUDA(h, cudaMemsetAsync(it.E, 0, (size_t)it.ncol * it.nrow * 4, st), "memset");
+    } else {
+      if (det) {
+        FR_CUDA(h, cudaMemsetAsync(it.Pfix, 0, (size_t)it.ncu * it.ncv * 8, st), "memset");
+        cudaError_t e = fr::launch_absmax(it.dLdE, (size_t)it.ncol * it.nrow, const_cast<float*>(it.gmax), st);
+        if (e != cudaSuccess) return cuda_error(h, e, "absmax kernel");
+      } else if (!o.accumulate) {
+        FR_CUDA(h, cudaMemsetAsync(it.dLdP, 0, (size_t)it.ncu * it.ncv * 4, st), "memset");
+      }
+    }
+  }
+  // Trace.
+  const int threads = warps * 32;
+  const bool batch = CAP > 1;
+  const int occ = adjoint ? fr::adjoint_occupancy(threads, smem, det, batch)
+                          : fr::forward_occupancy(threads, smem, det, batch);
+  if (occ <= 0) return set_error(h, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
+  const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
+  int total_tiles = 0;
+  for (auto& it : items) total_tiles += it.tiles;
+  if (total_tiles > 0) {
+    const int want = std::max<int>(1, h->sm_count * per_sm);
+    if (items.size() == 1) {
+      items[0].cta_begin = 0;
+      items[0].cta_end = std::min(want, items[0].tiles);
+    } else {
+      assign_ctas(items, std::max<int>(want, (int)items.size()));
+    }
+    int grid = 0;
+    fr::Launch<CAP> L;
+    std::memset(&L, 0, sizeof L);
+    L.n_items = (int)items.size();
+    L.warps = warps;
+    for (size_t i = 0; i < items.size(); ++i) {
+      L.items[i] = items[i];
+      grid = std::max(grid, items[i].cta_end);
+    }
+    // Items without CTAs keep cta_end == cta_begin and are skipped by the lookup.
+    cudaError_t e = adjoint ? fr::launch_adjoint<CAP>(L, grid, smem, det, st)
+                            : fr::launch_forward<CAP>(L, grid, smem, det, st);
+    if (e != cudaSuccess) return cuda_error(h, e, adjoint ? "adjoint kernel" : "forward kernel");
+  }
+  // Fixed point back to float.
+  if (det) {
+    for (auto& it : items) {
+      cudaError_t e = adjoint ? fr::launch_grad_fix_to_float(it, o.accumulate, st)
+                              : fr::launch_fix_to_float(it.Efix, it.E, (size_t)it.ncol * it.nrow,
+                                                        1.0f / it.fixE, o.accumulate, st);
+      if (e != cudaSuccess) return cuda_error(h, e, "fixed-point conversion");
+    }
+  }
+  return FR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t fr_abi_version(void) { return FR_ABI_VERSION; }
+
+fr_status fr_create(fr_handle** out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  fr_handle* h = new (std::nothrow) fr_handle();
+  if (!h) return FR_ERR_INVALID_ARG;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = fr::configure_forward();
+  if (e == cudaSuccess) e = fr::configure_adjoint();
+  if (e != cudaSuccess) {
+    delete h;
+    return FR_ERR_CUDA;
+  }
+  *out = h;
+  return FR_OK;
+}
+
+fr_status fr_destroy(fr_handle* h) {
+  if (!h) return FR_OK;
+  fr_status s = FR_OK;
+  if (h->ws) {
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaFree(h->ws) != cudaSuccess) s = FR_ERR_CUDA;
+  }
+  delete h;
+  return s;
+}
+
+const char* fr_last_error(const fr_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+fr_status fr_trace_forward(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                           const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
+                           uint64_t ray_count, const fr_options* options, float* E_out, fr_stats* stats_out,
+                           void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  const fr_options o = defaults(options);
+  if (!E_out) return set_error(h, FR_ERR_INVALID_ARG, "E_out is null");
+  std::vector<Item> items(1);
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &items[0]);
+  if (s != FR_OK) return s;
+  items[0].E = E_out;
+  items[0].stats = stats_out;
+  return run_trace<1>(h, items, o, false, as_stream(stream));
+}
+
+fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                           const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
+                           uint64_t ray_count, const fr_options* options, const float* dLdE, float* dLdP_out,
+                           fr_stats* stats_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  const fr_options o = defaults(options);
+  if (!dLdE || !dLdP_out) return set_error(h, FR_ERR_INVALID_ARG, "dLdE or dLdP_out is null");
+  std::vector<Item> items(1);
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &items[0]);
+  if (s != FR_OK) return s;
+  items[0].dLdE = dLdE;
+  items[0].dLdP = dLdP_out;
+  items[0].stats = stats_out;
+  return run_trace<1>(h, items, o, true, as_stream(stream));
+}
+
+fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                         const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
+                         uint64_t ray_count, const fr_options* options, fr_ray_record* out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  const fr_options o = defaults(options);
+  if (!out) return set_error(h, FR_ERR_INVALID_ARG, "out is null");
+  Item it;
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
+  if (s != FR_OK) return s;
+  const ItemWs w = plan(it, kHeaderBytes, false, false);
+  s = ensure_workspace(h, w.end, as_stream(stream));
+  if (s != FR_OK) return s;
+  it.patch = reinterpret_cast<float4*>(h->ws + w.patch);
+  it.basis_u = reinterpret_cast<float4*>(h->ws + w.basis_u);
+  it.basis_v = reinterpret_cast<float4*>(h->ws + w.basis_v);
+  it.zb = reinterpret_cast<float*>(h->ws + w.zb);
+  cudaError_t e = fr::launch_prep(&it, 1, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "prep kernel");
+  e = fr::launch_debug(it, out, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "debug kernel");
+  return FR_OK;
+}
+
+fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny, int32_t nu_x,
+                     int32_t nu_y, double* loss_out, float* dLdE_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || nu_x < 1 || nu_y < 1 || nu_x % 2 == 0 || nu_y % 2 == 0)
+    return set_error(h, FR_ERR_INVALID_ARG, "bad grid sizes");
+  fr_status s = ensure_workspace(h, kHeaderBytes, as_stream(stream));
+  if (s != FR_OK) return s;
+  double* partials = reinterpret_cast<double*>(h->ws);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(h->ws + fr::kLossBlocks * sizeof(double));
+  cudaError_t e = fr::launch_loss(E, E_ref, nx, ny, nu_x, nu_y, partials, counter, loss_out, dLdE_out,
+                                  as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "loss kernel");
+  return FR_OK;
+}
+
+fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* g, int64_t n, float lr, float beta1,
+                       float beta2, float eps, int32_t* step, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!P || !m || !v || !g || !step) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  if (n < 0) return set_error(h, FR_ERR_INVALID_ARG, "n < 0");
+  if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) || !finite(lr))
+    return set_error(h, FR_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+  cudaError_t e = fr::launch_adam(P, m, v, g, n, lr, beta1, beta2, eps, step, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "adam kernel");
+  return FR_OK;
+}
+
+static fr_status batch(fr_handle* h, const fr_batch_item* in, int32_t n_items, const fr_options* options,
+                       void* stream, bool adjoint) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!in || n_items < 1 || n_items > fr::kMaxItems)
+    return set_error(h, FR_ERR_INVALID_ARG, "n_items must be 1..%d", fr::kMaxItems);
+  const fr_options o = defaults(options);
+  std::vector<Item> items(n_items);
+  for (int i = 0; i < n_items; ++i) {
+    fr_status s = make_item(h, &in[i].lens, &in[i].source, &in[i].target, in[i].n_rays, in[i].seed, 0,
+                            UINT64_MAX, o, &items[i]);
+    if (s != FR_OK) {
+      const std::string msg = h->err;
+      return set_error(h, s, "item %d: %s", i, msg.c_str());
+    }
+    if (adjoint ? (!in[i].dLdE || !in[i].dLdP) : !in[i].E)
+      return set_error(h, FR_ERR_INVALID_ARG, "item %d: null buffer", i);
+    items[i].E = in[i].E;
+    items[i].dLdE = in[i].dLdE;
+    items[i].dLdP = in[i].dLdP;
+    items[i].stats = in[i].stats;
+  }
+  return run_trace<fr::kMaxItems>(h, items, o, adjoint, as_stream(stream));
+}
+
+fr_status fr_trace_batch_forward(fr_handle* h, const fr_batch_item* items, int32_t n_items,
+                                 const fr_options* options, void* stream) {
+  return batch(h, items, n_items, options, stream, false);
+}
+
+fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32_t n_items,
+                                 const fr_options* options, void* stream) {
+  return batch(h, items, n_items, options, stream, true);
+}
+
+fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(as_stream(stream));
+    if (e == cudaSuccess) return FR_OK;
+    if (e != cudaErrorNotReady) return cuda_error(h, e, "cudaStreamQuery");
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+    if (ms.count() >= timeout_ms) return set_error(h, FR_ERR_TIMEOUT, "stream not done after %d ms", timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+}
+
+}  // extern "C"

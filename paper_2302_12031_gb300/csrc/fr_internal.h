@@ -1,0 +1,105 @@
+// Internal declarations shared by the CUDA translation units of libfreeray.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "freeray.h"
+
+namespace fr {
+
+constexpr int kMaxCtrl = 32;              // control points per direction
+constexpr int kMaxSpans = kMaxCtrl - 3;   // knot spans per direction (degree 3)
+constexpr int kMaxItems = 64;             // lenses per batched launch
+constexpr int kLossBlocks = 120;          // fixed grid of the loss reduction
+
+// Device view of one lens problem: lens, source, screen, outputs and schedule.
+// Built on the host by the C ABI from the public descriptors.
+struct Item {
+  // Lens (Sec. 2.1). Spans are the non-empty knot spans of the clamped uniform
+  // knot vector: nsu = ncu - 3 along u, nsv = ncv - 3 along v.
+  const float* ctrl;
+  int ncu, ncv, nsu, nsv;
+  float rx, ry, z_in, n_glass;
+  float ku, kv;                 // d(span coordinate)/dx = nsu/(2 rx), likewise kv
+  float R0;                     // ((n-1)/(n+1))^2
+  // Workspace written by the prep kernel.
+  float4* patch;                // [nsu*nsv][4]: row e holds C[e][0..3] of Z = sum C[e][f] s^e t^f
+  float4* basis_u;              // [nsu][4]: coefficients of N_{k+a}(s) in powers of s
+  float4* basis_v;              // [nsv][4]
+  float* zb;                    // [2]: min and max control height
+  // Source (Sec. 2.2.1).
+  int kind, jitter, cols, rows;
+  float px, py, pz;             // source position (grid centre)
+  float omc_max;                // 1 - cos(phi_max)
+  int gnx, gny;
+  float gx0, gy0, gdx, gdy;     // first grid position offset and spacing
+  uint32_t per_src;             // rays per point source of the grid
+  uint64_t seed, n_rays;
+  uint64_t ray_begin, ray_end;  // rays traced by this call
+  float omega0;                 // flux / n_rays
+  // Screen and filter (Sec. 2.3).
+  float z_screen, Rx, Ry;
+  int nx, ny, nu, ncol, nrow;
+  float inv_wx, inv_wy;         // 1/w
+  float Rsx, Rsy;               // R* = R + (nu-1)/2 w
+  float ax, ay;                 // alpha * log2(e)
+  float cut;                    // exp(-alpha (nu/2)^2)
+  float inv_area;               // 1/(w_x w_y)
+  // Outputs.
+  float* E;                     // forward, float mode
+  unsigned long long* Efix;     // forward, deterministic mode
+  float fixE;                   // fixed-point scale of E (a power of two)
+  const float* dLdE;            // adjoint input
+  float* dLdP;                  // adjoint, float mode
+  unsigned long long* Pfix;     // adjoint, deterministic mode
+  const float* gmax;            // adjoint, deterministic: max |dL/dE| (device)
+  float fixP_unit;              // adjoint, deterministic: flux / (w_x w_y)
+  fr_stats* stats;
+  // Newton (Sec. 2.2.1 intersection, point sources).
+  int newton_max;
+  float newton_tol;
+  // Schedule.
+  int rays_per_lane;            // consecutive rays per lane in a tile row (collimated) or per tile
+  int row_lo, row_hi;           // collimated: grid rows touched by [ray_begin, ray_end)
+  int segs;                     // collimated: tiles per row group
+  int tiles;                    // tiles of this item
+  int smem_hist;                // forward: 1 = privatised histogram in shared memory
+  int cta_begin, cta_end;       // CTAs of the launch that work on this item
+};
+
+template <int CAP>
+struct Launch {
+  int n_items;
+  int warps;                    // warps per CTA
+  Item items[CAP];
+};
+
+// Shared-memory bytes a CTA of the forward / adjoint kernel needs for `it`.
+size_t fwd_smem_bytes(const Item& it, bool det);
+size_t adj_smem_bytes(const Item& it, bool det);
+
+// Launchers (return the CUDA error of the launch).
+cudaError_t launch_prep(const Item* items, int n_items, cudaStream_t st);
+template <int CAP>
+cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
+template <int CAP>
+cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
+cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st);
+cudaError_t launch_fix_to_float(const unsigned long long* q, float* out, size_t n, float inv_scale,
+                                int accumulate, cudaStream_t st);
+cudaError_t launch_absmax(const float* x, size_t n, float* out, cudaStream_t st);
+cudaError_t launch_loss(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y,
+                        double* partials, unsigned int* counter, double* loss, float* dLdE,
+                        cudaStream_t st);
+cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1,
+                        float b2, float eps, int32_t* step, cudaStream_t st);
+
+// Kernel attributes that must be set before the first launch (max dynamic smem).
+cudaError_t configure_kernels();
+// Occupancy of the trace kernels for a block size and dynamic shared memory.
+int forward_occupancy(int threads, size_t smem, bool det, bool batch);
+int adjoint_occupancy(int threads, size_t smem, bool det, bool batch);
+
+}  // namespace fr

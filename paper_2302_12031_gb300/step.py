@@ -1,0 +1,117 @@
+"""The optimisation step (rows a1-a10) for one lens or a batch of lenses.
+
+One step = forward trace -> squared-L2 loss and dL/dE -> recompute adjoint ->
+Adam on the control heights, all on one stream. With graph=True the step is
+captured once into a CUDA graph and every later step is one graph replay.
+The control heights, Adam moments and the step counter of all lenses live in
+flat device buffers, so one Adam launch updates every lens.
+"""
+import torch
+
+from . import api
+
+
+class OptimStep:
+    def __init__(self, workloads, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, options=None, graph=True,
+                 device="cuda"):
+        if isinstance(workloads, dict):
+            workloads = [workloads]
+        self.h = api.default_handle()
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.options = options
+        sizes = [(w["lens"]["n1"] + 1) * (w["lens"]["n2"] + 1) for w in workloads]
+        n = sum(sizes)
+        self.n_params = n
+        self.P = torch.empty(n, dtype=torch.float32, device=device)
+        self.m = torch.zeros(n, dtype=torch.float32, device=device)
+        self.v = torch.zeros(n, dtype=torch.float32, device=device)
+        self.g = torch.zeros(n, dtype=torch.float32, device=device)
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.problems, self.E, self.dLdE, self.E_ref, self.loss = [], [], [], [], []
+        at = 0
+        for w, sz in zip(workloads, sizes):
+            shape = (w["lens"]["n1"] + 1, w["lens"]["n2"] + 1)
+            view = self.P[at:at + sz].view(shape)
+            view.copy_(torch.as_tensor(w["lens"]["P"], dtype=torch.float32))
+            pb = api.Problem(w, ctrl_z=view, device=device)
+            self.problems.append(pb)
+            self.E.append(torch.zeros(pb.ext_shape, dtype=torch.float32, device=device))
+            self.dLdE.append(torch.zeros(pb.ext_shape, dtype=torch.float32, device=device))
+            self.E_ref.append(torch.as_tensor(w["E_ref"], dtype=torch.float32, device=device).contiguous())
+            self.loss.append(torch.zeros((), dtype=torch.float64, device=device))
+            at += sz
+        self.grads = []
+        at = 0
+        for pb, sz in zip(self.problems, sizes):
+            self.grads.append(self.g[at:at + sz].view(pb.ctrl_shape))
+            at += sz
+        self.n_rays = sum(pb.n_rays for pb in self.problems)
+        self.batched = len(self.problems) > 1
+        self.graph = None
+        if graph:
+            self._capture()
+
+    def _forward(self):
+        if self.batched:
+            items = [pb.batch_item(E=E) for pb, E in zip(self.problems, self.E)]
+            api.fr_trace_batch_forward(self.h, items, self.options)
+        else:
+            pb = self.problems[0]
+            api.fr_trace_forward(self.h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS,
+                                 self.options, self.E[0])
+
+    def _loss(self):
+        for pb, E, Er, d, L in zip(self.problems, self.E, self.E_ref, self.dLdE, self.loss):
+            api.fr_loss_l2(self.h, E, Er, pb.nx, pb.ny, pb.nu_x, pb.nu_y, L, d)
+
+    def _adjoint(self):
+        if self.batched:
+            items = [pb.batch_item(dLdE=d, dLdP=g) for pb, d, g in zip(self.problems, self.dLdE, self.grads)]
+            api.fr_trace_batch_adjoint(self.h, items, self.options)
+        else:
+            pb = self.problems[0]
+            api.fr_trace_adjoint(self.h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS,
+                                 self.options, self.dLdE[0], self.grads[0])
+
+    def _adam(self):
+        api.fr_adam_step(self.h, self.P, self.m, self.v, self.g, self.n_params, self.lr, self.betas[0],
+                         self.betas[1], self.eps, self.step_count)
+
+    def eager_step(self):
+        self._forward()
+        self._loss()
+        self._adjoint()
+        self._adam()
+
+    def _capture(self):
+        saved = [t.clone() for t in (self.P, self.m, self.v, self.step_count)]
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.eager_step()          # sizes the handle's scratch memory before capture
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.eager_step()
+        torch.cuda.synchronize()
+        for t, v in zip((self.P, self.m, self.v, self.step_count), saved):
+            t.copy_(v)
+        torch.cuda.synchronize()
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.eager_step()
+
+    def losses(self):
+        return torch.stack(self.loss).cpu()
+
+    # Kernel launches per step (for the launch count of a timed region).
+    def launches_per_step(self):
+        n_items = len(self.problems)
+        det = bool(self.options is not None and self.options.deterministic)
+        fwd = 2 + (n_items if det else 0)                 # prep + trace (+ fixed->float)
+        adj = 2 + (2 * n_items if det else 0)             # prep + trace (+ absmax, fixed->float)
+        return fwd + n_items + adj + 1                    # + one loss per lens + Adam

@@ -24,14 +24,14 @@ def test_philox_known_answer_vectors(oracle):
         assert oracle.philox4x32_10(ctr, key) == expect
 
 
-def test_ray_uniforms_are_top_24_bits_plus_half(oracle):
+def test_ray_uniforms_are_top_23_bits_plus_half(oracle):
     for seed, rid in [(1, 0), (4, 12345), (2**40 + 7, 2**33 + 5)]:
         ctr = [rid & 0xffffffff, rid >> 32, 0, 0]
         key = [seed & 0xffffffff, seed >> 32]
         w = oracle.philox4x32_10(ctr, key)
         a, b = oracle.ray_uniforms(seed, rid)
-        assert a == ((w[0] >> 8) + 0.5) / 2**24
-        assert b == ((w[1] >> 8) + 0.5) / 2**24
+        assert a == ((w[0] >> 9) + 0.5) / 2**23
+        assert b == ((w[1] >> 9) + 0.5) / 2**23
         assert 0.0 < a < 1.0 and 0.0 < b < 1.0
 
 
