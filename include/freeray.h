@@ -161,7 +161,8 @@ typedef struct fr_handle fr_handle;
 fr_status fr_create(fr_handle** out);
 fr_status fr_destroy(fr_handle* h);
 
-/* Message of the last failure on this handle ("" if none). Valid until the next call. */
+/* Message of the last failure on this handle ("" if none). Valid until the next
+ * call. With h == NULL: the last failure of fr_create on this host thread. */
 const char* fr_last_error(const fr_handle* h);
 
 /* ABI version (FR_ABI_VERSION) of the loaded library. */

@@ -131,7 +131,7 @@ class Handle:
         h = C.c_void_p()
         st = lib().fr_create(C.byref(h))
         if st != FR_OK:
-            raise FreerayError(st, "fr_create failed")
+            raise FreerayError(st, lib().fr_last_error(None).decode())
         self.ptr = h
 
     def check(self, status):

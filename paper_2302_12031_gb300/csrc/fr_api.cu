@@ -14,14 +14,15 @@
 #include "fr_internal.h"
 
 namespace fr {
-cudaError_t configure_forward();
-cudaError_t configure_adjoint();
+cudaError_t configure_forward(int optin);
+cudaError_t configure_adjoint(int optin);
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);
 }  // namespace fr
 
 struct fr_handle {
   int device = 0;
   int sm_count = 0;
+  int smem_optin = 0;           // max dynamic + static shared memory per block
   unsigned char* ws = nullptr;   // scratch memory owned by the handle
   size_t ws_bytes = 0;
   std::string err;
@@ -36,6 +37,8 @@ constexpr size_t kHeaderBytes = 2048;   // loss partials and counter at the star
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+thread_local std::string g_err;   // failures without a handle (fr_create)
+
 fr_status set_error(fr_handle* h, fr_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -43,6 +46,7 @@ fr_status set_error(fr_handle* h, fr_status s, const char* fmt, ...) {
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
   if (h) h->err = buf;
+  else g_err = buf;
   return s;
 }
 
@@ -340,7 +344,8 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   const bool batch = CAP > 1;
   const int occ = adjoint ? fr::adjoint_occupancy(threads, smem, det, batch)
                           : fr::forward_occupancy(threads, smem, det, batch);
-  if (occ <= 0) return set_error(h, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
+  if (occ <= 0 || smem + 1024 > (size_t)h->smem_optin)
+    return set_error(h, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
   const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
   int total_tiles = 0;
   for (auto& it : items) total_tiles += it.tiles;
@@ -385,17 +390,19 @@ extern "C" {
 int32_t fr_abi_version(void) { return FR_ABI_VERSION; }
 
 fr_status fr_create(fr_handle** out) {
-  if (!out) return FR_ERR_INVALID_ARG;
+  if (!out) return set_error(nullptr, FR_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
   fr_handle* h = new (std::nothrow) fr_handle();
-  if (!h) return FR_ERR_INVALID_ARG;
+  if (!h) return set_error(nullptr, FR_ERR_INVALID_ARG, "out of host memory");
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-  if (e == cudaSuccess) e = fr::configure_forward();
-  if (e == cudaSuccess) e = fr::configure_adjoint();
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e == cudaSuccess) e = fr::configure_forward(h->smem_optin);
+  if (e == cudaSuccess) e = fr::configure_adjoint(h->smem_optin);
   if (e != cudaSuccess) {
     delete h;
-    return FR_ERR_CUDA;
+    return cuda_error(nullptr, e, "fr_create");
   }
   *out = h;
   return FR_OK;
@@ -411,7 +418,10 @@ fr_status fr_destroy(fr_handle* h) {
   return s;
 }
 
-const char* fr_last_error(const fr_handle* h) { return h ? h->err.c_str() : "null handle"; }
+const char* fr_last_error(const fr_handle* h) {
+  if (h) return h->err.c_str();
+  return g_err.empty() ? "null handle" : g_err.c_str();
+}
 
 fr_status fr_trace_forward(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
                            const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,

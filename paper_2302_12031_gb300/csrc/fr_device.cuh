@@ -357,8 +357,10 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const RayFwd& r, con
   }
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    gxa[a] = (gxa[a] - Fx[a] * Spx) * f.rsx;
-    gya[a] = (gya[a] - Fy[a] * Spy) * f.rsy;
+    // With nu = 1 the normalised filter is identically 1 on its pixel: its
+    // derivative is exactly 0 (the general formula leaves rounding noise).
+    gxa[a] = NU == 1 ? 0.0f : (gxa[a] - Fx[a] * Spx) * f.rsx;
+    gya[a] = NU == 1 ? 0.0f : (gya[a] - Fy[a] * Spy) * f.rsy;
   }
   float wbar = 0.0f, Xs = 0.0f, Ys = 0.0f;
 #pragma unroll

@@ -96,8 +96,8 @@ cudaError_t launch_loss(const float* E, const float* Eref, int nx, int ny, int n
 cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1,
                         float b2, float eps, int32_t* step, cudaStream_t st);
 
-// Kernel attributes that must be set before the first launch (max dynamic smem).
-cudaError_t configure_kernels();
+
+
 // Occupancy of the trace kernels for a block size and dynamic shared memory.
 int forward_occupancy(int threads, size_t smem, bool det, bool batch);
 int adjoint_occupancy(int threads, size_t smem, bool det, bool batch);

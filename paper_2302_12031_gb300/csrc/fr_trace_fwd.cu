@@ -298,14 +298,22 @@ int forward_occupancy(int threads, size_t smem, bool det, bool batch) {
   return n;
 }
 
-cudaError_t configure_forward() {
-  const int mx = 227 * 1024;
+// Opt every variant of the kernel in to the largest dynamic shared memory the
+// device allows next to the kernel's own static shared memory.
+template <class K>
+static cudaError_t allow_max_smem(K kernel, int optin) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+}
+
+cudaError_t configure_forward(int optin) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_forward<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-  if ((e = cudaFuncSetAttribute(k_forward<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-  if ((e = cudaFuncSetAttribute(k_forward<kMaxItems, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)))
-    return e;
-  return cudaFuncSetAttribute(k_forward<kMaxItems, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if ((e = allow_max_smem(k_forward<1, false>, optin))) return e;
+  if ((e = allow_max_smem(k_forward<1, true>, optin))) return e;
+  if ((e = allow_max_smem(k_forward<kMaxItems, false>, optin))) return e;
+  return allow_max_smem(k_forward<kMaxItems, true>, optin);
 }
 
 }  // namespace fr
