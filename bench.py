@@ -1,0 +1,361 @@
+"""Benchmark of the differentiable freeform-lens trace on GB300.
+
+Default workload (N = 1): collimated beam, 2048 x 2048 rays (4.2M), bicubic
+16 x 16 control net, 128 x 128 bins over a 2 x 2 screen. One step is the whole
+hot path: forward trace, squared-L2 loss and dL/dE, recompute adjoint to the
+control heights, Adam, replayed from a CUDA graph. The headline `value` is
+forward+adjoint rays per second over all GPUs; the forward-only rays/s, the
+roofline of the dominant kernel (timed live with CUDA events on its stream),
+an end-to-end figure through the public API with host buffers, the oracle on
+the host cores, and secondary workloads (point source, batched graph steps)
+are reported beside it on the same JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 it runs under torchrun, one rank per GPU; every rank traces its own
+replica (the path has no exchange step), and the timing is the max over ranks.
+`--impl reference` times the FP64 oracle on the host cores instead (the paper
+publishes no code to run).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/s per forward+adjoint step vs forward-only at stated error; % roofline"
+L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
+
+# Algorithmic work per ray, counted from the formulas the kernels evaluate
+# (FMA = 2 flops; +, -, *, exp2, sqrt, rsqrt, reciprocal = 1). The counts and
+# their breakdown are in the design doc.
+FLOPS_FWD_COLLIMATED = 185
+FLOPS_ADJ_COLLIMATED = 490
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, mhz):
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_steps(fn, steps, warmup, flush):
+    """Per-step device time (ms) of fn() with an L2 flush before every step."""
+    import torch
+    for _ in range(warmup):
+        flush()
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        flush()
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def graphed(fn):
+    """fn captured into a CUDA graph (after one eager run); returns its replay."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g.replay
+
+
+def oracle_rays_per_s(wl, n_sample, begin):
+    """The FP64 oracle (forward + gradient) on rays [begin, begin+n_sample)."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    E, _ = O.trace_forward(wl, begin=begin, count=n_sample)
+    _, d = O.loss_l2(wl, E)
+    O.trace_gradient(wl, d, begin=begin, count=n_sample)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm, on the host cores."""
+    if rank != 0:
+        return
+    from paper_2302_12031_gb300 import workloads as W
+    from oracle import oracle as O
+    wl = W.config(2)
+    n_sample = 1 << 16
+    mid = wl["n_rays"] // 2
+    for _ in range(max(1, args.warmup)):
+        oracle_rays_per_s(wl, n_sample // 8, mid)
+    times = []
+    for k in range(args.steps):
+        v, dt = oracle_rays_per_s(wl, n_sample, mid + (k % 4) * n_sample)
+        times.append(dt)
+    value = args.steps * n_sample / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": "rays/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "rays": wl["n_rays"], "sample_rays_per_step": n_sample},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": O.default_threads(), "kind": "oracle",
+                             "sample": "%d consecutive rays per step from the middle of the 2048x2048 grid, "
+                                       "forward + gradient" % n_sample},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2302_12031_gb300 import api, step
+    from paper_2302_12031_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.zero_()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = W.config(2)
+    n_rays = wl["n_rays"]
+    ev_f = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev_a = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e in ev_f + ev_a:
+        e.record()                      # materialise the events before handing out their handles
+    torch.cuda.synchronize()
+    st = step.OptimStep(wl, lr=1e-3, graph=True, options=api.make_options(events=ev_f),
+                        adj_options=api.make_options(events=ev_a))
+
+    # --- headline: forward + loss + adjoint + Adam, one graph replay per step
+    for _ in range(args.warmup):
+        flush()
+        st.step()
+    barrier()
+    step_ms, fwd_kernel_ms, adj_kernel_ms = [], [], []
+    outer = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with ClockSampler(local) as clocks:
+        barrier()
+        total_ms = 0.0
+        for _ in range(args.steps):
+            flush()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st.step()
+            b.record()
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            fwd_kernel_ms.append(ev_f[0].elapsed_time(ev_f[1]))
+            adj_kernel_ms.append(ev_a[0].elapsed_time(ev_a[1]))
+        barrier()
+    t_local = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t)
+    else:
+        t_max = t_local
+    ms_per_step = t_max / args.steps
+    value = world * n_rays * args.steps / (t_max * 1e-3)
+
+    # --- forward only (prep + trace kernel through the C ABI)
+    pb = st.problems[0]
+    E = torch.empty(pb.ext_shape, dtype=torch.float32, device=dev)
+    h = api.default_handle()
+
+    def fwd():
+        api.fr_trace_forward(h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS, None, E)
+
+    f_ms = time_steps(graphed(fwd), args.steps, args.warmup, flush)
+    fwd_value = world * n_rays / (statistics.mean(f_ms) * 1e-3)
+
+    # --- end to end through the public API: pinned host heights in, loss out
+    P_host = torch.as_tensor(wl["lens"]["P"], dtype=torch.float32).reshape(-1).pin_memory()
+    loss_host = torch.zeros((), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.P.copy_(P_host, non_blocking=True)
+        st.step()
+        loss_host.copy_(st.loss[0], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = world * n_rays / (statistics.mean(e2e_ms) * 1e-3)
+
+    # --- roofline of the dominant kernel (the adjoint trace), timed live
+    pk, pk_kind = peaks()
+    fwd_k = statistics.mean(fwd_kernel_ms)
+    adj_k = statistics.mean(adj_kernel_ms)
+    dominant = "adjoint" if adj_k >= fwd_k else "forward"
+    k_ms = max(adj_k, fwd_k)
+    flops = n_rays * (FLOPS_ADJ_COLLIMATED if dominant == "adjoint" else FLOPS_FWD_COLLIMATED)
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(sm_count, pk.get("sm_max_mhz", 2070.0))
+    roofline = {"bound": "alu", "kernel": "k_%s (trace)" % dominant, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_note": "FP32 FMA peak %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock of %s peaks file)"
+                             % (sm_count, pk.get("sm_max_mhz", 2070.0), pk_kind),
+                "kernel_ms": {"forward": fwd_k, "adjoint": adj_k}}
+
+    line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "rays": n_rays, "control_net": "16x16", "bins": "128x128",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "step": "graph: prep+forward, loss, prep+adjoint, Adam"},
+            "forward_rays_per_s": fwd_value,
+            "forward_ms": statistics.mean(f_ms),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "rays/s", "h2d_bytes_per_step": P_host.numel() * 4,
+                    "d2h_bytes_per_step": 8},
+            "gpu_launches": st.launches_per_step() * args.steps,
+            "clocks": clocks.summary()}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import oracle as O
+        n_sample = 1 << 20
+        v, dt = oracle_rays_per_s(wl, n_sample, n_rays // 2 - n_sample // 2)
+        line["cpu_baseline"] = {"value": v, "unit": "rays/s", "cores": O.default_threads(), "kind": "oracle",
+                                "sample": "%d consecutive rays from the middle of the grid, forward + gradient, "
+                                          "%.1f s" % (n_sample, dt)}
+
+    if not args.no_extra:
+        line["extra"] = extra_workloads(args, flush, world)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extra_workloads(args, flush, world):
+    """Point source (16M rays) and the batched graph steps, fewer steps each."""
+    import torch
+    from paper_2302_12031_gb300 import step
+    from paper_2302_12031_gb300 import workloads as W
+    out = {}
+    k = max(3, args.steps // 4)
+    for name, wls in (("point_16M", W.config(3)), ("grid_8x8_64M_batched_graph", W.config(4)),
+                      ("sweep_32_lenses_batched_graph", W.config(5))):
+        st = step.OptimStep(wls, lr=1e-3, graph=True)
+        ms = time_steps(st.step, k, 2, flush)
+        rays = st.n_rays
+        out[name] = {"rays_per_step": rays, "ms_per_step": statistics.mean(ms),
+                     "rays_per_s": world * rays / (statistics.mean(ms) * 1e-3),
+                     "steps_per_s": 1e3 / statistics.mean(ms), "lenses": len(st.problems)}
+        del st
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

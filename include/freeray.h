@@ -120,6 +120,9 @@ typedef struct fr_options {
   int32_t rays_per_lane;    /* 0 -> tuned; 1..64 */
   int32_t ctas_per_sm;      /* 0 -> tuned; 1..8 */
   int32_t hist_mode;        /* 0 auto, 1 global atomics, 2 shared-memory privatised */
+  void* event_begin;        /* optional cudaEvent_t, recorded on the stream right before the
+                               trace kernel (not the prep or conversion kernels) */
+  void* event_end;          /* optional cudaEvent_t, recorded right after the trace kernel */
   int32_t reserved[8];
 } fr_options;
 

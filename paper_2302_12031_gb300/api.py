@@ -50,6 +50,7 @@ class Options(C.Structure):
                 ("newton_max_iter", C.c_int32), ("newton_tol", C.c_float),
                 ("warps_per_cta", C.c_int32), ("rays_per_lane", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("hist_mode", C.c_int32),
+                ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
                 ("reserved", C.c_int32 * 8)]
 
 
@@ -229,7 +230,8 @@ def fr_stream_wait(h, timeout_ms, stream=None):
 # --- descriptors from a workload dict ----------------------------------------
 
 def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newton_tol=0.0, warps_per_cta=0,
-                 rays_per_lane=0, ctas_per_sm=0, hist_mode=0):
+                 rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None):
+    """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel."""
     o = Options()
     o.deterministic = int(deterministic)
     o.accumulate = int(accumulate)
@@ -239,6 +241,9 @@ def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newto
     o.rays_per_lane = rays_per_lane
     o.ctas_per_sm = ctas_per_sm
     o.hist_mode = hist_mode
+    if events is not None:
+        o.event_begin = events[0].cuda_event
+        o.event_end = events[1].cuda_event
     return o
 
 

@@ -367,9 +367,17 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
       grid = std::max(grid, items[i].cta_end);
     }
     // Items without CTAs keep cta_end == cta_begin and are skipped by the lookup.
+    // While capturing, external records become event nodes of the graph.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (o.event_begin || o.event_end) FR_CUDA(h, cudaStreamIsCapturing(st, &cap), "cudaStreamIsCapturing");
+    const unsigned int rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (o.event_begin)
+      FR_CUDA(h, cudaEventRecordWithFlags((cudaEvent_t)o.event_begin, st, rec_flags), "cudaEventRecord");
     cudaError_t e = adjoint ? fr::launch_adjoint<CAP>(L, grid, smem, det, st)
                             : fr::launch_forward<CAP>(L, grid, smem, det, st);
     if (e != cudaSuccess) return cuda_error(h, e, adjoint ? "adjoint kernel" : "forward kernel");
+    if (o.event_end)
+      FR_CUDA(h, cudaEventRecordWithFlags((cudaEvent_t)o.event_end, st, rec_flags), "cudaEventRecord");
   }
   // Fixed point back to float.
   if (det) {

@@ -13,12 +13,15 @@ from . import api
 
 class OptimStep:
     def __init__(self, workloads, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, options=None, graph=True,
-                 device="cuda"):
+                 device="cuda", adj_options=None):
+        """`options` apply to both traces unless `adj_options` is given for the adjoint
+        (e.g. to record timing events around each trace kernel separately)."""
         if isinstance(workloads, dict):
             workloads = [workloads]
         self.h = api.default_handle()
         self.lr, self.betas, self.eps = lr, betas, eps
         self.options = options
+        self.adj_options = adj_options if adj_options is not None else options
         sizes = [(w["lens"]["n1"] + 1) * (w["lens"]["n2"] + 1) for w in workloads]
         n = sum(sizes)
         self.n_params = n
@@ -67,11 +70,11 @@ class OptimStep:
     def _adjoint(self):
         if self.batched:
             items = [pb.batch_item(dLdE=d, dLdP=g) for pb, d, g in zip(self.problems, self.dLdE, self.grads)]
-            api.fr_trace_batch_adjoint(self.h, items, self.options)
+            api.fr_trace_batch_adjoint(self.h, items, self.adj_options)
         else:
             pb = self.problems[0]
             api.fr_trace_adjoint(self.h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS,
-                                 self.options, self.dLdE[0], self.grads[0])
+                                 self.adj_options, self.dLdE[0], self.grads[0])
 
     def _adam(self):
         api.fr_adam_step(self.h, self.P, self.m, self.v, self.g, self.n_params, self.lr, self.betas[0],
