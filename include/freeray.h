@@ -225,6 +225,35 @@ fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32
  * Returns FR_ERR_TIMEOUT if the work has not finished by then. */
 fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms);
 
+/* Forward trace that allocates nothing (the paper has no counterpart; this is
+ * an interface for callers that cannot allocate device memory: code running in
+ * a host process whose device memory is owned by another allocator or budget,
+ * real-time loops that cannot afford cudaMalloc's implicit synchronisation,
+ * and plug-ins that may only use the buffers they are handed).
+ * Same arguments and results as fr_trace_forward, without a handle: the
+ * caller passes the lens, source, screen and the output E_out (and stats_out);
+ * the scratch memory this trace needs (power-form patches, basis tables and
+ * height bounds of the lens, and the int64 accumulator of deterministic mode)
+ * lives in one static device array of 1 MiB that every GPU loading the
+ * library holds until the process exits. No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *  - Limits: control nets up to 32x32 (as fr_trace_forward); in deterministic
+ *    mode the extended grid (nx+nu_x-1)*(ny+nu_y-1) may have at most 122,000
+ *    cells. Larger problems are rejected with FR_ERR_WORKSPACE and a message.
+ *  - The first call on a device, with that device current, sets it up: it looks
+ *    up the device address of the static array (cudaGetSymbolAddress) and sets
+ *    the kernels' shared-memory limit. Make that first call before any stream
+ *    capture.
+ *  - All calls share the one array and it keeps the last call's contents; the
+ *    call clears what must start at zero. Calls whose work overlaps on the GPU
+ *    (on different streams, or from different host threads) race on it:
+ *    serialise them.
+ *  - Errors are reported by the return code and fr_last_error(NULL). */
+fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_source_desc* source,
+                                  const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
+                                  uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
+                                  float* E_out, fr_stats* stats_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

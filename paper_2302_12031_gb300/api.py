@@ -99,6 +99,9 @@ _SIGNATURES = {
     "fr_trace_batch_adjoint": (C.c_int, [C.c_void_p, C.POINTER(BatchItem), C.c_int32, C.POINTER(Options),
                                          C.c_void_p]),
     "fr_stream_wait": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "fr_trace_forward_static": (C.c_int, [C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
+                                          C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -225,6 +228,15 @@ def fr_trace_batch_adjoint(h, items, options=None, stream=None):
 
 def fr_stream_wait(h, timeout_ms, stream=None):
     h.check(lib().fr_stream_wait(h.ptr, _stream(stream), timeout_ms))
+
+
+def fr_trace_forward_static(lens, source, target, n_rays, seed, ray_begin, ray_count, options, E_out,
+                            stats_out=None, stream=None):
+    """fr_trace_forward without a handle and without any allocation (see the header)."""
+    st = lib().fr_trace_forward_static(C.byref(lens), C.byref(source), C.byref(target), n_rays, seed, ray_begin,
+                                       ray_count, _opts(options), _ptr(E_out), _ptr(stats_out), _stream(stream))
+    if st != FR_OK:
+        raise FreerayError(st, lib().fr_last_error(None).decode())
 
 
 # --- descriptors from a workload dict ----------------------------------------

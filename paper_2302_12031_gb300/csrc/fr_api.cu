@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -567,3 +568,117 @@ fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fr_trace_forward_static: the forward trace with its scratch memory in one
+// static device array instead of the handle's workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = 1u << 20;
+constexpr int kStaticMaxDevices = 64;
+
+// The scratch of fr_trace_forward_static. In host code this name is only a
+// stand-in for the symbol; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;   // device address of g_static_scratch on this device
+  int sm_count = 0;
+  int smem_optin = 0;
+};
+
+std::mutex g_static_mu;
+StaticDevice g_static_dev[kStaticMaxDevices];
+
+// Once per device, with that device current.
+fr_status static_setup(StaticDevice** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kStaticMaxDevices)
+    return set_error(nullptr, FR_ERR_UNSUPPORTED, "device ordinal %d beyond %d", dev, kStaticMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDevice& d = g_static_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaGetSymbolAddress(static scratch)");
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = fr::configure_forward(d.smem_optin);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "static trace set-up");
+    d.scratch = static_cast<unsigned char*>(p);
+    d.ready = true;
+  }
+  *out = &d;
+  return FR_OK;
+}
+
+}  // namespace
+
+extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_source_desc* source,
+                                             const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
+                                             uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
+                                             float* E_out, fr_stats* stats_out, void* stream) {
+  const fr_options o = defaults(options);
+  if (!E_out) return set_error(nullptr, FR_ERR_INVALID_ARG, "E_out is null");
+  Item it;
+  fr_status s = make_item(nullptr, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
+  if (s != FR_OK) return s;
+  StaticDevice* dev = nullptr;
+  s = static_setup(&dev);
+  if (s != FR_OK) return s;
+  const bool det = o.deterministic != 0;
+  if (det && it.ncol * it.nrow > 122000)
+    return set_error(nullptr, FR_ERR_WORKSPACE,
+                     "deterministic mode: the extended grid has %d cells, the static scratch holds at most 122000",
+                     it.ncol * it.nrow);
+  const ItemWs w = plan(it, 0, det, false);
+  if (w.end > kStaticScratchBytes)
+    return set_error(nullptr, FR_ERR_WORKSPACE,
+                     "the problem needs %zu bytes of scratch, more than the %zu of the static array (in "
+                     "deterministic mode the extended grid may have at most 122000 cells; it has %d)",
+                     w.end, kStaticScratchBytes, it.ncol * it.nrow);
+  cudaStream_t st = as_stream(stream);
+  unsigned char* base = dev->scratch;
+  it.patch = reinterpret_cast<float4*>(base + w.patch);
+  it.basis_u = reinterpret_cast<float4*>(base + w.basis_u);
+  it.basis_v = reinterpret_cast<float4*>(base + w.basis_v);
+  it.zb = reinterpret_cast<float*>(base + w.zb);
+  it.Efix = reinterpret_cast<unsigned long long*>(base + w.efix);
+  it.E = E_out;
+  it.stats = stats_out;
+  const int warps = pick_warps(o);
+  schedule_item(&it, warps, o);
+  it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
+  const size_t smem = fr::fwd_smem_bytes(it, det);
+  cudaError_t e = fr::launch_prep(&it, 1, st);
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "prep kernel");
+  if (det) e = cudaMemsetAsync(it.Efix, 0, (size_t)it.ncol * it.nrow * 8, st);
+  else if (!o.accumulate) e = cudaMemsetAsync(it.E, 0, (size_t)it.ncol * it.nrow * 4, st);
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaMemsetAsync");
+  if (it.tiles > 0) {
+    const int occ = fr::forward_occupancy(warps * 32, smem, det, false);
+    if (occ <= 0 || smem + 1024 > (size_t)dev->smem_optin)
+      return set_error(nullptr, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
+    const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
+    it.cta_begin = 0;
+    it.cta_end = std::min(std::max(1, dev->sm_count * per_sm), it.tiles);
+    fr::Launch<1> L;
+    std::memset(&L, 0, sizeof L);
+    L.n_items = 1;
+    L.warps = warps;
+    L.items[0] = it;
+    e = fr::launch_forward<1>(L, it.cta_end, smem, det, st);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "forward kernel");
+  }
+  if (det) {
+    e = fr::launch_fix_to_float(it.Efix, it.E, (size_t)it.ncol * it.nrow, 1.0f / it.fixE, o.accumulate, st);
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "fixed-point conversion");
+  }
+  return FR_OK;
+}
+
