@@ -215,7 +215,8 @@ fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* 
 
 /* Batched forward / adjoint: every item (its own lens, source, screen, rays and
  * buffers) in one launch of the trace kernel. Same semantics per item as
- * fr_trace_forward / fr_trace_adjoint over all rays of the item. n_items <= 64. */
+ * fr_trace_forward / fr_trace_adjoint over all rays of the item. n_items <= 64;
+ * the items must share the filter size (FR_ERR_UNSUPPORTED otherwise). */
 fr_status fr_trace_batch_forward(fr_handle* h, const fr_batch_item* items, int32_t n_items,
                                  const fr_options* options, void* stream);
 fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32_t n_items,
@@ -232,9 +233,8 @@ fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms);
  * and plug-ins that may only use the buffers they are handed).
  * Same arguments and results as fr_trace_forward, without a handle: the
  * caller passes the lens, source, screen and the output E_out (and stats_out);
- * the scratch memory this trace needs (power-form patches, basis tables and
- * height bounds of the lens, and the int64 accumulator of deterministic mode)
- * lives in one static device array of 1 MiB that every GPU loading the
+ * the scratch memory this trace needs (the int64 accumulator of deterministic
+ * mode) lives in one static device array of 1 MiB that every GPU loading the
  * library holds until the process exits. No cudaMalloc, cudaFree or other
  * allocating call is made.
  *  - Limits: control nets up to 32x32 (as fr_trace_forward); in deterministic

@@ -7,18 +7,14 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <thread>
 #include <vector>
 
 #include "fr_internal.h"
-
-namespace fr {
-cudaError_t configure_forward(int optin);
-cudaError_t configure_adjoint(int optin);
-cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);
-}  // namespace fr
 
 struct fr_handle {
   int device = 0;
@@ -27,6 +23,8 @@ struct fr_handle {
   unsigned char* ws = nullptr;   // scratch memory owned by the handle
   size_t ws_bytes = 0;
   std::string err;
+  // CTAs per SM of a trace kernel, by (adjoint, det, batch, nu, kinds, threads, smem).
+  std::map<std::tuple<int, int, int, int, int, int, size_t>, int> occupancy;
 };
 
 namespace {
@@ -72,21 +70,14 @@ fr_options defaults(const fr_options* o) {
   return d;
 }
 
-// Per-item offsets into the workspace.
+// Per-item offsets into the workspace: the int64 accumulators of deterministic
+// mode and max |dL/dE|.
 struct ItemWs {
-  size_t patch, basis_u, basis_v, zb, efix, pfix, gmax, end;
+  size_t efix, pfix, gmax, end;
 };
 
 ItemWs plan(const Item& it, size_t at, bool det_fwd, bool det_adj) {
   ItemWs w;
-  w.patch = at;
-  at = align_up(at + (size_t)it.nsu * it.nsv * 4 * sizeof(float4));
-  w.basis_u = at;
-  at = align_up(at + (size_t)it.nsu * 4 * sizeof(float4));
-  w.basis_v = at;
-  at = align_up(at + (size_t)it.nsv * 4 * sizeof(float4));
-  w.zb = at;
-  at = align_up(at + 2 * sizeof(float));
   w.efix = at;
   if (det_fwd) at = align_up(at + (size_t)it.ncol * it.nrow * sizeof(unsigned long long));
   w.pfix = at;
@@ -212,6 +203,8 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   it->inv_wy = (float)(1.0 / wy);
   it->Rsx = (float)(T->Rx + 0.5 * (T->nu_x - 1) * wx);
   it->Rsy = (float)(T->Ry + 0.5 * (T->nu_y - 1) * wy);
+  it->gx_off = (float)((T->Rx + 0.5 * (T->nu_x - 1) * wx) / wx);
+  it->gy_off = (float)((T->Ry + 0.5 * (T->nu_y - 1) * wy) / wy);
   it->ax = (float)(T->alpha * 1.4426950408889634);
   it->ay = it->ax;
   it->cut = (float)std::exp(-(double)T->alpha * 0.25 * T->nu_x * T->nu_x);
@@ -230,39 +223,27 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
 }
 
 
-// Tiles of an item for a CTA of `warps` warps.
+// The most CTAs worth launching for an item: every lane should trace at least
+// `rays_per_lane` rays (options; by default 8 collimated, 4 point-source).
 void schedule_item(Item* it, int warps, const fr_options& o) {
   const uint64_t count = it->ray_end - it->ray_begin;
-  if (it->kind == FR_SOURCE_COLLIMATED) {
-    int R = o.rays_per_lane > 0 ? o.rays_per_lane : std::min(16, std::max(1, (it->cols + 31) / 32));
-    R = std::min(R, 64);
-    it->rays_per_lane = R;
-    if (count == 0) {
-      it->row_lo = it->row_hi = 0;
-      it->segs = 1;
-      it->tiles = 0;
-      return;
-    }
-    it->row_lo = (int)(it->ray_begin / (uint64_t)it->cols);
-    it->row_hi = (int)((it->ray_end - 1) / (uint64_t)it->cols) + 1;
-    const int groups = (it->row_hi - it->row_lo + warps - 1) / warps;
-    it->segs = (it->cols + 32 * R - 1) / (32 * R);
-    it->tiles = groups * it->segs;
-  } else {
-    int R = o.rays_per_lane > 0 ? o.rays_per_lane : 4;
-    R = std::min(R, 64);
-    it->rays_per_lane = R;
-    const uint64_t per_tile = (uint64_t)warps * 32 * (uint64_t)R;
-    it->tiles = (int)((count + per_tile - 1) / per_tile);
-  }
+  const int rpl = o.rays_per_lane > 0 ? std::min(o.rays_per_lane, 64)
+                                      : (it->kind == FR_SOURCE_COLLIMATED ? 8 : 4);
+  const uint64_t per_cta = (uint64_t)warps * 32 * (uint64_t)rpl;
+  it->max_ctas = (int)std::min<uint64_t>((count + per_cta - 1) / per_cta, 1 << 20);
 }
 
-int pick_warps(const fr_options& o) { return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 8) : 8; }
+// Warps per CTA: 12 for the collimated forward kernel (whose launch bounds
+// allow 384 threads: two such CTAs share an SM with their histograms), 8 else.
+int pick_warps(const fr_options& o, bool adjoint, int kind) {
+  const int cap = (!adjoint && kind == FR_SOURCE_COLLIMATED) ? 12 : 8;
+  return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, cap) : cap;
+}
 
 bool want_smem_hist(const Item& it, const fr_options& o, bool det) {
   const size_t hist = (size_t)it.ncol * it.nrow * (det ? 8 : 4);
-  const size_t patches = (size_t)it.nsu * it.nsv * 4 * sizeof(float4);
-  if (hist + patches > 200 * 1024) return false;
+  const size_t tables = (size_t)(it.nsu * it.nsv + it.nsu + it.nsv) * 4 * sizeof(float4);
+  if (hist + tables > 200 * 1024) return false;
   if (o.hist_mode == 1) return false;
   if (o.hist_mode == 2) return true;
   return hist <= 100 * 1024;
@@ -279,9 +260,9 @@ void assign_ctas(std::vector<Item>& items, int total_ctas) {
   }
   int at = 0;
   for (size_t i = 0; i < items.size(); ++i) {
-    int g = items[i].tiles == 0 ? 0
+    int g = items[i].max_ctas == 0 ? 0
             : std::max(1, (int)std::lround(cost_sum > 0 ? total_ctas * cost[i] / cost_sum : 1.0));
-    g = std::min(g, items[i].tiles);
+    g = std::min(g, items[i].max_ctas);
     items[i].cta_begin = at;
     items[i].cta_end = at + g;
     at += g;
@@ -295,7 +276,7 @@ template <int CAP>
 fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o, bool adjoint,
                     cudaStream_t st) {
   const bool det = o.deterministic != 0;
-  const int warps = pick_warps(o);
+  const int warps = pick_warps(o, adjoint, items.size() == 1 ? items[0].kind : FR_SOURCE_POINT);
   // Workspace.
   size_t at = kHeaderBytes;
   std::vector<ItemWs> ws(items.size());
@@ -308,21 +289,12 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   size_t smem = 0;
   for (size_t i = 0; i < items.size(); ++i) {
     Item& it = items[i];
-    it.patch = reinterpret_cast<float4*>(h->ws + ws[i].patch);
-    it.basis_u = reinterpret_cast<float4*>(h->ws + ws[i].basis_u);
-    it.basis_v = reinterpret_cast<float4*>(h->ws + ws[i].basis_v);
-    it.zb = reinterpret_cast<float*>(h->ws + ws[i].zb);
     it.Efix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].efix);
     it.Pfix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].pfix);
     it.gmax = reinterpret_cast<float*>(h->ws + ws[i].gmax);
     schedule_item(&it, warps, o);
     if (!adjoint) it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
     smem = std::max(smem, adjoint ? fr::adj_smem_bytes(it, det) : fr::fwd_smem_bytes(it, det));
-  }
-  // Prep: power-form patches, basis tables and bounds of every lens.
-  {
-    cudaError_t e = fr::launch_prep(items.data(), (int)items.size(), st);
-    if (e != cudaSuccess) return cuda_error(h, e, "prep kernel");
   }
   // Outputs.
   for (size_t i = 0; i < items.size(); ++i) {
@@ -343,18 +315,31 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   // Trace.
   const int threads = warps * 32;
   const bool batch = CAP > 1;
-  const int occ = adjoint ? fr::adjoint_occupancy(threads, smem, det, batch)
-                          : fr::forward_occupancy(threads, smem, det, batch);
+  // A batch runs in one launch: its items must share the filter size.
+  for (auto& it : items)
+    if (it.nu != items[0].nu)
+      return set_error(h, FR_ERR_UNSUPPORTED, "the items of a batch must have the same filter size");
+  const int kinds = items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2;
+  const auto key = std::make_tuple((int)adjoint, (int)det, (int)batch, items[0].nu, kinds, threads, smem);
+  auto found = h->occupancy.find(key);
+  int occ;
+  if (found != h->occupancy.end()) {
+    occ = found->second;
+  } else {
+    occ = adjoint ? fr::adjoint_occupancy(threads, smem, det, batch, items[0].nu, kinds)
+                  : fr::forward_occupancy(threads, smem, det, batch, items[0].nu, kinds);
+    h->occupancy[key] = occ;
+  }
   if (occ <= 0 || smem + 1024 > (size_t)h->smem_optin)
     return set_error(h, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
   const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
-  int total_tiles = 0;
-  for (auto& it : items) total_tiles += it.tiles;
-  if (total_tiles > 0) {
+  int total_ctas = 0;
+  for (auto& it : items) total_ctas += it.max_ctas;
+  if (total_ctas > 0) {
     const int want = std::max<int>(1, h->sm_count * per_sm);
     if (items.size() == 1) {
       items[0].cta_begin = 0;
-      items[0].cta_end = std::min(want, items[0].tiles);
+      items[0].cta_end = std::min(want, items[0].max_ctas);
     } else {
       assign_ctas(items, std::max<int>(want, (int)items.size()));
     }
@@ -475,16 +460,7 @@ fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source
   Item it;
   fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
   if (s != FR_OK) return s;
-  const ItemWs w = plan(it, kHeaderBytes, false, false);
-  s = ensure_workspace(h, w.end, as_stream(stream));
-  if (s != FR_OK) return s;
-  it.patch = reinterpret_cast<float4*>(h->ws + w.patch);
-  it.basis_u = reinterpret_cast<float4*>(h->ws + w.basis_u);
-  it.basis_v = reinterpret_cast<float4*>(h->ws + w.basis_v);
-  it.zb = reinterpret_cast<float*>(h->ws + w.zb);
-  cudaError_t e = fr::launch_prep(&it, 1, as_stream(stream));
-  if (e != cudaSuccess) return cuda_error(h, e, "prep kernel");
-  e = fr::launch_debug(it, out, as_stream(stream));
+  cudaError_t e = fr::launch_debug(it, out, as_stream(stream));
   if (e != cudaSuccess) return cuda_error(h, e, "debug kernel");
   return FR_OK;
 }
@@ -644,29 +620,25 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
                      w.end, kStaticScratchBytes, it.ncol * it.nrow);
   cudaStream_t st = as_stream(stream);
   unsigned char* base = dev->scratch;
-  it.patch = reinterpret_cast<float4*>(base + w.patch);
-  it.basis_u = reinterpret_cast<float4*>(base + w.basis_u);
-  it.basis_v = reinterpret_cast<float4*>(base + w.basis_v);
-  it.zb = reinterpret_cast<float*>(base + w.zb);
   it.Efix = reinterpret_cast<unsigned long long*>(base + w.efix);
   it.E = E_out;
   it.stats = stats_out;
-  const int warps = pick_warps(o);
+  const int warps = pick_warps(o, false, it.kind);
   schedule_item(&it, warps, o);
   it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
   const size_t smem = fr::fwd_smem_bytes(it, det);
-  cudaError_t e = fr::launch_prep(&it, 1, st);
-  if (e != cudaSuccess) return cuda_error(nullptr, e, "prep kernel");
+  cudaError_t e = cudaSuccess;
   if (det) e = cudaMemsetAsync(it.Efix, 0, (size_t)it.ncol * it.nrow * 8, st);
   else if (!o.accumulate) e = cudaMemsetAsync(it.E, 0, (size_t)it.ncol * it.nrow * 4, st);
   if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaMemsetAsync");
-  if (it.tiles > 0) {
-    const int occ = fr::forward_occupancy(warps * 32, smem, det, false);
+  if (it.max_ctas > 0) {
+    const int occ = fr::forward_occupancy(warps * 32, smem, det, false, it.nu,
+                                          it.kind == FR_SOURCE_COLLIMATED ? 1 : 2);
     if (occ <= 0 || smem + 1024 > (size_t)dev->smem_optin)
       return set_error(nullptr, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
     const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
     it.cta_begin = 0;
-    it.cta_end = std::min(std::max(1, dev->sm_count * per_sm), it.tiles);
+    it.cta_end = std::min(std::max(1, dev->sm_count * per_sm), it.max_ctas);
     fr::Launch<1> L;
     std::memset(&L, 0, sizeof L);
     L.n_items = 1;

@@ -1,6 +1,7 @@
-// Device functions of the freeform-lens trace: counter-based ray generation,
-// B-spline patch evaluation, refraction, propagation, the reconstruction filter
-// and the reverse-mode derivatives of all of them.
+// Device functions of the freeform-lens trace: the lens tables each CTA builds
+// in shared memory, counter-based ray generation, B-spline patch evaluation,
+// refraction, propagation, the reconstruction filter and the reverse-mode
+// derivatives of all of them.
 #pragma once
 
 #include <cstdint>
@@ -38,16 +39,161 @@ __device__ __forceinline__ float unit23(uint32_t w) {
   return fmaf((float)(w >> 9), 1.0f / 8388608.0f, 0.5f / 8388608.0f);
 }
 
+// PTX approximate instructions (single MUFU operations): 2^x with a relative
+// error below 2^-22, 1/x within 1 ulp. Both flush denormals to zero.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float fast_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // ---------------------------------------------------------------------------
-// Sec. 2.1: the bicubic B-spline height field as power-form patches. On span
-// product (k, l) with local coordinates s, t in [0,1],
-//   Z(s,t) = sum_{e,f} C[e][f] s^e t^f,
-// where C is the prep kernel's exact re-expression of sum N_i N_j P^z_ij.
+// Sec. 2.1: the bicubic B-spline in power form. On knot span k of a clamped
+// uniform knot vector with nspan spans, the four non-zero basis functions
+// N_{k..k+3,3} are cubics in the local coordinate s = u*nspan - k; the
+// Cox-de Boor recursion run on polynomials in s gives their coefficients. The
+// knots are handled in units of the span width, where they are the integers
+// K(j) = clamp(j-3, 0, nspan), so every ratio in the recursion is a ratio of
+// small integers.
 // ---------------------------------------------------------------------------
-struct Patch {
-  int k, l;
-  float4 c0, c1, c2, c3;   // c_e = (C[e][0], C[e][1], C[e][2], C[e][3])
+__device__ __forceinline__ int knot_units(int j, int nspan) { return min(max(j - 3, 0), nspan); }
+
+__device__ inline void span_basis(int k, int nspan, float4 out[4]) {
+  const int i = k + 3;  // knot index of the span's left end
+  float poly[5][4];
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) poly[a][e] = 0.0f;
+  poly[3][0] = 1.0f;    // N_{i,0} = 1 on its own span
+  const int Ki = knot_units(i, nspan);
+#pragma unroll
+  for (int d = 1; d <= 3; ++d) {
+    float next[5][4];
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) next[a][e] = 0.0f;
+#pragma unroll
+    for (int jj = 3 - d; jj <= 3; ++jj) {
+      const int j = i - 3 + jj;
+      // The denominators are knot differences of at most d <= 3 spans.
+      const int den1 = knot_units(j + d, nspan) - knot_units(j, nspan);
+      const int den2 = knot_units(j + d + 1, nspan) - knot_units(j + 1, nspan);
+      const float r1 = den1 == 1 ? 1.0f : (den1 == 2 ? 0.5f : (den1 == 3 ? (1.0f / 3.0f) : 0.0f));
+      const float r2 = den2 == 1 ? 1.0f : (den2 == 2 ? 0.5f : (den2 == 3 ? (1.0f / 3.0f) : 0.0f));
+      // (u - u_j)/(u_{j+d} - u_j) = (Ki - K(j) + s)/den1
+      const float a0 = (float)(Ki - knot_units(j, nspan)) * r1;
+      const float a1 = r1;
+      // (u_{j+d+1} - u)/(u_{j+d+1} - u_{j+1}) = (K(j+d+1) - Ki - s)/den2
+      const float b0 = (float)(knot_units(j + d + 1, nspan) - Ki) * r2;
+      const float b1 = -r2;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float c = a0 * poly[jj][e] + b0 * poly[jj + 1][e];
+        if (e > 0) c += a1 * poly[jj][e - 1] + b1 * poly[jj + 1][e - 1];
+        next[jj][e] = c;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) poly[a][e] = next[a][e];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) out[a] = make_float4(poly[a][0], poly[a][1], poly[a][2], poly[a][3]);
+}
+
+// Tables of one lens in shared memory.
+struct LensSmem {
+  float4* patch;   // [nsu*nsv][4]: row e holds C[e][0..3] of Z = sum_{e,f} C[e][f] s^e t^f
+  float4* bu;      // [nsu][4]: coefficients of N_{k+a}(s) in powers of s
+  float4* bv;      // [nsv][4]
+  float* zb;       // [2]: min and max control height (convex hull, Sec. 2.1.2)
 };
+
+__host__ __device__ inline size_t lens_smem_bytes(int nsu, int nsv) {
+  return (size_t)(nsu * nsv + nsu + nsv) * 4 * sizeof(float4) + 16;
+}
+
+__device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv) {
+  LensSmem s;
+  s.patch = reinterpret_cast<float4*>(base);
+  s.bu = s.patch + nsu * nsv * 4;
+  s.bv = s.bu + nsu * 4;
+  s.zb = reinterpret_cast<float*>(s.bv + nsv * 4);
+  return s;
+}
+
+// Every thread of the CTA takes part; ends with __syncthreads.
+//   Z(s,t) = sum_{a,b} N_{k+a}(s) N_{l+b}(t) P^z_{k+a,l+b} = sum_{e,f} C[e][f] s^e t^f,
+//   C[e][f] = sum_a sum_b Bu[a][e] Bv[b][f] P^z_{k+a,l+b}.
+__device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
+  for (int q = threadIdx.x; q < it.nsu + it.nsv; q += blockDim.x) {
+    const bool isu = q < it.nsu;
+    const int k = isu ? q : q - it.nsu;
+    float4 B[4];
+    span_basis(k, isu ? it.nsu : it.nsv, B);
+    float4* dst = (isu ? s.bu : s.bv) + k * 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) dst[a] = B[a];
+  }
+  if (threadIdx.x < 32) {
+    float zmn = INFINITY, zmx = -INFINITY;
+    for (int q = threadIdx.x; q < it.ncu * it.ncv; q += 32) {
+      const float z = __ldg(it.ctrl + q);
+      zmn = fminf(zmn, z);
+      zmx = fmaxf(zmx, z);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      zmn = fminf(zmn, __shfl_xor_sync(0xffffffffu, zmn, o));
+      zmx = fmaxf(zmx, __shfl_xor_sync(0xffffffffu, zmx, o));
+    }
+    if (threadIdx.x == 0) {
+      s.zb[0] = zmn;
+      s.zb[1] = zmx;
+    }
+  }
+  __syncthreads();
+  const int npatch = it.nsu * it.nsv;
+  for (int p = threadIdx.x; p < npatch; p += blockDim.x) {
+    const int k = p / it.nsv, l = p - k * it.nsv;
+    float T[4][4];   // T[a][f] = sum_b P[k+a][l+b] Bv_l[b][f]
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float P = __ldg(it.ctrl + (k + a) * it.ncv + (l + b));
+        const float4 q = s.bv[l * 4 + b];
+        c0 = fmaf(P, q.x, c0);
+        c1 = fmaf(P, q.y, c1);
+        c2 = fmaf(P, q.z, c2);
+        c3 = fmaf(P, q.w, c3);
+      }
+      T[a][0] = c0; T[a][1] = c1; T[a][2] = c2; T[a][3] = c3;
+    }
+    const float4 u0 = s.bu[k * 4 + 0], u1 = s.bu[k * 4 + 1], u2 = s.bu[k * 4 + 2], u3 = s.bu[k * 4 + 3];
+    const float ue[4][4] = {{u0.x, u1.x, u2.x, u3.x}, {u0.y, u1.y, u2.y, u3.y},
+                            {u0.z, u1.z, u2.z, u3.z}, {u0.w, u1.w, u2.w, u3.w}};  // ue[e][a]
+    float4* out = s.patch + (size_t)p * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float c[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+        c[f] = fmaf(ue[e][0], T[0][f], fmaf(ue[e][1], T[1][f], fmaf(ue[e][2], T[2][f], ue[e][3] * T[3][f])));
+      out[e] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+  }
+  __syncthreads();
+}
 
 __device__ __forceinline__ void locate(float u, int ns, int* k, float* s) {
   const float us = fminf(fmaxf(u, 0.0f), 1.0f) * (float)ns;
@@ -56,19 +202,7 @@ __device__ __forceinline__ void locate(float u, int ns, int* k, float* s) {
   *s = us - (float)kk;
 }
 
-__device__ __forceinline__ void fetch_patch(const float4* sp, int nsv, int k, int l, Patch* p) {
-  if (k != p->k || l != p->l) {
-    const float4* q = sp + (size_t)(k * nsv + l) * 4;
-    p->c0 = q[0];
-    p->c1 = q[1];
-    p->c2 = q[2];
-    p->c3 = q[3];
-    p->k = k;
-    p->l = l;
-  }
-}
-
-// One cubic in t and its derivative (Horner with synthetic division).
+// One cubic c.x + c.y t + c.z t^2 + c.w t^3 and its derivative.
 __device__ __forceinline__ void cubic_d(const float4 c, float t, float* v, float* dv) {
   const float a = fmaf(t, c.w, c.z);
   const float b = fmaf(t, a, c.y);
@@ -77,13 +211,13 @@ __device__ __forceinline__ void cubic_d(const float4 c, float t, float* v, float
   *dv = fmaf(t, db, b);
 }
 
-// Z, dZ/ds, dZ/dt.
-__device__ __forceinline__ void patch_eval(const Patch& p, float s, float t, float* Z, float* Zs, float* Zt) {
+// Z, dZ/ds, dZ/dt of patch q at (s, t).
+__device__ __forceinline__ void patch_eval(const float4* q, float s, float t, float* Z, float* Zs, float* Zt) {
   float r0, r1, r2, r3, d0, d1, d2, d3;
-  cubic_d(p.c0, t, &r0, &d0);
-  cubic_d(p.c1, t, &r1, &d1);
-  cubic_d(p.c2, t, &r2, &d2);
-  cubic_d(p.c3, t, &r3, &d3);
+  cubic_d(q[0], t, &r0, &d0);
+  cubic_d(q[1], t, &r1, &d1);
+  cubic_d(q[2], t, &r2, &d2);
+  cubic_d(q[3], t, &r3, &d3);
   const float a = fmaf(s, r3, r2);
   const float b = fmaf(s, a, r1);
   const float db = fmaf(s, r3, a);
@@ -92,38 +226,37 @@ __device__ __forceinline__ void patch_eval(const Patch& p, float s, float t, flo
   *Zt = fmaf(s, fmaf(s, fmaf(s, d3, d2), d1), d0);
 }
 
-// Second derivatives d2Z/ds2, d2Z/dsdt, d2Z/dt2.
-__device__ __forceinline__ void patch_eval2(const Patch& p, float s, float t, float* Zss, float* Zst, float* Ztt) {
+// d2Z/ds2, d2Z/dsdt, d2Z/dt2 of patch q at (s, t).
+__device__ __forceinline__ void patch_eval2(const float4* q, float s, float t, float* Zss, float* Zst, float* Ztt) {
   float r2, r3, d1, d2, d3, tmp;
-  cubic_d(p.c1, t, &tmp, &d1);
-  cubic_d(p.c2, t, &r2, &d2);
-  cubic_d(p.c3, t, &r3, &d3);
+  cubic_d(q[1], t, &tmp, &d1);
+  cubic_d(q[2], t, &r2, &d2);
+  cubic_d(q[3], t, &r3, &d3);
   *Zss = fmaf(6.0f * s, r3, 2.0f * r2);
   *Zst = fmaf(s, fmaf(3.0f * s, d3, 2.0f * d2), d1);
-  // d2/dt2 of each row cubic: 2 c_e2 + 6 c_e3 t
-  const float e0 = fmaf(6.0f * t, p.c0.w, 2.0f * p.c0.z);
-  const float e1 = fmaf(6.0f * t, p.c1.w, 2.0f * p.c1.z);
-  const float e2 = fmaf(6.0f * t, p.c2.w, 2.0f * p.c2.z);
-  const float e3 = fmaf(6.0f * t, p.c3.w, 2.0f * p.c3.z);
+  const float4 c0 = q[0], c1 = q[1], c2 = q[2], c3 = q[3];
+  const float e0 = fmaf(6.0f * t, c0.w, 2.0f * c0.z);
+  const float e1 = fmaf(6.0f * t, c1.w, 2.0f * c1.z);
+  const float e2 = fmaf(6.0f * t, c2.w, 2.0f * c2.z);
+  const float e3 = fmaf(6.0f * t, c3.w, 2.0f * c3.z);
   *Ztt = fmaf(s, fmaf(s, fmaf(s, e3, e2), e1), e0);
 }
 
-// The four non-zero basis functions N_{k+a}(s) of a span and dN/ds from the
-// prep kernel's power-form table.
+// The four non-zero basis functions of a span and their s-derivatives.
 __device__ __forceinline__ void basis_eval(const float4* tab, float s, float N[4], float dN[4]) {
 #pragma unroll
   for (int a = 0; a < 4; ++a) cubic_d(tab[a], s, &N[a], &dN[a]);
 }
 
 // ---------------------------------------------------------------------------
-// One ray up to the screen (Secs. 2.2-2.3). Everything the adjoint needs is
-// kept, so that forward and adjoint run the same code.
+// One ray up to the screen (Secs. 2.2-2.3); forward and adjoint run this code.
 // ---------------------------------------------------------------------------
 struct RayFwd {
   int status;
   int iters;
+  int k, l;             // patch (knot span product) of the hit
   float u, v;           // hit in the B-spline parameter domain
-  float s, t;           // patch coordinates of the hit (patch in the Patch cache)
+  float s, t;           // patch coordinates of the hit
   float x, y, z;        // hit on the freeform
   float dx, dy, dz;     // direction inside the glass
   float Zs, Zt;         // surface derivatives in patch coordinates at the hit
@@ -138,41 +271,74 @@ struct RayFwd {
 };
 
 // Exit face: normal, Snell glass -> air, TIR, Schlick, propagation (a5, a6).
+// COLL: the ray travels along (0,0,1) inside the glass.
+template <bool COLL>
 __device__ __forceinline__ void exit_and_propagate(const Item& it, RayFwd& r) {
   const float Zx = r.Zs * it.ku, Zy = r.Zt * it.kv;
-  const float invL = rsqrtf(fmaf(Zx, Zx, fmaf(Zy, Zy, 1.0f)));
+  const float q2 = fmaf(Zx, Zx, Zy * Zy);
+  const float invL = rsqrtf(1.0f + q2);
   r.invL = invL;
   r.nx = -Zx * invL;
   r.ny = -Zy * invL;
   r.nz = invL;
   const float eta = it.n_glass;
-  const float c = fmaf(r.dx, r.nx, fmaf(r.dy, r.ny, r.dz * r.nz));
+  float c, sin2;
+  if (COLL) {
+    c = invL;
+    sin2 = q2 * invL * invL;            // 1 - c^2 without cancellation
+  } else {
+    c = fmaf(r.dx, r.nx, fmaf(r.dy, r.ny, r.dz * r.nz));
+    sin2 = fmaf(-c, c, 1.0f);
+  }
   r.c = c;
-  const float k = fmaf(-eta * eta, fmaf(-c, c, 1.0f), 1.0f);
-  if (!(k >= 0.0f)) { r.status = FR_RAY_TIR; return; }
-  const float cs = sqrtf(k);
+  const float k = fmaf(-eta * eta, sin2, 1.0f);
+  if (!(k > 0.0f)) { r.status = FR_RAY_TIR; return; }
+  const float cs = k * rsqrtf(k);
   r.cs = cs;
   const float a = fmaf(eta, c, -cs);
   r.a = a;
-  r.tx = fmaf(eta, r.dx, -a * r.nx);
-  r.ty = fmaf(eta, r.dy, -a * r.ny);
-  r.tz = fmaf(eta, r.dz, -a * r.nz);
+  if (COLL) {
+    r.tx = -a * r.nx;
+    r.ty = -a * r.ny;
+    r.tz = fmaf(-a, r.nz, eta);
+  } else {
+    r.tx = fmaf(eta, r.dx, -a * r.nx);
+    r.ty = fmaf(eta, r.dy, -a * r.ny);
+    r.tz = fmaf(eta, r.dz, -a * r.nz);
+  }
   const float om = 1.0f - cs;
   const float om2 = om * om;
   r.T2 = (1.0f - it.R0) * fmaf(-om2 * om2, om, 1.0f);
   r.w = it.omega0 * r.T1 * r.T2;
   if (!(r.tz > 0.0f)) { r.status = FR_RAY_OFF_SCREEN; return; }
-  const float lam = __fdividef(it.z_screen - r.z, r.tz);
+  const float lam = (it.z_screen - r.z) * fast_rcp(r.tz);
   r.lam = lam;
   r.X = fmaf(lam, r.tx, r.x);
   r.Y = fmaf(lam, r.ty, r.y);
-  if (!(fabsf(r.X) < it.Rx && fabsf(r.Y) < it.Ry)) { r.status = FR_RAY_OFF_SCREEN; return; }
-  r.status = FR_RAY_ON_SCREEN;
+  r.status = (fabsf(r.X) < it.Rx && fabsf(r.Y) < it.Ry) ? FR_RAY_ON_SCREEN : FR_RAY_OFF_SCREEN;
 }
 
-// Collimated ray (a1, a3-a6): (u,v) on the square grid, d = (0,0,1), starting
-// on the freeform.
-__device__ __forceinline__ void trace_collimated(const Item& it, const float4* sp, Patch& pc, int row, int col,
+// Collimated ray through the freeform at (u, v) = ((x/rx+1)/2, (y/ry+1)/2)
+// given Z and its slopes.
+__device__ __forceinline__ void collimated_at(const Item& it, float u, float v, float y, float Z, float Zs,
+                                              float Zt, RayFwd& r) {
+  r.u = u;
+  r.v = v;
+  r.x = fmaf(2.0f, u, -1.0f) * it.rx;
+  r.y = y;
+  r.z = Z;
+  r.Zs = Zs;
+  r.Zt = Zt;
+  r.dx = 0.0f;
+  r.dy = 0.0f;
+  r.dz = 1.0f;
+  r.T1 = 1.0f - it.R0;   // normal incidence on the flat entry face
+  r.iters = 0;
+  exit_and_propagate<true>(it, r);
+}
+
+// Collimated ray (a1, a3-a6) on the square grid, any patch (jittered rays).
+__device__ __forceinline__ void trace_collimated(const Item& it, const LensSmem& ls, uint32_t row, uint32_t col,
                                                  uint64_t id, float inv_cols, float inv_rows, RayFwd& r) {
   float ja = 0.5f, jb = 0.5f;
   if (it.jitter) {
@@ -182,34 +348,66 @@ __device__ __forceinline__ void trace_collimated(const Item& it, const float4* s
   }
   const float u = ((float)col + ja) * inv_cols;
   const float v = ((float)row + jb) * inv_rows;
-  r.u = u;
-  r.v = v;
-  r.x = fmaf(2.0f, u, -1.0f) * it.rx;
-  r.y = fmaf(2.0f, v, -1.0f) * it.ry;
+  locate(u, it.nsu, &r.k, &r.s);
+  locate(v, it.nsv, &r.l, &r.t);
+  float Z, Zs, Zt;
+  patch_eval(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Z, &Zs, &Zt);
+  collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zs, Zt, r);
+}
+
+// Along one grid row t is fixed: the row cubics of the current patch,
+// r_e(t) = sum_f C[e][f] t^f and their t-derivatives, serve every ray of the
+// row that falls in that patch.
+struct RowPatch {
+  uint32_t row;
   int k, l;
+  float v, t, y;
+  float r0, r1, r2, r3, d0, d1, d2, d3;
+};
+
+__device__ __forceinline__ void row_patch_load(const Item& it, const LensSmem& ls, int k, RowPatch& rp) {
+  const float4* q = ls.patch + (size_t)(k * it.nsv + rp.l) * 4;
+  cubic_d(q[0], rp.t, &rp.r0, &rp.d0);
+  cubic_d(q[1], rp.t, &rp.r1, &rp.d1);
+  cubic_d(q[2], rp.t, &rp.r2, &rp.d2);
+  cubic_d(q[3], rp.t, &rp.r3, &rp.d3);
+  rp.k = k;
+}
+
+// Collimated ray at a cell centre, with the row cache.
+__device__ __forceinline__ void trace_collimated_row(const Item& it, const LensSmem& ls, uint32_t row, uint32_t col,
+                                                     float inv_cols, float inv_rows, RowPatch& rp, RayFwd& r) {
+  if (row != rp.row) {
+    rp.row = row;
+    rp.v = ((float)row + 0.5f) * inv_rows;
+    rp.y = fmaf(2.0f, rp.v, -1.0f) * it.ry;
+    locate(rp.v, it.nsv, &rp.l, &rp.t);
+    rp.k = -1;
+  }
+  const float u = ((float)col + 0.5f) * inv_cols;
+  int k;
   locate(u, it.nsu, &k, &r.s);
-  locate(v, it.nsv, &l, &r.t);
-  fetch_patch(sp, it.nsv, k, l, &pc);
-  float Z;
-  patch_eval(pc, r.s, r.t, &Z, &r.Zs, &r.Zt);
-  r.z = Z;
-  r.dx = 0.0f;
-  r.dy = 0.0f;
-  r.dz = 1.0f;
-  r.T1 = 1.0f - it.R0;   // normal incidence on the flat entry face
-  r.iters = 0;
-  exit_and_propagate(it, r);
+  if (k != rp.k) row_patch_load(it, ls, k, rp);
+  r.k = k;
+  r.l = rp.l;
+  r.t = rp.t;
+  const float s = r.s;
+  const float a = fmaf(s, rp.r3, rp.r2);
+  const float b = fmaf(s, a, rp.r1);
+  const float db = fmaf(s, rp.r3, a);
+  const float Z = fmaf(s, b, rp.r0);
+  const float Zs = fmaf(s, db, b);
+  const float Zt = fmaf(s, fmaf(s, fmaf(s, rp.d3, rp.d2), rp.d1), rp.d0);
+  collimated_at(it, u, rp.v, rp.y, Z, Zs, Zt, r);
 }
 
 // f(t) = Z(o_uv + d_uv t) - o_z - d_z t (Eq. surfaceintersect) and df/dt.
-__device__ __forceinline__ void f_eval(const Item& it, const float4* sp, Patch& pc, float ou, float ov, float du,
-                                       float dv, float oz, float dz, float t, RayFwd& r, float* f, float* fp) {
-  int k, l;
-  locate(fmaf(du, t, ou), it.nsu, &k, &r.s);
-  locate(fmaf(dv, t, ov), it.nsv, &l, &r.t);
-  fetch_patch(sp, it.nsv, k, l, &pc);
+__device__ __forceinline__ void f_eval(const Item& it, const LensSmem& ls, float ou, float ov, float du, float dv,
+                                       float oz, float dz, float t, RayFwd& r, float* f, float* fp) {
+  locate(fmaf(du, t, ou), it.nsu, &r.k, &r.s);
+  locate(fmaf(dv, t, ov), it.nsv, &r.l, &r.t);
   float Z;
-  patch_eval(pc, r.s, r.t, &Z, &r.Zs, &r.Zt);
+  patch_eval(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Z, &r.Zs, &r.Zt);
   *f = Z - fmaf(dz, t, oz);
   *fp = fmaf(r.Zs, du * (float)it.nsu, fmaf(r.Zt, dv * (float)it.nsv, -dz));
 }
@@ -217,8 +415,8 @@ __device__ __forceinline__ void f_eval(const Item& it, const float4* sp, Patch& 
 // Point source (a1, a2, a4-a6): Philox direction uniform in the cone, flat
 // entry face, Snell + Schlick into the glass, safeguarded Newton on f(t)
 // bracketed by the convex hull of the control heights (Sec. 2.1.2).
-__device__ __forceinline__ void trace_point(const Item& it, const float4* sp, Patch& pc, uint64_t id, float zmin,
-                                            float zmax, RayFwd& r) {
+__device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, uint64_t id, float zmin, float zmax,
+                                            RayFwd& r) {
   r.iters = 0;
   const uint2 w = philox_ray_words(it.seed, id);
   const float xi1 = unit23(w.x), xi2 = unit23(w.y);
@@ -235,7 +433,7 @@ __device__ __forceinline__ void trace_point(const Item& it, const float4* sp, Pa
   const float omc = it.omc_max * xi2;            // 1 - cos(phi)
   const float sphi = sqrtf(omc * (2.0f - omc));
   const float d0x = cn * sphi, d0y = sn * sphi, d0z = 1.0f - omc;
-  const float tau = __fdividef(it.z_in - it.pz, d0z);
+  const float tau = (it.z_in - it.pz) * fast_rcp(d0z);
   const float ox = fmaf(tau, d0x, sx), oy = fmaf(tau, d0y, sy), oz = it.z_in;
   if (!(tau > 0.0f) || fabsf(ox) > it.rx || fabsf(oy) > it.ry) { r.status = FR_RAY_APERTURE_MISS; return; }
   // Snell air -> glass at the flat face, normal (0,0,1).
@@ -248,7 +446,7 @@ __device__ __forceinline__ void trace_point(const Item& it, const float4* sp, Pa
   // Bracket: the slab zmin <= z <= zmax, widened a little for FP32 rounding,
   // cut where the ray leaves the domain [0,1]^2 (the side of the lens).
   const float pad = 1e-6f * (1.0f + fmaxf(fabsf(zmin), fabsf(zmax)));
-  const float inv_dz = 1.0f / r.dz;
+  const float inv_dz = fast_rcp(r.dz);
   float ta = fmaxf(0.0f, (zmin - pad - oz) * inv_dz);
   const float t_hi = (zmax + pad - oz) * inv_dz;
   const float ou = fmaf(0.5f / it.rx, ox, 0.5f), ov = fmaf(0.5f / it.ry, oy, 0.5f);
@@ -262,20 +460,27 @@ __device__ __forceinline__ void trace_point(const Item& it, const float4* sp, Pa
   float tb = fminf(t_hi, t_dom);
   float f, fp;
   if (tb < t_hi) {
-    f_eval(it, sp, pc, ou, ov, du, dv, oz, r.dz, tb, r, &f, &fp);
+    f_eval(it, ls, ou, ov, du, dv, oz, r.dz, tb, r, &f, &fp);
     if (f > 0.0f) { r.status = FR_RAY_OUT_OF_DOMAIN; return; }   // leaves the side first
   }
-  float t = ta;
-  f_eval(it, sp, pc, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
-  if (f < 0.0f) { r.status = FR_RAY_INVALID; return; }
+  // f(ta) >= 0 by the convex hull unless the slab starts at the entry face,
+  // where the freeform may lie below it.
+  if (ta == 0.0f) {
+    f_eval(it, ls, ou, ov, du, dv, oz, r.dz, 0.0f, r, &f, &fp);
+    if (f < 0.0f) { r.status = FR_RAY_INVALID; return; }
+  }
+  // Newton from the middle of the bracket, with bisection as the safeguard.
+  float t = 0.5f * (ta + tb);
+  f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
+  if (f > 0.0f) ta = t; else tb = t;
   bool converged = (f == 0.0f);
-  for (int it_n = 0; it_n < it.newton_max && !converged; ++it_n) {
+  for (int n = 0; n < it.newton_max && !converged; ++n) {
     float tn = t - __fdividef(f, fp);
     if (!(fp < 0.0f) || !(tn > ta && tn < tb)) tn = 0.5f * (ta + tb);
     const float step = fabsf(tn - t);
     t = tn;
-    f_eval(it, sp, pc, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
-    r.iters = it_n + 1;
+    f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
+    r.iters = n + 1;
     if (f > 0.0f) ta = t; else tb = t;
     if (step <= it.newton_tol || f == 0.0f) converged = true;
   }
@@ -287,7 +492,7 @@ __device__ __forceinline__ void trace_point(const Item& it, const float4* sp, Pa
   r.x = fmaf(r.dx, t, ox);
   r.y = fmaf(r.dy, t, oy);
   r.z = fmaf(r.dz, t, oz);
-  exit_and_propagate(it, r);
+  exit_and_propagate<false>(it, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,36 +502,39 @@ __device__ __forceinline__ void trace_point(const Item& it, const float4* sp, Pa
 template <int NU>
 struct Foot {
   int ie, je;           // extended column / row of the footprint's first cell
-  float gx, gy;         // hit in extended pixel units
+  float dx0, dy0;       // hit minus the centre of the first cell, in pixels
   float fx[NU], fy[NU]; // filter values
   float rsx, rsy;       // 1 / sum f
 };
 
 template <int NU>
-__device__ __forceinline__ bool footprint(const Item& it, float X, float Y, Foot<NU>& f) {
+__device__ __forceinline__ void axis_footprint(float g, int n, float a2, float cut, int* first, float* d0, float* f,
+                                               float* rs) {
   constexpr int h = (NU - 1) / 2;
-  const float gx = (X + it.Rsx) * it.inv_wx;
-  const float gy = (Y + it.Rsy) * it.inv_wy;
-  const int ic = min(max((int)floorf(gx), h), it.nx + h - 1);
-  const int jc = min(max((int)floorf(gy), h), it.ny + h - 1);
-  f.gx = gx;
-  f.gy = gy;
-  f.ie = ic - h;
-  f.je = jc - h;
-  float sx = 0.0f, sy = 0.0f;
+  const float fl = fminf(fmaxf(floorf(g), (float)h), (float)(n + h - 1));
+  *first = (int)fl - h;
+  const float dfirst = g - fl + ((float)h - 0.5f);   // g - (first + 0.5)
+  *d0 = dfirst;
+  float sum = 0.0f;
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    const float dxa = gx - ((float)(f.ie + a) + 0.5f);
-    const float dya = gy - ((float)(f.je + a) + 0.5f);
-    f.fx[a] = fabsf(dxa) < 0.5f * NU ? exp2f(-it.ax * dxa * dxa) - it.cut : 0.0f;
-    f.fy[a] = fabsf(dya) < 0.5f * NU ? exp2f(-it.ay * dya * dya) - it.cut : 0.0f;
-    sx += f.fx[a];
-    sy += f.fy[a];
+    // Outside the support |d| >= nu/2 the exponential is at most `cut`, so the
+    // clamp at 0 is the support test.
+    const float d = dfirst - (float)a;
+    f[a] = fmaxf(ex2_approx(-a2 * d * d) - cut, 0.0f);
+    sum += f[a];
   }
-  if (!(sx > 0.0f) || !(sy > 0.0f)) return false;  // nu = 1 exactly on a pixel edge
-  f.rsx = 1.0f / sx;
-  f.rsy = 1.0f / sy;
-  return true;
+  // For nu >= 3 the hit's own pixel is well inside the support: sum > 0.
+  *rs = (NU >= 3 || sum > 0.0f) ? fast_rcp(sum) : 0.0f;
+}
+
+template <int NU>
+__device__ __forceinline__ bool footprint(const Item& it, float X, float Y, Foot<NU>& f) {
+  const float gx = fmaf(X, it.inv_wx, it.gx_off);
+  const float gy = fmaf(Y, it.inv_wy, it.gy_off);
+  axis_footprint<NU>(gx, it.nx, it.ax, it.cut, &f.ie, &f.dx0, f.fx, &f.rsx);
+  axis_footprint<NU>(gy, it.ny, it.ay, it.cut, &f.je, &f.dy0, f.fy, &f.rsy);
+  return NU >= 3 || (f.rsx > 0.0f && f.rsy > 0.0f);   // nu = 1 exactly on a pixel edge: all f = 0
 }
 
 // ---------------------------------------------------------------------------
@@ -335,21 +543,20 @@ __device__ __forceinline__ bool footprint(const Item& it, float X, float Y, Foot
 // slopes, from which dL/dP^z_{k+a,l+b} = zeta N_a N_b + Zs_bar N'_a N_b
 // + Zt_bar N_a N'_b.
 // ---------------------------------------------------------------------------
-template <int NU>
-__device__ __forceinline__ void ray_reverse(const Item& it, const RayFwd& r, const Foot<NU>& f,
-                                            const float (&G)[NU][NU], bool point, const Patch& pc,
-                                            float* zeta, float* Zs_bar, float* Zt_bar) {
-  // Filter: F_a = f_a / S, dF_a/dX = (f'_a - F_a S') / S with f'_a = -2 alpha delta_a e_a / w.
+template <int NU, bool COLL>
+__device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, const RayFwd& r, const Foot<NU>& f,
+                                            const float (&G)[NU][NU], float* zeta, float* Zs_bar, float* Zt_bar) {
+  // Filter: F_a = f_a / S, dF_a/dX = (f'_a - F_a S') / S, f'_a = -2 alpha delta_a e_a / w.
+  // With nu = 1 the normalised filter is identically 1 on its pixel: dF = 0.
   const float ln2 = 0.69314718055994531f;
+  const float kx = -2.0f * (it.ax * ln2) * it.inv_wx, ky = -2.0f * (it.ay * ln2) * it.inv_wy;
   float Fx[NU], Fy[NU], gxa[NU], gya[NU];
   float Spx = 0.0f, Spy = 0.0f;
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    const float dxa = f.gx - ((float)(f.ie + a) + 0.5f);
-    const float dya = f.gy - ((float)(f.je + a) + 0.5f);
-    // exp part e = f + cut inside the support, its derivative in world units
-    gxa[a] = f.fx[a] != 0.0f ? -2.0f * (it.ax * ln2) * dxa * (f.fx[a] + it.cut) * it.inv_wx : 0.0f;
-    gya[a] = f.fy[a] != 0.0f ? -2.0f * (it.ay * ln2) * dya * (f.fy[a] + it.cut) * it.inv_wy : 0.0f;
+    const float dxa = f.dx0 - (float)a, dya = f.dy0 - (float)a;
+    gxa[a] = f.fx[a] != 0.0f ? kx * dxa * (f.fx[a] + it.cut) : 0.0f;
+    gya[a] = f.fy[a] != 0.0f ? ky * dya * (f.fy[a] + it.cut) : 0.0f;
     Spx += gxa[a];
     Spy += gya[a];
     Fx[a] = f.fx[a] * f.rsx;
@@ -357,8 +564,6 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const RayFwd& r, con
   }
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    // With nu = 1 the normalised filter is identically 1 on its pixel: its
-    // derivative is exactly 0 (the general formula leaves rounding noise).
     gxa[a] = NU == 1 ? 0.0f : (gxa[a] - Fx[a] * Spx) * f.rsx;
     gya[a] = NU == 1 ? 0.0f : (gya[a] - Fy[a] * Spy) * f.rsy;
   }
@@ -379,10 +584,10 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const RayFwd& r, con
   wbar *= it.inv_area;
   const float Xbar = K * Xs, Ybar = K * Ys;
   // Propagation X = x + lam t_x, lam = (z_s - z)/t_z.
-  float txb = r.lam * Xbar, tyb = r.lam * Ybar;
+  const float txb = r.lam * Xbar, tyb = r.lam * Ybar;
   const float lamb = fmaf(Xbar, r.tx, Ybar * r.ty);
-  const float inv_tz = 1.0f / r.tz;
-  float tzb = -lamb * r.lam * inv_tz;
+  const float inv_tz = fast_rcp(r.tz);
+  const float tzb = -lamb * r.lam * inv_tz;
   const float zbar = -lamb * inv_tz;
   // Weight w = omega0 T1 T2, T2 = (1-R0)(1-(1-cs)^5).
   const float om = 1.0f - r.cs;
@@ -394,25 +599,29 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const RayFwd& r, con
   float nbx = -r.a * txb, nby = -r.a * tyb, nbz = -r.a * tzb;
   float cbar = eta * abar;
   csb -= abar;
-  const float kbar = csb * 0.5f / r.cs;
+  const float kbar = csb * 0.5f * fast_rcp(r.cs);
   cbar = fmaf(kbar * 2.0f * eta * eta, r.c, cbar);
-  nbx = fmaf(cbar, r.dx, nbx);
-  nby = fmaf(cbar, r.dy, nby);
-  nbz = fmaf(cbar, r.dz, nbz);
+  if (COLL) {
+    nbz += cbar;
+  } else {
+    nbx = fmaf(cbar, r.dx, nbx);
+    nby = fmaf(cbar, r.dy, nby);
+    nbz = fmaf(cbar, r.dz, nbz);
+  }
   // Normalisation n = m / |m|, m = (-Z_x, -Z_y, 1).
   const float ndot = nbx * r.nx + nby * r.ny + nbz * r.nz;
   const float mbx = (nbx - ndot * r.nx) * r.invL;
   const float mby = (nby - ndot * r.ny) * r.invL;
   *Zs_bar = -mbx * it.ku;
   *Zt_bar = -mby * it.kv;
-  if (!point) {
+  if (COLL) {
     *zeta = zbar;   // the hit height is Z itself
     return;
   }
-  // Point source: the hit moves along the ray with t*; implicit function
+  // Point source: the hit moves along the ray with t*; the implicit function
   // theorem on f(t*, P) = 0 gives dt*/dP_ab = -N_a N_b / f'(t*).
   float Zss, Zst, Ztt;
-  patch_eval2(pc, r.s, r.t, &Zss, &Zst, &Ztt);
+  patch_eval2(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Zss, &Zst, &Ztt);
   const float dsdt = r.dx * (0.5f / it.rx) * (float)it.nsu;
   const float dtdt = r.dy * (0.5f / it.ry) * (float)it.nsv;
   const float tbar = Xbar * r.dx + Ybar * r.dy + zbar * r.dz +
@@ -420,25 +629,18 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const RayFwd& r, con
   *zeta = -tbar / r.gp;
 }
 
-// Per-thread ray counts by cause (FR_RAY_*), summed per CTA and added to the
-// caller's fr_stats once per CTA.
-struct Counters {
-  unsigned int n[FR_RAY_NCAUSES];
-  __device__ __forceinline__ void clear() {
-#pragma unroll
-    for (int s = 0; s < FR_RAY_NCAUSES; ++s) n[s] = 0u;
+// Ray counts by cause (FR_RAY_*): a per-thread count of deposited rays and
+// shared-memory counters for the rest (only when the caller asked for them).
+struct RayCount {
+  unsigned int on_screen;
+  __device__ __forceinline__ void add(int status, unsigned int* s_cnt) {
+    if (status == FR_RAY_ON_SCREEN) ++on_screen;
+    else if (s_cnt) atomicAdd(&s_cnt[status], 1u);
   }
-  __device__ __forceinline__ void add(int status) {
-#pragma unroll
-    for (int s = 0; s < FR_RAY_NCAUSES; ++s) n[s] += (status == s) ? 1u : 0u;
-  }
-  // Warp sums, then one shared atomic per warp and cause (all lanes active).
+  // All lanes of every warp call this.
   __device__ __forceinline__ void reduce_into(unsigned int* s_cnt) const {
-#pragma unroll
-    for (int s = 0; s < FR_RAY_NCAUSES; ++s) {
-      const unsigned int v = __reduce_add_sync(0xffffffffu, n[s]);
-      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[s], v);
-    }
+    const unsigned int v = __reduce_add_sync(0xffffffffu, on_screen);
+    if ((threadIdx.x & 31) == 0 && v && s_cnt) atomicAdd(&s_cnt[FR_RAY_ON_SCREEN], v);
   }
   // After a __syncthreads that follows reduce_into.
   static __device__ __forceinline__ void publish(const unsigned int* s_cnt, fr_stats* stats) {
@@ -447,5 +649,19 @@ struct Counters {
                 (unsigned long long)s_cnt[threadIdx.x]);
   }
 };
+
+// The rays [a, b) of this lane: the item's rays are split evenly over all warps
+// of the item's CTAs, and each warp's share evenly over its 32 lanes, so every
+// lane traces a run of consecutive ray ids (consecutive grid cells of one row
+// for a collimated source).
+__device__ __forceinline__ void lane_range(const Item& it, int warps, uint64_t* a, uint64_t* b) {
+  const uint64_t n = it.ray_end - it.ray_begin;
+  const uint64_t W = (uint64_t)(it.cta_end - it.cta_begin) * (uint64_t)warps;
+  const uint64_t gw = (uint64_t)((int)blockIdx.x - it.cta_begin) * (uint64_t)warps + (threadIdx.x >> 5);
+  const uint64_t w0 = n * gw / W, w1 = n * (gw + 1) / W;
+  const uint64_t m = w1 - w0, lane = threadIdx.x & 31;
+  *a = it.ray_begin + w0 + m * lane / 32;
+  *b = it.ray_begin + w0 + m * (lane + 1) / 32;
+}
 
 }  // namespace fr

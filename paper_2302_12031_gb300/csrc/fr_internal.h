@@ -24,11 +24,6 @@ struct Item {
   float rx, ry, z_in, n_glass;
   float ku, kv;                 // d(span coordinate)/dx = nsu/(2 rx), likewise kv
   float R0;                     // ((n-1)/(n+1))^2
-  // Workspace written by the prep kernel.
-  float4* patch;                // [nsu*nsv][4]: row e holds C[e][0..3] of Z = sum C[e][f] s^e t^f
-  float4* basis_u;              // [nsu][4]: coefficients of N_{k+a}(s) in powers of s
-  float4* basis_v;              // [nsv][4]
-  float* zb;                    // [2]: min and max control height
   // Source (Sec. 2.2.1).
   int kind, jitter, cols, rows;
   float px, py, pz;             // source position (grid centre)
@@ -44,6 +39,7 @@ struct Item {
   int nx, ny, nu, ncol, nrow;
   float inv_wx, inv_wy;         // 1/w
   float Rsx, Rsy;               // R* = R + (nu-1)/2 w
+  float gx_off, gy_off;         // R* / w: the screen edge -R* in extended pixel units
   float ax, ay;                 // alpha * log2(e)
   float cut;                    // exp(-alpha (nu/2)^2)
   float inv_area;               // 1/(w_x w_y)
@@ -60,13 +56,11 @@ struct Item {
   // Newton (Sec. 2.2.1 intersection, point sources).
   int newton_max;
   float newton_tol;
-  // Schedule.
-  int rays_per_lane;            // consecutive rays per lane in a tile row (collimated) or per tile
-  int row_lo, row_hi;           // collimated: grid rows touched by [ray_begin, ray_end)
-  int segs;                     // collimated: tiles per row group
-  int tiles;                    // tiles of this item
+  // Schedule: the item's rays are split evenly over the lanes of CTAs
+  // [cta_begin, cta_end) of the launch (lane_range in fr_device.cuh).
+  int max_ctas;                 // CTAs worth launching (every lane gets a minimum run)
   int smem_hist;                // forward: 1 = privatised histogram in shared memory
-  int cta_begin, cta_end;       // CTAs of the launch that work on this item
+  int cta_begin, cta_end;
 };
 
 template <int CAP>
@@ -81,7 +75,6 @@ size_t fwd_smem_bytes(const Item& it, bool det);
 size_t adj_smem_bytes(const Item& it, bool det);
 
 // Launchers (return the CUDA error of the launch).
-cudaError_t launch_prep(const Item* items, int n_items, cudaStream_t st);
 template <int CAP>
 cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
 template <int CAP>
@@ -95,11 +88,13 @@ cudaError_t launch_loss(const float* E, const float* Eref, int nx, int ny, int n
                         cudaStream_t st);
 cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1,
                         float b2, float eps, int32_t* step, cudaStream_t st);
-
-
+cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);
+cudaError_t configure_forward(int optin);
+cudaError_t configure_adjoint(int optin);
 
 // Occupancy of the trace kernels for a block size and dynamic shared memory.
-int forward_occupancy(int threads, size_t smem, bool det, bool batch);
-int adjoint_occupancy(int threads, size_t smem, bool det, bool batch);
+// kinds: 1 collimated, 2 point source (single-lens launches); batches use both.
+int forward_occupancy(int threads, size_t smem, bool det, bool batch, int nu, int kinds);
+int adjoint_occupancy(int threads, size_t smem, bool det, bool batch, int nu, int kinds);
 
 }  // namespace fr

@@ -1,15 +1,17 @@
 // Adjoint kernel (row a9): reverse mode of the forward trace, recomputing each
 // ray's path from its id instead of storing it.
 //
-// Per ray: the forward code of fr_device.cuh runs again; dL/dE is gathered on
-// the nu x nu footprint (kept in registers while the footprint does not move);
-// ray_reverse() carries it back through the filter, propagation, Schlick,
-// Snell and the normal (and, for point sources, the intersection by the
-// implicit function theorem) to the three adjoints (zeta, Zs_bar, Zt_bar); the
-// 16 control-point gradients of the ray's knot span are
-//   dL/dP_{k+a,l+b} += zeta N_a N_b + Zs_bar N'_a N_b + Zt_bar N_a N'_b
-// and are summed in registers while the span does not change, then flushed to a
-// CTA-private copy of dL/dP in shared memory, which is added to global memory
+// The CTA builds its lens's tables in shared memory as the forward kernel does
+// and every lane takes the same run of rays. Per ray: the forward code of
+// fr_device.cuh runs again; dL/dE is gathered on the nu x nu footprint (kept in
+// registers while the footprint does not move); ray_reverse() carries it back
+// through the filter, propagation, Schlick, Snell and the normal (and, for
+// point sources, the intersection by the implicit function theorem) to three
+// adjoints (zeta, Zs_bar, Zt_bar); the 16 control-point gradients of the ray's
+// knot span are
+//   dL/dP_{k+a,l+b} += zeta N_a N_b + Zs_bar N'_a N_b + Zt_bar N_a N'_b,
+// summed in registers while the span does not change, then flushed to a
+// CTA-private copy of dL/dP in shared memory that is added to global memory
 // once at the end.
 #include "fr_device.cuh"
 
@@ -47,30 +49,41 @@ __device__ __forceinline__ void grad_flush(GradAcc<DET>& acc, int ncv, float* sg
   acc.k = -1;
 }
 
-template <int NU, bool DET>
-__device__ __forceinline__ void adjoint_ray(const Item& it, const RayFwd& r, const Patch& pc, const float4* sbu,
-                                            const float4* sbv, float (&G)[NU][NU], int& gie, int& gje,
-                                            GradAcc<DET>& acc, float fixP, float* sg_f, unsigned long long* sg_q,
-                                            bool point) {
+struct GradOut {
+  float* sg_f;
+  unsigned long long* sg_q;
+  float fixP;
+};
+
+// The footprint of dL/dE, re-read only when the footprint moves.
+template <int NU>
+struct GCache {
+  int ie, je;
+  float G[NU][NU];
+};
+
+template <int NU, bool DET, bool COLL>
+__device__ __forceinline__ void adjoint_ray(const Item& it, const LensSmem& ls, const RayFwd& r, GCache<NU>& gc,
+                                            const float (&Nv)[4], const float (&dNv)[4], GradAcc<DET>& acc,
+                                            const GradOut& go) {
   Foot<NU> f;
   if (!footprint<NU>(it, r.X, r.Y, f)) return;
-  if (f.ie != gie || f.je != gje) {
+  if (f.ie != gc.ie || f.je != gc.je) {
 #pragma unroll
     for (int b = 0; b < NU; ++b)
 #pragma unroll
-      for (int a = 0; a < NU; ++a) G[b][a] = __ldg(it.dLdE + (size_t)(f.je + b) * it.ncol + f.ie + a);
-    gie = f.ie;
-    gje = f.je;
+      for (int a = 0; a < NU; ++a) gc.G[b][a] = __ldg(it.dLdE + (size_t)(f.je + b) * it.ncol + f.ie + a);
+    gc.ie = f.ie;
+    gc.je = f.je;
   }
   float zeta, Zsb, Ztb;
-  ray_reverse<NU>(it, r, f, G, point, pc, &zeta, &Zsb, &Ztb);
-  float Nu[4], dNu[4], Nv[4], dNv[4];
-  basis_eval(sbu + pc.k * 4, r.s, Nu, dNu);
-  basis_eval(sbv + pc.l * 4, r.t, Nv, dNv);
-  if (pc.k != acc.k || pc.l != acc.l) {
-    grad_flush<DET>(acc, it.ncv, sg_f, sg_q);
-    acc.k = pc.k;
-    acc.l = pc.l;
+  ray_reverse<NU, COLL>(it, ls, r, f, gc.G, &zeta, &Zsb, &Ztb);
+  float Nu[4], dNu[4];
+  basis_eval(ls.bu + r.k * 4, r.s, Nu, dNu);
+  if (r.k != acc.k || r.l != acc.l) {
+    grad_flush<DET>(acc, it.ncv, go.sg_f, go.sg_q);
+    acc.k = r.k;
+    acc.l = r.l;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -83,116 +96,211 @@ __device__ __forceinline__ void adjoint_ray(const Item& it, const RayFwd& r, con
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const float c = fmaf(A, Nv[b], B * dNv[b]);
-      if constexpr (DET) acc.g[a][b] += __float2ll_rn(c * fixP);
+      if constexpr (DET) acc.g[a][b] += __float2ll_rn(c * go.fixP);
       else acc.g[a][b] += c;
     }
   }
 }
 
-template <int NU, bool DET>
-__device__ void run_adjoint_tiles(const Item& it, const float4* sp, const float4* sbu, const float4* sbv, int t0,
-                                  int t1, float zmin, float zmax, float fixP, float* sg_f,
-                                  unsigned long long* sg_q, unsigned int* s_cnt) {
-  const int R = it.rays_per_lane;
-  Patch pc;
-  pc.k = -1;
-  pc.l = -1;
+// Along one grid row of a collimated source t, N_b(t) and N'_b(t) are fixed, so
+// the 16 gradient terms of the rays that fall in one patch factor through
+// power moments of s:
+//   sum_rays (zeta N_a(s) + Zs_bar N'_a(s)) = sum_e c_ae M_e + sum_e e c_ae D_{e-1},
+//   sum_rays Zt_bar N_a(s) = sum_e c_ae Q_e,
+// with N_a(s) = sum_e c_ae s^e, M_e = sum zeta s^e, D_e = sum Zs_bar s^e,
+// Q_e = sum Zt_bar s^e. The moments are summed per ray and expanded through the
+// basis table only when the patch or the row changes (float mode).
+struct RowMoments {
+  int k, l;
+  uint32_t row;
+  float M0, M1, M2, M3, D0, D1, D2, Q0, Q1, Q2, Q3;
+};
+
+__device__ __forceinline__ void moments_flush(RowMoments& m, const LensSmem& ls, int ncv, const float (&Nv)[4],
+                                              const float (&dNv)[4], float* sg) {
+  if (m.k < 0) return;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float4 c = ls.bu[m.k * 4 + a];
+    const float SA = fmaf(c.x, m.M0, fmaf(c.y, m.M1, fmaf(c.z, m.M2, fmaf(c.w, m.M3,
+                     fmaf(c.y, m.D0, fmaf(2.0f * c.z, m.D1, 3.0f * c.w * m.D2))))));
+    const float SB = fmaf(c.x, m.Q0, fmaf(c.y, m.Q1, fmaf(c.z, m.Q2, c.w * m.Q3)));
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float v = fmaf(SA, Nv[b], SB * dNv[b]);
+      if (v != 0.0f) atomicAdd(sg + (m.k + a) * ncv + m.l + b, v);
+    }
+  }
+  m.k = -1;
+}
+
+template <int NU>
+__device__ __forceinline__ void adjoint_ray_moments(const Item& it, const LensSmem& ls, const RayFwd& r,
+                                                    uint32_t row, GCache<NU>& gc, RowMoments& m,
+                                                    const float (&Nv)[4], const float (&dNv)[4], float* sg) {
+  Foot<NU> f;
+  if (!footprint<NU>(it, r.X, r.Y, f)) return;
+  if (f.ie != gc.ie || f.je != gc.je) {
+#pragma unroll
+    for (int b = 0; b < NU; ++b)
+#pragma unroll
+      for (int a = 0; a < NU; ++a) gc.G[b][a] = __ldg(it.dLdE + (size_t)(f.je + b) * it.ncol + f.ie + a);
+    gc.ie = f.ie;
+    gc.je = f.je;
+  }
+  float zeta, Zsb, Ztb;
+  ray_reverse<NU, true>(it, ls, r, f, gc.G, &zeta, &Zsb, &Ztb);
+  if (r.k != m.k || row != m.row) {
+    moments_flush(m, ls, it.ncv, Nv, dNv, sg);
+    m.k = r.k;
+    m.l = r.l;
+    m.row = row;
+    m.M0 = m.M1 = m.M2 = m.M3 = m.D0 = m.D1 = m.D2 = m.Q0 = m.Q1 = m.Q2 = m.Q3 = 0.0f;
+  }
+  const float s = r.s, s2 = s * s, s3 = s2 * s;
+  m.M0 += zeta;
+  m.M1 = fmaf(zeta, s, m.M1);
+  m.M2 = fmaf(zeta, s2, m.M2);
+  m.M3 = fmaf(zeta, s3, m.M3);
+  m.D0 += Zsb;
+  m.D1 = fmaf(Zsb, s, m.D1);
+  m.D2 = fmaf(Zsb, s2, m.D2);
+  m.Q0 += Ztb;
+  m.Q1 = fmaf(Ztb, s, m.Q1);
+  m.Q2 = fmaf(Ztb, s2, m.Q2);
+  m.Q3 = fmaf(Ztb, s3, m.Q3);
+}
+
+// KINDS: bit 0 = the kernel handles collimated items, bit 1 = point-source items.
+template <int NU, bool DET, int KINDS>
+__device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, uint64_t a, uint64_t b, float zmin, float zmax,
+                                 const GradOut& go, RayCount& cnt, unsigned int* s_cnt) {
   GradAcc<DET> acc;
   acc.k = -1;
-  float G[NU][NU];
-  int gie = -1, gje = -1;
-  Counters cnt;
-  cnt.clear();
-  if (it.kind == FR_SOURCE_COLLIMATED) {
-    const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
-    for (int tile = t0; tile < t1; ++tile) {
-      const int rg = tile / it.segs, sg = tile - rg * it.segs;
-      const int row = it.row_lo + rg * warps + warp;
-      if (row >= it.row_hi) continue;
-      const int col0 = (sg * 32 + lane) * R;
-      for (int j = 0; j < R; ++j) {
-        const int col = col0 + j;
-        if (col >= it.cols) break;
-        const uint64_t id = (uint64_t)row * (uint64_t)it.cols + (uint64_t)col;
-        if (id < it.ray_begin || id >= it.ray_end) continue;
-        RayFwd r;
-        trace_collimated(it, sp, pc, row, col, id, inv_cols, inv_rows, r);
-        cnt.add(r.status);
-        if (r.status != FR_RAY_ON_SCREEN) continue;
-        adjoint_ray<NU, DET>(it, r, pc, sbu, sbv, G, gie, gje, acc, fixP, sg_f, sg_q, false);
+  GCache<NU> gc;
+  gc.ie = gc.je = -1;
+  if (a < b) {
+    if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
+      const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+      uint32_t row = (uint32_t)(a / (uint64_t)it.cols);
+      uint32_t col = (uint32_t)(a - (uint64_t)row * (uint64_t)it.cols);
+      float Nv[4], dNv[4];
+      const uint32_t n = (uint32_t)(b - a);
+      if (!it.jitter && !DET) {
+        RowPatch rp;
+        rp.row = 0xffffffffu;
+        RowMoments m;
+        m.k = -1;
+        m.row = 0xffffffffu;
+        uint32_t nv_row = 0xffffffffu;
+        for (uint32_t j = 0; j < n; ++j) {
+          RayFwd r;
+          trace_collimated_row(it, ls, row, col, inv_cols, inv_rows, rp, r);
+          cnt.add(r.status, s_cnt);
+          if (r.status == FR_RAY_ON_SCREEN) {
+            if (row != nv_row) {   // the v basis is fixed along a row
+              moments_flush(m, ls, it.ncv, Nv, dNv, go.sg_f);   // moments of the previous row
+              basis_eval(ls.bv + rp.l * 4, rp.t, Nv, dNv);
+              nv_row = row;
+            }
+            adjoint_ray_moments<NU>(it, ls, r, row, gc, m, Nv, dNv, go.sg_f);
+          }
+          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
+        }
+        moments_flush(m, ls, it.ncv, Nv, dNv, go.sg_f);
+      } else if (!it.jitter) {
+        RowPatch rp;
+        rp.row = 0xffffffffu;
+        uint32_t nv_row = 0xffffffffu;
+        for (uint32_t j = 0; j < n; ++j) {
+          RayFwd r;
+          trace_collimated_row(it, ls, row, col, inv_cols, inv_rows, rp, r);
+          cnt.add(r.status, s_cnt);
+          if (r.status == FR_RAY_ON_SCREEN) {
+            if (row != nv_row) {   // the v basis is fixed along a row
+              basis_eval(ls.bv + rp.l * 4, rp.t, Nv, dNv);
+              nv_row = row;
+            }
+            adjoint_ray<NU, DET, true>(it, ls, r, gc, Nv, dNv, acc, go);
+          }
+          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
+        }
+      } else {
+        for (uint32_t j = 0; j < n; ++j) {
+          RayFwd r;
+          trace_collimated(it, ls, row, col, a + j, inv_cols, inv_rows, r);
+          cnt.add(r.status, s_cnt);
+          if (r.status == FR_RAY_ON_SCREEN) {
+            basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+            adjoint_ray<NU, DET, true>(it, ls, r, gc, Nv, dNv, acc, go);
+          }
+          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
+        }
       }
-    }
-  } else {
-    const uint64_t per_tile = (uint64_t)blockDim.x * (uint64_t)R;
-    for (int tile = t0; tile < t1; ++tile) {
-      const uint64_t base = it.ray_begin + (uint64_t)tile * per_tile + threadIdx.x;
-      for (int j = 0; j < R; ++j) {
-        const uint64_t id = base + (uint64_t)j * blockDim.x;
-        if (id >= it.ray_end) break;
+    } else if (KINDS & 2) {
+      float Nv[4], dNv[4];
+      for (uint64_t id = a; id < b; ++id) {
         RayFwd r;
-        trace_point(it, sp, pc, id, zmin, zmax, r);
-        cnt.add(r.status);
-        if (r.status != FR_RAY_ON_SCREEN) continue;
-        adjoint_ray<NU, DET>(it, r, pc, sbu, sbv, G, gie, gje, acc, fixP, sg_f, sg_q, true);
+        trace_point(it, ls, id, zmin, zmax, r);
+        cnt.add(r.status, s_cnt);
+        if (r.status == FR_RAY_ON_SCREEN) {
+          basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+          adjoint_ray<NU, DET, false>(it, ls, r, gc, Nv, dNv, acc, go);
+        }
       }
     }
   }
-  grad_flush<DET>(acc, it.ncv, sg_f, sg_q);
-  cnt.reduce_into(s_cnt);
+  grad_flush<DET>(acc, it.ncv, go.sg_f, go.sg_q);
 }
 
-template <int CAP, bool DET>
-__global__ void __launch_bounds__(256) k_adjoint(const __grid_constant__ Launch<CAP> L) {
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <int CAP, bool DET, int NU, int KINDS>
+__global__ void __launch_bounds__(256, 2) k_adjoint(const __grid_constant__ Launch<CAP> L) {
   int ii = 0;
   while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
   const Item& it = L.items[ii];
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* sp = reinterpret_cast<float4*>(smem);
-  const int np4 = it.nsu * it.nsv * 4;
-  float4* sbu = sp + np4;
-  float4* sbv = sbu + it.nsu * 4;
-  unsigned char* grad_raw = reinterpret_cast<unsigned char*>(sbv + it.nsv * 4);
-  float* sg_f = reinterpret_cast<float*>(grad_raw);
-  unsigned long long* sg_q = reinterpret_cast<unsigned long long*>(grad_raw);
-  for (int q = threadIdx.x; q < np4; q += blockDim.x) sp[q] = it.patch[q];
-  for (int q = threadIdx.x; q < it.nsu * 4; q += blockDim.x) sbu[q] = it.basis_u[q];
-  for (int q = threadIdx.x; q < it.nsv * 4; q += blockDim.x) sbv[q] = it.basis_v[q];
+  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  unsigned char* grad_raw = smem + align16(lens_smem_bytes(it.nsu, it.nsv));
+  GradOut go;
+  go.sg_f = reinterpret_cast<float*>(grad_raw);
+  go.sg_q = reinterpret_cast<unsigned long long*>(grad_raw);
   const int nctrl = it.ncu * it.ncv;
   for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
-    if constexpr (DET) sg_q[q] = 0ull;
-    else sg_f[q] = 0.0f;
+    if constexpr (DET) go.sg_q[q] = 0ull;
+    else go.sg_f[q] = 0.0f;
   }
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
-  __syncthreads();
-  float fixP = 0.0f;
+  build_lens_tables(it, ls);   // ends with __syncthreads
+  go.fixP = 0.0f;
   if constexpr (DET) {
     // Fixed-point scale 2^40 / (max|dL/dE| * flux / pixel area), a power of two.
     const float unit = *it.gmax * it.fixP_unit;
     int e = 0;
     if (unit > 0.0f) frexpf(unit, &e);
-    fixP = unit > 0.0f ? ldexpf(1.0f, 40 - e) : 1.0f;
+    go.fixP = unit > 0.0f ? ldexpf(1.0f, 40 - e) : 1.0f;
   }
-  const float zmin = it.zb[0], zmax = it.zb[1];
-  const int ci = (int)blockIdx.x - it.cta_begin, G = it.cta_end - it.cta_begin;
-  const int t0 = (int)((long long)it.tiles * ci / G), t1 = (int)((long long)it.tiles * (ci + 1) / G);
-  switch (it.nu) {
-    case 1: run_adjoint_tiles<1, DET>(it, sp, sbu, sbv, t0, t1, zmin, zmax, fixP, sg_f, sg_q, s_cnt); break;
-    case 3: run_adjoint_tiles<3, DET>(it, sp, sbu, sbv, t0, t1, zmin, zmax, fixP, sg_f, sg_q, s_cnt); break;
-    default: run_adjoint_tiles<5, DET>(it, sp, sbu, sbv, t0, t1, zmin, zmax, fixP, sg_f, sg_q, s_cnt); break;
-  }
+  const float zmin = ls.zb[0], zmax = ls.zb[1];
+  uint64_t a, b;
+  lane_range(it, L.warps, &a, &b);
+  RayCount cnt;
+  cnt.on_screen = 0u;
+  unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+  run_adjoint_lane<NU, DET, KINDS>(it, ls, a, b, zmin, zmax, go, cnt, cnt_dst);
+  cnt.reduce_into(cnt_dst);
   __syncthreads();
   for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
     if constexpr (DET) {
-      const unsigned long long v = sg_q[q];
+      const unsigned long long v = go.sg_q[q];
       if (v) atomicAdd(it.Pfix + q, v);
     } else {
-      const float v = sg_f[q];
+      const float v = go.sg_f[q];
       if (v != 0.0f) atomicAdd(it.dLdP + q, v);
     }
   }
-  Counters::publish(s_cnt, it.stats);
+  RayCount::publish(s_cnt, it.stats);
 }
 
 // Deterministic mode: int64 fixed point -> float gradient, with the scale the
@@ -211,15 +319,34 @@ __global__ void k_grad_fix_to_float(const __grid_constant__ Item it, int accumul
 }  // namespace
 
 size_t adj_smem_bytes(const Item& it, bool det) {
-  return (size_t)it.nsu * it.nsv * 4 * sizeof(float4) + (size_t)(it.nsu + it.nsv) * 4 * sizeof(float4) +
-         (size_t)it.ncu * it.ncv * (det ? 8 : 4);
+  return ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15) + (size_t)it.ncu * it.ncv * (det ? 8 : 4);
+}
+
+template <int CAP>
+using AdjKernel = void (*)(Launch<CAP>);
+
+template <int CAP, bool DET, int KINDS>
+AdjKernel<CAP> pick_nu(int nu) {
+  return nu == 1 ? k_adjoint<CAP, DET, 1, KINDS> : (nu == 3 ? k_adjoint<CAP, DET, 3, KINDS> : k_adjoint<CAP, DET, 5, KINDS>);
+}
+
+template <int CAP>
+AdjKernel<CAP> pick_adjoint(bool det, int nu, int kinds);
+template <>
+AdjKernel<1> pick_adjoint<1>(bool det, int nu, int kinds) {
+  if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
+  return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
+}
+template <>
+AdjKernel<kMaxItems> pick_adjoint<kMaxItems>(bool det, int nu, int) {
+  return det ? pick_nu<kMaxItems, true, 3>(nu) : pick_nu<kMaxItems, false, 3>(nu);
 }
 
 template <int CAP>
 cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
   const int threads = 32 * L.warps;
-  if (det) k_adjoint<CAP, true><<<grid, threads, smem, st>>>(L);
-  else k_adjoint<CAP, false><<<grid, threads, smem, st>>>(L);
+  const int kinds = L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2;
+  pick_adjoint<CAP>(det, L.items[0].nu, kinds)<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
 template cudaError_t launch_adjoint<1>(const Launch<1>&, int, size_t, bool, cudaStream_t);
@@ -231,20 +358,13 @@ cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_
   return cudaGetLastError();
 }
 
-int adjoint_occupancy(int threads, size_t smem, bool det, bool batch) {
+int adjoint_occupancy(int threads, size_t smem, bool det, bool batch, int nu, int kinds) {
   int n = 0;
-  if (batch) {
-    if (det) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adjoint<kMaxItems, true>, threads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adjoint<kMaxItems, false>, threads, smem);
-  } else {
-    if (det) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adjoint<1, true>, threads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adjoint<1, false>, threads, smem);
-  }
+  if (batch) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_adjoint<kMaxItems>(det, nu, kinds), threads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_adjoint<1>(det, nu, kinds), threads, smem);
   return n;
 }
 
-// Opt every variant of the kernel in to the largest dynamic shared memory the
-// device allows next to the kernel's own static shared memory.
 template <class K>
 static cudaError_t allow_max_smem(K kernel, int optin) {
   cudaFuncAttributes a;
@@ -255,10 +375,13 @@ static cudaError_t allow_max_smem(K kernel, int optin) {
 
 cudaError_t configure_adjoint(int optin) {
   cudaError_t e;
-  if ((e = allow_max_smem(k_adjoint<1, false>, optin))) return e;
-  if ((e = allow_max_smem(k_adjoint<1, true>, optin))) return e;
-  if ((e = allow_max_smem(k_adjoint<kMaxItems, false>, optin))) return e;
-  return allow_max_smem(k_adjoint<kMaxItems, true>, optin);
+  for (int det = 0; det < 2; ++det)
+    for (int nu = 1; nu <= 5; nu += 2) {
+      for (int kinds = 1; kinds <= 2; ++kinds)
+        if ((e = allow_max_smem(pick_adjoint<1>(det != 0, nu, kinds), optin))) return e;
+      if ((e = allow_max_smem(pick_adjoint<kMaxItems>(det != 0, nu, 3), optin))) return e;
+    }
+  return cudaSuccess;
 }
 
 }  // namespace fr

@@ -1,16 +1,17 @@
 // Forward trace kernel (rows a1-a7) and the per-ray debug kernel.
 //
-// Schedule: each CTA works on one lens (item) and on a contiguous range of that
-// item's tiles, so its rays come from one compact part of the aperture.
-//  - collimated: a tile is `warps` consecutive grid rows x (32 * R) columns;
-//    lane l of warp w traces the R consecutive rays (row w, columns l*R ...);
-//  - point: a tile is blockDim * R consecutive ray ids.
+// Each CTA works on one lens (item). It first builds that lens's tables in
+// shared memory (the power form of the B-spline on every knot span, the basis
+// tables and the convex-hull bounds, Sec. 2.1), then every lane traces an equal
+// run of consecutive ray ids (lane_range), so the CTA's rays come from one
+// compact part of the aperture. For a collimated source without jitter the
+// row cubics of the current patch are kept in registers along a grid row.
 // Each lane keeps the nu x nu footprint of its last ray in registers and adds
 // the next ray there while the footprint does not move; it flushes the
-// registers (with atomics) when it does. Consecutive collimated rays usually
-// share a pixel, so most rays cost no atomic at all. The flush goes to a
-// privatised histogram in shared memory when the extended grid fits, else
-// straight to global memory.
+// registers (with atomics) when it does: consecutive collimated rays usually
+// share a pixel, so most rays cost no atomic. The flush goes to a privatised
+// histogram in shared memory when the extended grid fits, else straight to
+// global memory.
 #include "fr_device.cuh"
 
 namespace fr {
@@ -27,10 +28,16 @@ struct Bbox {
   int imin, imax, jmin, jmax;
 };
 
+// Where flushed footprints go. Float mode with a shared-memory histogram keeps
+// it as unsigned 32-bit fixed point (integer shared atomics are native and
+// twice as fast as float ones): sh_scale is a power of two chosen so that the
+// CTA's rays cannot overflow a cell (each ray adds at most flux/(n w_x w_y) to
+// a cell). Deterministic mode keeps int64 fixed point at the global scale.
 struct Target {
   bool smem;
   int ncol;
-  float* sh_f;
+  float sh_scale;
+  unsigned int* sh_u;
   unsigned long long* sh_q;
   float* gl_f;
   unsigned long long* gl_q;
@@ -49,26 +56,26 @@ __device__ __forceinline__ void acc_flush(FootAcc<NU, DET>& acc, const Target& t
   bb.imax = max(bb.imax, acc.ie);
   bb.jmin = min(bb.jmin, acc.je);
   bb.jmax = max(bb.jmax, acc.je);
+  const int base = acc.je * tg.ncol + acc.ie;
 #pragma unroll
   for (int b = 0; b < NU; ++b) {
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
       const auto val = acc.v[b][a];
-      if (val != 0) {
-        const int idx = (acc.je + b) * tg.ncol + acc.ie + a;
-        if constexpr (DET) {
-          if (tg.smem) atomicAdd(tg.sh_q + idx, (unsigned long long)val);
-          else atomicAdd(tg.gl_q + idx, (unsigned long long)val);
-        } else {
-          if (tg.smem) atomicAdd(tg.sh_f + idx, val);
-          else atomicAdd(tg.gl_f + idx, val);
-        }
+      const int idx = base + b * tg.ncol + a;
+      if constexpr (DET) {
+        if (tg.smem) atomicAdd(tg.sh_q + idx, (unsigned long long)val);
+        else atomicAdd(tg.gl_q + idx, (unsigned long long)val);
+      } else {
+        if (tg.smem) atomicAdd(tg.sh_u + idx, __float2uint_rn(val * tg.sh_scale));
+        else atomicAdd(tg.gl_f + idx, val);
       }
     }
   }
   acc.ie = -1;
 }
 
+// E_ij += w F_ij / (w_x w_y), F_ij = (f_i / S_x) (f_j / S_y).
 template <int NU, bool DET>
 __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const Target& tg, FootAcc<NU, DET>& acc,
                                         Bbox& bb) {
@@ -83,63 +90,59 @@ __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const T
 #pragma unroll
       for (int a = 0; a < NU; ++a) acc.v[b][a] = 0;
   }
-  // E_ij += w F_ij / (w_x w_y), F_ij = (f_i / S_x) (f_j / S_y).
-  const float K = r.w * it.inv_area;
+  const float Kx = r.w * it.inv_area * f.rsx;
   float kx[NU], ky[NU];
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    kx[a] = f.fx[a] * f.rsx * K;
+    kx[a] = f.fx[a] * Kx;
     ky[a] = f.fy[a] * f.rsy;
   }
 #pragma unroll
   for (int b = 0; b < NU; ++b) {
 #pragma unroll
     for (int a = 0; a < NU; ++a) {
-      const float c = kx[a] * ky[b];
-      if constexpr (DET) acc.v[b][a] += __float2ll_rn(c * it.fixE);
-      else acc.v[b][a] += c;
+      if constexpr (DET) acc.v[b][a] += __float2ll_rn(kx[a] * ky[b] * it.fixE);
+      else acc.v[b][a] = fmaf(kx[a], ky[b], acc.v[b][a]);
     }
   }
 }
 
-template <int NU, bool DET>
-__device__ void run_tiles(const Item& it, const float4* sp, const Target& tg, int t0, int t1, float zmin, float zmax,
-                          Counters& cnt, Bbox& bb) {
-  const int R = it.rays_per_lane;
-  Patch pc;
-  pc.k = -1;
-  pc.l = -1;
+// KINDS: bit 0 = the kernel handles collimated items, bit 1 = point-source items.
+template <int NU, bool DET, int KINDS>
+__device__ void run_lane(const Item& it, const LensSmem& ls, const Target& tg, uint64_t a, uint64_t b, float zmin,
+                         float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb) {
   FootAcc<NU, DET> acc;
   acc.ie = -1;
-  if (it.kind == FR_SOURCE_COLLIMATED) {
-    const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
-    for (int tile = t0; tile < t1; ++tile) {
-      const int rg = tile / it.segs, sg = tile - rg * it.segs;
-      const int row = it.row_lo + rg * warps + warp;
-      if (row >= it.row_hi) continue;
-      const int col0 = (sg * 32 + lane) * R;
-      for (int j = 0; j < R; ++j) {
-        const int col = col0 + j;
-        if (col >= it.cols) break;
-        const uint64_t id = (uint64_t)row * (uint64_t)it.cols + (uint64_t)col;
-        if (id < it.ray_begin || id >= it.ray_end) continue;
-        RayFwd r;
-        trace_collimated(it, sp, pc, row, col, id, inv_cols, inv_rows, r);
-        cnt.add(r.status);
-        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+  if (a < b) {
+    if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
+      const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+      uint32_t row = (uint32_t)(a / (uint64_t)it.cols);
+      uint32_t col = (uint32_t)(a - (uint64_t)row * (uint64_t)it.cols);
+      const uint32_t n = (uint32_t)(b - a);
+      if (!it.jitter) {
+        RowPatch rp;
+        rp.row = 0xffffffffu;
+        for (uint32_t j = 0; j < n; ++j) {
+          RayFwd r;
+          trace_collimated_row(it, ls, row, col, inv_cols, inv_rows, rp, r);
+          cnt.add(r.status, s_cnt);
+          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
+        }
+      } else {
+        for (uint32_t j = 0; j < n; ++j) {
+          RayFwd r;
+          trace_collimated(it, ls, row, col, a + j, inv_cols, inv_rows, r);
+          cnt.add(r.status, s_cnt);
+          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
+        }
       }
-    }
-  } else {
-    const uint64_t per_tile = (uint64_t)blockDim.x * (uint64_t)R;
-    for (int tile = t0; tile < t1; ++tile) {
-      const uint64_t base = it.ray_begin + (uint64_t)tile * per_tile + threadIdx.x;
-      for (int j = 0; j < R; ++j) {
-        const uint64_t id = base + (uint64_t)j * blockDim.x;
-        if (id >= it.ray_end) break;
+    } else if (KINDS & 2) {
+      for (uint64_t id = a; id < b; ++id) {
         RayFwd r;
-        trace_point(it, sp, pc, id, zmin, zmax, r);
-        cnt.add(r.status);
+        trace_point(it, ls, id, zmin, zmax, r);
+        cnt.add(r.status, s_cnt);
         if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
       }
     }
@@ -147,60 +150,70 @@ __device__ void run_tiles(const Item& it, const float4* sp, const Target& tg, in
   acc_flush<NU, DET>(acc, tg, bb);
 }
 
-template <int CAP, bool DET>
-__global__ void __launch_bounds__(256) k_forward(const __grid_constant__ Launch<CAP> L) {
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <int CAP, bool DET, int NU, int KINDS>
+__global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __grid_constant__ Launch<CAP> L) {
   int ii = 0;
   while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
   const Item& it = L.items[ii];
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* sp = reinterpret_cast<float4*>(smem);
-  const int np4 = it.nsu * it.nsv * 4;
-  for (int q = threadIdx.x; q < np4; q += blockDim.x) sp[q] = it.patch[q];
-  unsigned char* hist_raw = smem + (size_t)np4 * sizeof(float4);
+  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  unsigned char* hist_raw = smem + align16(lens_smem_bytes(it.nsu, it.nsv));
   const int ncell = it.ncol * it.nrow;
+  uint64_t a, b;
+  lane_range(it, L.warps, &a, &b);
   Target tg;
   tg.smem = it.smem_hist != 0;
   tg.ncol = it.ncol;
-  tg.sh_f = reinterpret_cast<float*>(hist_raw);
+  tg.sh_u = reinterpret_cast<unsigned int*>(hist_raw);
   tg.sh_q = reinterpret_cast<unsigned long long*>(hist_raw);
   tg.gl_f = it.E;
   tg.gl_q = it.Efix;
+  {
+    // 2^31 / (rays of this CTA x largest contribution of one ray), a power of two.
+    const uint64_t n = it.ray_end - it.ray_begin;
+    const uint64_t G = (uint64_t)(it.cta_end - it.cta_begin);
+    const uint64_t ci = (uint64_t)((int)blockIdx.x - it.cta_begin);
+    const float rays = (float)(n * (ci + 1) / G - n * ci / G) + 1.0f;
+    int e = 0;
+    frexpf(rays * it.omega0 * it.inv_area, &e);
+    tg.sh_scale = ldexpf(1.0f, 31 - e);
+  }
   if (tg.smem) {
     if constexpr (DET) {
       for (int q = threadIdx.x; q < ncell; q += blockDim.x) tg.sh_q[q] = 0ull;
     } else {
-      for (int q = threadIdx.x; q < ncell; q += blockDim.x) tg.sh_f[q] = 0.0f;
+      for (int q = threadIdx.x; q < ncell; q += blockDim.x) tg.sh_u[q] = 0u;
     }
   }
   __shared__ int s_bb[4];
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < 4) s_bb[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
-  __syncthreads();
-  const float zmin = it.zb[0], zmax = it.zb[1];
-  const int ci = (int)blockIdx.x - it.cta_begin, G = it.cta_end - it.cta_begin;
-  const int t0 = (int)((long long)it.tiles * ci / G), t1 = (int)((long long)it.tiles * (ci + 1) / G);
-  Counters cnt;
-#pragma unroll
-  for (int s = 0; s < FR_RAY_NCAUSES; ++s) cnt.n[s] = 0u;
+  build_lens_tables(it, ls);   // ends with __syncthreads
+  const float zmin = ls.zb[0], zmax = ls.zb[1];
+  RayCount cnt;
+  cnt.on_screen = 0u;
+  unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
   Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
-  switch (it.nu) {
-    case 1: run_tiles<1, DET>(it, sp, tg, t0, t1, zmin, zmax, cnt, bb); break;
-    case 3: run_tiles<3, DET>(it, sp, tg, t0, t1, zmin, zmax, cnt, bb); break;
-    default: run_tiles<5, DET>(it, sp, tg, t0, t1, zmin, zmax, cnt, bb); break;
-  }
-  cnt.reduce_into(s_cnt);
-  if (tg.smem && bb.imax >= 0) {
-    atomicMin(&s_bb[0], bb.imin);
-    atomicMax(&s_bb[1], bb.imax);
-    atomicMin(&s_bb[2], bb.jmin);
-    atomicMax(&s_bb[3], bb.jmax);
+  run_lane<NU, DET, KINDS>(it, ls, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
+  cnt.reduce_into(cnt_dst);
+  if (tg.smem) {
+    // Touched window: warp reductions, then one shared atomic per warp.
+    const int i0 = __reduce_min_sync(0xffffffffu, bb.imin), i1 = __reduce_max_sync(0xffffffffu, bb.imax);
+    const int j0 = __reduce_min_sync(0xffffffffu, bb.jmin), j1 = __reduce_max_sync(0xffffffffu, bb.jmax);
+    if ((threadIdx.x & 31) == 0 && i1 >= 0) {
+      atomicMin(&s_bb[0], i0);
+      atomicMax(&s_bb[1], i1);
+      atomicMin(&s_bb[2], j0);
+      atomicMax(&s_bb[3], j1);
+    }
   }
   __syncthreads();
   if (tg.smem && s_bb[1] >= 0) {
     // Flush the touched window of the privatised histogram.
-    const int nu = it.nu;
-    const int c0 = s_bb[0], c1 = s_bb[1] + nu - 1, r0 = s_bb[2], r1 = s_bb[3] + nu - 1;
+    const int c0 = s_bb[0], c1 = s_bb[1] + NU - 1, r0 = s_bb[2], r1 = s_bb[3] + NU - 1;
     const int wcols = c1 - c0 + 1, n = wcols * (r1 - r0 + 1);
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
       const int rr = r0 + q / wcols, cc = c0 + q % wcols;
@@ -209,37 +222,38 @@ __global__ void __launch_bounds__(256) k_forward(const __grid_constant__ Launch<
         const unsigned long long v = tg.sh_q[idx];
         if (v) atomicAdd(tg.gl_q + idx, v);
       } else {
-        const float v = tg.sh_f[idx];
-        if (v != 0.0f) atomicAdd(tg.gl_f + idx, v);
+        const unsigned int v = tg.sh_u[idx];
+        if (v) atomicAdd(tg.gl_f + idx, (float)v / tg.sh_scale);
       }
     }
   }
-  Counters::publish(s_cnt, it.stats);
+  RayCount::publish(s_cnt, it.stats);
 }
 
-// One thread per ray: the full record of rays [ray_begin, ray_end).
-__global__ void k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
+// The full record of every ray of [ray_begin, ray_end), one thread per ray.
+__global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  build_lens_tables(it, ls);
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t id = it.ray_begin + i;
   if (id >= it.ray_end) return;
-  Patch pc;
-  pc.k = -1;
-  pc.l = -1;
   RayFwd r;
   r.status = FR_RAY_ON_SCREEN;
+  r.k = r.l = -1;
   r.u = r.v = r.s = r.t = r.x = r.y = r.z = r.dx = r.dy = r.dz = 0.0f;
   r.tx = r.ty = r.tz = r.w = r.X = r.Y = r.tstar = 0.0f;
   r.iters = 0;
   if (it.kind == FR_SOURCE_COLLIMATED) {
-    const int row = (int)(id / (uint64_t)it.cols), col = (int)(id % (uint64_t)it.cols);
-    trace_collimated(it, it.patch, pc, row, col, id, 1.0f / (float)it.cols, 1.0f / (float)it.rows, r);
+    const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
+    trace_collimated(it, ls, row, col, id, 1.0f / (float)it.cols, 1.0f / (float)it.rows, r);
   } else {
-    trace_point(it, it.patch, pc, id, it.zb[0], it.zb[1], r);
+    trace_point(it, ls, id, ls.zb[0], ls.zb[1], r);
   }
   fr_ray_record rec;
   rec.status = r.status;
-  rec.span_i = pc.k >= 0 ? pc.k + 3 : -1;
-  rec.span_j = pc.l >= 0 ? pc.l + 3 : -1;
+  rec.span_i = r.k >= 0 ? r.k + 3 : -1;
+  rec.span_j = r.l >= 0 ? r.l + 3 : -1;
   rec.newton_iters = r.iters;
   rec.u = r.u;
   rec.v = r.v;
@@ -262,16 +276,37 @@ __global__ void k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
 }  // namespace
 
 size_t fwd_smem_bytes(const Item& it, bool det) {
-  size_t b = (size_t)it.nsu * it.nsv * 4 * sizeof(float4);
+  size_t b = (lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15;
   if (it.smem_hist) b += (size_t)it.ncol * it.nrow * (det ? 8 : 4);
   return b;
+}
+
+// The kernel variant for (deterministic, nu, kinds); KINDS as in run_lane.
+template <int CAP>
+using FwdKernel = void (*)(Launch<CAP>);
+
+template <int CAP, bool DET, int KINDS>
+FwdKernel<CAP> pick_nu(int nu) {
+  return nu == 1 ? k_forward<CAP, DET, 1, KINDS> : (nu == 3 ? k_forward<CAP, DET, 3, KINDS> : k_forward<CAP, DET, 5, KINDS>);
+}
+
+template <int CAP>
+FwdKernel<CAP> pick_forward(bool det, int nu, int kinds);
+template <>
+FwdKernel<1> pick_forward<1>(bool det, int nu, int kinds) {
+  if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
+  return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
+}
+template <>
+FwdKernel<kMaxItems> pick_forward<kMaxItems>(bool det, int nu, int) {
+  return det ? pick_nu<kMaxItems, true, 3>(nu) : pick_nu<kMaxItems, false, 3>(nu);
 }
 
 template <int CAP>
 cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
   const int threads = 32 * L.warps;
-  if (det) k_forward<CAP, true><<<grid, threads, smem, st>>>(L);
-  else k_forward<CAP, false><<<grid, threads, smem, st>>>(L);
+  const int kinds = L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2;
+  pick_forward<CAP>(det, L.items[0].nu, kinds)<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
 template cudaError_t launch_forward<1>(const Launch<1>&, int, size_t, bool, cudaStream_t);
@@ -282,19 +317,14 @@ cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int threads = 128;
   const unsigned int blocks = (unsigned int)((n + threads - 1) / threads);
-  k_debug<<<blocks, threads, 0, st>>>(it, out);
+  k_debug<<<blocks, threads, lens_smem_bytes(it.nsu, it.nsv), st>>>(it, out);
   return cudaGetLastError();
 }
 
-int forward_occupancy(int threads, size_t smem, bool det, bool batch) {
+int forward_occupancy(int threads, size_t smem, bool det, bool batch, int nu, int kinds) {
   int n = 0;
-  if (batch) {
-    if (det) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward<kMaxItems, true>, threads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward<kMaxItems, false>, threads, smem);
-  } else {
-    if (det) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward<1, true>, threads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward<1, false>, threads, smem);
-  }
+  if (batch) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_forward<kMaxItems>(det, nu, kinds), threads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_forward<1>(det, nu, kinds), threads, smem);
   return n;
 }
 
@@ -310,10 +340,14 @@ static cudaError_t allow_max_smem(K kernel, int optin) {
 
 cudaError_t configure_forward(int optin) {
   cudaError_t e;
-  if ((e = allow_max_smem(k_forward<1, false>, optin))) return e;
-  if ((e = allow_max_smem(k_forward<1, true>, optin))) return e;
-  if ((e = allow_max_smem(k_forward<kMaxItems, false>, optin))) return e;
-  return allow_max_smem(k_forward<kMaxItems, true>, optin);
+  if ((e = allow_max_smem(k_debug, optin))) return e;
+  for (int det = 0; det < 2; ++det)
+    for (int nu = 1; nu <= 5; nu += 2) {
+      for (int kinds = 1; kinds <= 2; ++kinds)
+        if ((e = allow_max_smem(pick_forward<1>(det != 0, nu, kinds), optin))) return e;
+      if ((e = allow_max_smem(pick_forward<kMaxItems>(det != 0, nu, 3), optin))) return e;
+    }
+  return cudaSuccess;
 }
 
 }  // namespace fr
