@@ -32,11 +32,16 @@ sys.path.insert(0, ROOT)
 METRIC = "rays/s per forward+adjoint step vs forward-only at stated error; % roofline"
 L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
 
-# Algorithmic work per ray, counted from the formulas the kernels evaluate
-# (FMA = 2 flops; +, -, *, exp2, sqrt, rsqrt, reciprocal = 1). The counts and
-# their breakdown are in the design doc.
-FLOPS_FWD_COLLIMATED = 185
-FLOPS_ADJ_COLLIMATED = 490
+# Algorithmic FP32 work per collimated ray, counted from the formulas the
+# kernels evaluate (FMA = 2 flops; +, -, *, exp2, rsqrt, reciprocal = 1):
+# forward = trace 62 + filter 46 + deposit 26; adjoint = trace 62 + filter 46
+# + reverse pass 161 + gradient moments 21 (breakdown in the design doc).
+FLOPS_FWD_COLLIMATED = 134
+FLOPS_ADJ_COLLIMATED = 290
+# DRAM bytes (read + write) per launch of each trace kernel on this workload,
+# from the ncu capture summarised in profiles/trace_kernels_collimated_2048x2048.md.
+# Set to None whenever the kernel changes after that capture.
+PROFILED_DRAM_BYTES = {"forward": 108032, "adjoint": 134656}
 
 
 def parse():
@@ -48,13 +53,6 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return p.parse_args()
-
-
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
 
 
 def peaks():
@@ -192,13 +190,12 @@ def run_reference(args, rank, world):
 
 def run_ours(args, rank, world, local):
     import torch
-    import torch.distributed as dist
     from paper_2302_12031_gb300 import api, step
+    from paper_2302_12031_gb300 import dist as D
     from paper_2302_12031_gb300 import workloads as W
 
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    D.init("nccl")
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
@@ -206,11 +203,6 @@ def run_ours(args, rank, world, local):
 
     def flush():
         flush_buf.zero_()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
 
     wl = W.config(2)
     n_rays = wl["n_rays"]
@@ -226,12 +218,10 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         flush()
         st.step()
-    barrier()
+    D.barrier(dev)
     step_ms, fwd_kernel_ms, adj_kernel_ms = [], [], []
-    outer = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     with ClockSampler(local) as clocks:
-        barrier()
-        total_ms = 0.0
+        D.barrier(dev)
         for _ in range(args.steps):
             flush()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -242,16 +232,9 @@ def run_ours(args, rank, world, local):
             step_ms.append(a.elapsed_time(b))
             fwd_kernel_ms.append(ev_f[0].elapsed_time(ev_f[1]))
             adj_kernel_ms.append(ev_a[0].elapsed_time(ev_a[1]))
-        barrier()
-    t_local = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t)
-    else:
-        t_max = t_local
-    ms_per_step = t_max / args.steps
-    value = world * n_rays * args.steps / (t_max * 1e-3)
+        D.barrier(dev)
+    value, t_max = D.replica_throughput(n_rays * args.steps, sum(step_ms) * 1e-3, dev)
+    ms_per_step = 1e3 * t_max / args.steps
 
     # --- forward only (prep + trace kernel through the C ABI)
     pb = st.problems[0]
@@ -262,7 +245,7 @@ def run_ours(args, rank, world, local):
         api.fr_trace_forward(h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS, None, E)
 
     f_ms = time_steps(graphed(fwd), args.steps, args.warmup, flush)
-    fwd_value = world * n_rays / (statistics.mean(f_ms) * 1e-3)
+    fwd_value, _ = D.replica_throughput(n_rays, statistics.mean(f_ms) * 1e-3, dev)
 
     # --- end to end through the public API: pinned host heights in, loss out
     P_host = torch.as_tensor(wl["lens"]["P"], dtype=torch.float32).reshape(-1).pin_memory()
@@ -278,7 +261,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.current_stream().synchronize()
         if k >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = world * n_rays / (statistics.mean(e2e_ms) * 1e-3)
+    e2e_value, _ = D.replica_throughput(n_rays, statistics.mean(e2e_ms) * 1e-3, dev)
 
     # --- roofline of the dominant kernel (the adjoint trace), timed live
     pk, pk_kind = peaks()
@@ -290,7 +273,8 @@ def run_ours(args, rank, world, local):
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak = fp32_peak_tflops(sm_count, pk.get("sm_max_mhz", 2070.0))
     roofline = {"bound": "alu", "kernel": "k_%s (trace)" % dominant, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": PROFILED_DRAM_BYTES.get(dominant),
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
                 "peak_note": "FP32 FMA peak %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock of %s peaks file)"
                              % (sm_count, pk.get("sm_max_mhz", 2070.0), pk_kind),
                 "kernel_ms": {"forward": fwd_k, "adjoint": adj_k}}
@@ -323,14 +307,15 @@ def run_ours(args, rank, world, local):
 
     if rank == 0:
         print(json.dumps(line), flush=True)
+    D.barrier(dev)
     if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
+        torch.distributed.destroy_process_group()
 
 
 def extra_workloads(args, flush, world):
     """Point source (16M rays) and the batched graph steps, fewer steps each."""
     import torch
+    from paper_2302_12031_gb300 import dist as D
     from paper_2302_12031_gb300 import step
     from paper_2302_12031_gb300 import workloads as W
     out = {}
@@ -340,9 +325,9 @@ def extra_workloads(args, flush, world):
         st = step.OptimStep(wls, lr=1e-3, graph=True)
         ms = time_steps(st.step, k, 2, flush)
         rays = st.n_rays
-        out[name] = {"rays_per_step": rays, "ms_per_step": statistics.mean(ms),
-                     "rays_per_s": world * rays / (statistics.mean(ms) * 1e-3),
-                     "steps_per_s": 1e3 / statistics.mean(ms), "lenses": len(st.problems)}
+        rays_per_s, t = D.replica_throughput(rays, statistics.mean(ms) * 1e-3)
+        out[name] = {"rays_per_step": rays, "ms_per_step": 1e3 * t, "rays_per_s": rays_per_s,
+                     "steps_per_s": 1.0 / t, "lenses": len(st.problems)}
         del st
         torch.cuda.empty_cache()
     return out
@@ -350,7 +335,8 @@ def extra_workloads(args, flush, world):
 
 def main():
     args = parse()
-    rank, world, local = dist_env()
+    from paper_2302_12031_gb300 import dist as D
+    rank, world, local = D.env()
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -275,7 +275,15 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 template <int CAP>
 fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o, bool adjoint,
                     cudaStream_t st) {
-  const bool det = o.deterministic != 0;
+  bool det = o.deterministic != 0;
+  // A forward whose histograms cannot live in shared memory deposits with
+  // global atomics; 64-bit integer reductions there are faster than float ones,
+  // so it runs the fixed-point (deterministic) kernel and converts at the end.
+  if (!adjoint && !det) {
+    bool any_smem = false;
+    for (auto& it : items) any_smem |= want_smem_hist(it, o, false);
+    det = !any_smem;
+  }
   const int warps = pick_warps(o, adjoint, items.size() == 1 ? items[0].kind : FR_SOURCE_POINT);
   // Workspace.
   size_t at = kHeaderBytes;

@@ -12,7 +12,7 @@ namespace fr {
 constexpr int kMaxCtrl = 32;              // control points per direction
 constexpr int kMaxSpans = kMaxCtrl - 3;   // knot spans per direction (degree 3)
 constexpr int kMaxItems = 64;             // lenses per batched launch
-constexpr int kLossBlocks = 120;          // fixed grid of the loss reduction
+constexpr int kLossBlocks = 64;           // fixed grid of the loss reduction
 
 // Device view of one lens problem: lens, source, screen, outputs and schedule.
 // Built on the host by the C ABI from the public descriptors.

@@ -9,8 +9,20 @@ namespace {
 
 // L = sum over interior pixels of (E - E_ref)^2; dL/dE = 2 (E - E_ref) there and
 // 0 on ghost pixels. A fixed grid of kLossBlocks blocks writes one partial sum
-// each; the last block to finish adds them in block order (bit-identical from
-// run to run) and re-arms the counter for the next launch.
+// each; the last block to finish adds them with a fixed-shape tree (the result
+// is bit-identical from run to run) and re-arms the counter for the next launch.
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? s_red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;   // valid in thread 0
+}
+
 __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ E, const float* __restrict__ Eref, int nx,
                                               int ny, int hx, int hy, int ncol, int nrow,
                                               double* __restrict__ partials, unsigned int* counter,
@@ -29,24 +41,24 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ E, const
     dLdE[q] = g;
   }
   __shared__ double s_red[8];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
-  __syncthreads();
   __shared__ bool s_last;
+  const double b = block_sum(acc, s_red);
   if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_red[w];
     partials[blockIdx.x] = b;
     __threadfence();
     s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) {
+  if (s_last) {
     __threadfence();
-    double total = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) total += ((volatile double*)partials)[b];
-    *loss = total;
-    *counter = 0u;
+    double v = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
+    __syncthreads();
+    const double total = block_sum(v, s_red);
+    if (threadIdx.x == 0) {
+      *loss = total;
+      *counter = 0u;
+    }
   }
 }
 
