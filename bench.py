@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--tune", action="store_true", help="autotune the trace kernels' schedule first")
     return p.parse_args()
 
 
@@ -211,8 +212,16 @@ def run_ours(args, rank, world, local):
     for e in ev_f + ev_a:
         e.record()                      # materialise the events before handing out their handles
     torch.cuda.synchronize()
-    st = step.OptimStep(wl, lr=1e-3, graph=True, options=api.make_options(events=ev_f),
-                        adj_options=api.make_options(events=ev_a))
+    sched_f, sched_a = {}, {}
+    if args.tune:
+        from paper_2302_12031_gb300 import autotune
+        pb = api.Problem(wl)
+        pick = lambda o: {k: getattr(o, k) for k in autotune.OPTION_FIELDS}
+        sched_f = pick(autotune.tune(pb, "forward", flush=flush))
+        sched_a = pick(autotune.tune(pb, "adjoint", flush=flush))
+        del pb
+    st = step.OptimStep(wl, lr=1e-3, graph=True, options=api.make_options(events=ev_f, **sched_f),
+                        adj_options=api.make_options(events=ev_a, **sched_a))
 
     # --- headline: forward + loss + adjoint + Adam, one graph replay per step
     for _ in range(args.warmup):
@@ -285,7 +294,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": wl["name"], "rays": n_rays, "control_net": "16x16", "bins": "128x128",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (256 MiB write)",
-                       "step": "graph: prep+forward, loss, prep+adjoint, Adam"},
+                       "step": "graph: prep+forward, loss, prep+adjoint, Adam",
+                       "schedule": {"forward": sched_f or "default", "adjoint": sched_a or "default"}},
             "forward_rays_per_s": fwd_value,
             "forward_ms": statistics.mean(f_ms),
             "roofline": roofline,
