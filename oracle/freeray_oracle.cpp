@@ -25,7 +25,14 @@
 //   Sec. 2.3   screen pixels, ghost pixels, Gaussian reconstruction filter
 //              (Eq. filter1dim) normalised over all pixels, irradiance sum
 //              I_ij = sum_k w_k F_ij(x_k), divided by the pixel area.
-//   Loss       squared L2 over the interior pixels, and its gradient dL/dE.
+//   Loss       squared L2 over the interior pixels, and its gradient dL/dE;
+//              the paper's loss (Sec. 2.5, Eq. pipelineLoss): the Frobenius norm of
+//              the difference of the sum-normalised images over sqrt(nx ny), and its
+//              gradient through both normalisations.
+//   Reparam.   control heights from unconstrained variables through tanh and the
+//              affine map onto (z_min, z_max), plus an offset f(P^x, P^y) taken at
+//              the Greville points (Sec. 2.4.2, Eqs. outputcorrection and
+//              outputcorrectionwfunc; spherical offsets of Table magndata).
 //   Gradient   dL/dP^z by forward-mode dual numbers carried through this same
 //              trace (an exact derivative of the code above), with the implicit
 //              function theorem at the FP64 root for the point source.
@@ -833,6 +840,101 @@ double or_loss_l2(const double* E, const double* E_ref, int32_t nx, int32_t ny, 
     }
   }
   return L;
+}
+
+// The paper's loss (Sec. 2.5): with I^ = I / sum(I) and I^_ref = I_ref / sum(I_ref)
+// over the nx x ny interior, L = ||I^ - I^_ref||_F / sqrt(nx ny). dLdE (extended
+// grid) gets dL/dI on the interior and 0 on ghost pixels. By the chain rule through
+// I^_kl = I_kl / S (S = sum I): dL/dI_ij = (g_ij - sum_kl g_kl I^_kl) / S, where
+// g = dL/dI^ = (I^ - I^_ref) / (sqrt(nx ny) ||I^ - I^_ref||_F).
+// Where the norm is 0 (images equal up to scale) the gradient is taken as 0.
+// Where S or sum(I_ref) is not positive the normalisation is undefined: the loss
+// is NaN and the gradient 0.
+double or_loss_frobenius(const double* E, const double* E_ref, int32_t nx, int32_t ny, int32_t nu_x, int32_t nu_y,
+                         double* dLdE) {
+  const int hx = (nu_x - 1) / 2, hy = (nu_y - 1) / 2;
+  const int ncol = nx + nu_x - 1, nrow = ny + nu_y - 1;
+  for (int c = 0; c < ncol * nrow; ++c) dLdE[c] = 0.0;
+  auto I = [&](int i, int j) { return E[(size_t)(j + hy) * ncol + (i + hx)]; };
+  double S = 0.0, Sref = 0.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      S += I(i, j);
+      Sref += E_ref[(size_t)j * nx + i];
+    }
+  if (!(S > 0.0) || !(Sref > 0.0)) return std::nan("");
+  std::vector<double> D((size_t)nx * ny);
+  double norm2 = 0.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double d = I(i, j) / S - E_ref[(size_t)j * nx + i] / Sref;
+      D[(size_t)j * nx + i] = d;
+      norm2 += d * d;
+    }
+  const double root_n = std::sqrt((double)nx * (double)ny);
+  const double norm = std::sqrt(norm2);
+  const double L = norm / root_n;
+  if (norm == 0.0) return L;
+  double gdot = 0.0;                        // sum_kl g_kl I^_kl
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) gdot += D[(size_t)j * nx + i] / (root_n * norm) * (I(i, j) / S);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double g = D[(size_t)j * nx + i] / (root_n * norm);
+      dLdE[(size_t)(j + hy) * ncol + (i + hx)] = (g - gdot) / S;
+    }
+  return L;
+}
+
+// Greville abscissae u*_i = (u_{i+1} + ... + u_{i+p}) / p, i = 0..n, of the clamped
+// uniform knot vector (Sec. 2.1, Farin sec. 8.6).
+void or_greville(int32_t n, int32_t p, double* out) {
+  const std::vector<double> U = clamped_uniform_knots(n, p);
+  for (int i = 0; i <= n; ++i) {
+    double s = 0.0;
+    for (int k = i + 1; k <= i + p; ++k) s += U[k];
+    out[i] = s / p;
+  }
+}
+
+// Offset f(P^x_ij, P^y_ij) at the control points, P^x_ij = (2u*_i - 1) r_x and
+// P^y_ij = (2v*_j - 1) r_y (Greville construction, Sec. 2.1). f is the spherical
+// cap of Table magndata: f = c + R - sign(R) sqrt(R^2 - x^2 - y^2), a sphere of
+// radius |R| through (0, 0, c); R = 0 gives the constant c. Returns -1 if a
+// control point lies outside the sphere's footprint (x^2 + y^2 > R^2).
+int32_t or_offset_spherical(int32_t n1, int32_t n2, int32_t p, int32_t q, double rx, double ry, double c, double R,
+                            double* out) {
+  std::vector<double> gu(n1 + 1), gv(n2 + 1);
+  or_greville(n1, p, gu.data());
+  or_greville(n2, q, gv.data());
+  for (int i = 0; i <= n1; ++i)
+    for (int j = 0; j <= n2; ++j) {
+      const double x = (2.0 * gu[i] - 1.0) * rx, y = (2.0 * gv[j] - 1.0) * ry;
+      double f = c;
+      if (R != 0.0) {
+        const double r2 = R * R - x * x - y * y;
+        if (r2 < 0.0) return -1;
+        f = c + R - (R > 0.0 ? 1.0 : -1.0) * std::sqrt(r2);
+      }
+      out[(size_t)i * (n2 + 1) + j] = f;
+    }
+  return 0;
+}
+
+// Control heights from unconstrained variables (Sec. 2.4.2): P_k = offset_k +
+// z_min + (tanh(theta_k) + 1)(z_max - z_min)/2; offset may be NULL (= 0).
+void or_reparam_tanh(const double* theta, const double* offset, int32_t n, double z_min, double z_max, double* P) {
+  for (int k = 0; k < n; ++k)
+    P[k] = (offset ? offset[k] : 0.0) + z_min + 0.5 * (std::tanh(theta[k]) + 1.0) * (z_max - z_min);
+}
+
+// Its adjoint: dL/dtheta_k = dL/dP_k (z_max - z_min)/2 (1 - tanh^2(theta_k)).
+void or_reparam_tanh_adjoint(const double* theta, const double* dLdP, int32_t n, double z_min, double z_max,
+                             double* dLdtheta) {
+  for (int k = 0; k < n; ++k) {
+    const double t = std::tanh(theta[k]);
+    dLdtheta[k] = dLdP[k] * 0.5 * (z_max - z_min) * (1.0 - t * t);
+  }
 }
 
 // Adam (Kingma & Ba, Algorithm 1), step number `step` counted from 1.

@@ -88,6 +88,14 @@ def lib():
         L.or_loss_l2.restype = C.c_double
         L.or_adam_step.argtypes = [dp, dp, dp, dp, C.c_int32, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int32]
+        L.or_loss_frobenius.argtypes = [dp, dp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, dp]
+        L.or_loss_frobenius.restype = C.c_double
+        L.or_greville.argtypes = [C.c_int32, C.c_int32, dp]
+        L.or_offset_spherical.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, dp]
+        L.or_offset_spherical.restype = C.c_int32
+        L.or_reparam_tanh.argtypes = [dp, dp, C.c_int32, C.c_double, C.c_double, dp]
+        L.or_reparam_tanh_adjoint.argtypes = [dp, dp, C.c_int32, C.c_double, C.c_double, dp]
         _lib = L
     return _lib
 
@@ -188,6 +196,47 @@ def loss_l2(wl, E):
     d = np.zeros_like(E)
     L = lib().or_loss_l2(_dptr(E), _dptr(Eref), tgt["nx"], tgt["ny"], tgt["nu_x"], tgt["nu_y"], _dptr(d))
     return L, d
+
+
+def loss_frobenius(wl, E, E_ref=None):
+    """(L, dL/dE on the extended grid) of the paper's normalised Frobenius loss."""
+    tgt = wl["target"]
+    E = _f64(E)
+    Eref = _f64(wl["E_ref"] if E_ref is None else E_ref)
+    d = np.zeros_like(E)
+    L = lib().or_loss_frobenius(_dptr(E), _dptr(Eref), tgt["nx"], tgt["ny"], tgt["nu_x"], tgt["nu_y"], _dptr(d))
+    return L, d
+
+
+def greville(n, p):
+    out = np.zeros(n + 1)
+    lib().or_greville(n, p, _dptr(out))
+    return out
+
+
+def offset_spherical(n1, n2, p, q, rx, ry, c, R):
+    """Offsets f(P^x, P^y) at the control points, (n1+1) x (n2+1); None if the
+    sphere does not cover every control point."""
+    out = np.zeros((n1 + 1, n2 + 1))
+    if lib().or_offset_spherical(n1, n2, p, q, rx, ry, c, R, _dptr(out)) != 0:
+        return None
+    return out
+
+
+def reparam_tanh(theta, z_min, z_max, offset=None):
+    theta = _f64(theta)
+    P = np.zeros_like(theta)
+    off = None if offset is None else _f64(offset)
+    lib().or_reparam_tanh(_dptr(theta), None if off is None else _dptr(off), theta.size, z_min, z_max, _dptr(P))
+    return P
+
+
+def reparam_tanh_adjoint(theta, dLdP, z_min, z_max):
+    theta = _f64(theta)
+    g = _f64(dLdP)
+    out = np.zeros_like(theta)
+    lib().or_reparam_tanh_adjoint(_dptr(theta), _dptr(g), theta.size, z_min, z_max, _dptr(out))
+    return out
 
 
 def adam_step(theta, m, v, g, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
