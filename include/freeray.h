@@ -213,6 +213,51 @@ fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t n
 fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* g, int64_t n,
                        float lr, float beta1, float beta2, float eps, int32_t* step, void* stream);
 
+/* The paper's loss (Sec. 2.5, Eq. pipelineLoss): with the interior images
+ * normalised to unit sum, I^ = E / sum(E) and I^_ref = E_ref / sum(E_ref),
+ * L = ||I^ - I^_ref||_F / sqrt(nx ny) into *loss_out (device double), and dL/dE
+ * through both normalisations into dLdE_out (device, extended grid; 0 on ghost
+ * pixels). E is on the extended grid, E_ref on the interior ny x nx grid.
+ * Where ||I^ - I^_ref|| = 0 the gradient is 0. Where sum(E) <= 0 or
+ * sum(E_ref) <= 0 the normalisation is undefined: *loss_out is NaN and the
+ * gradient 0 (reported on the device, not by the return code). Sums are
+ * reduced in a fixed order (bit-identical run to run). Needs no scratch. */
+fr_status fr_loss_frobenius(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny,
+                            int32_t nu_x, int32_t nu_y, double* loss_out, float* dLdE_out, void* stream);
+
+/* Control heights from unconstrained variables (Sec. 2.4.2, Eqs.
+ * outputcorrection and outputcorrectionwfunc):
+ *   P[k] = offset[k] + z_min + (tanh(theta[k]) + 1) (z_max - z_min) / 2,
+ * theta, offset and P_out device arrays of n floats; offset may be NULL (0).
+ * Requires z_min < z_max, both finite. P_out may alias offset. */
+fr_status fr_reparam_tanh(fr_handle* h, const float* theta, const float* offset, int64_t n, float z_min,
+                          float z_max, float* P_out, void* stream);
+
+/* Its adjoint: dLdtheta_out[k] = dLdP[k] (z_max - z_min)/2 (1 - tanh^2(theta[k]))
+ * (device arrays of n floats). */
+fr_status fr_reparam_tanh_adjoint(fr_handle* h, const float* theta, const float* dLdP, int64_t n, float z_min,
+                                  float z_max, float* dLdtheta_out, void* stream);
+
+/* Offsets f(P^x_ij, P^y_ij) of eq. outputcorrectionwfunc at the control points
+ * of `lens` (its n1, n2, p, q, rx, ry; ctrl_z is not read), with P^x_ij =
+ * (2u*_i - 1) r_x and P^y_ij = (2v*_j - 1) r_y at the Greville abscissae u*, v*
+ * (Sec. 2.1). f is the spherical cap of Table magndata,
+ *   f(x, y) = c + R - sign(R) sqrt(R^2 - x^2 - y^2),
+ * a sphere of radius |R| through (0, 0, c); R = 0 gives the constant c.
+ * offset_out: device, (n1+1)*(n2+1) floats in the control-height layout.
+ * FR_ERR_INVALID_ARG if the sphere does not reach every control point
+ * (R^2 < r_x^2 + r_y^2). */
+fr_status fr_offset_spherical(fr_handle* h, const fr_lens_desc* lens, float c, float R, float* offset_out,
+                              void* stream);
+
+/* Adam (as fr_adam_step) on the unconstrained variables theta, taking
+ * dL/dtheta from dL/dP (device, n) through the tanh map of fr_reparam_tanh, and
+ * then writing P_out from the updated theta, in one kernel. theta, m, v are
+ * updated in place; offset may be NULL. */
+fr_status fr_adam_step_tanh(fr_handle* h, float* theta, float* m, float* v, const float* dLdP, const float* offset,
+                            int64_t n, float lr, float beta1, float beta2, float eps, float z_min, float z_max,
+                            int32_t* step, float* P_out, void* stream);
+
 /* Batched forward / adjoint: every item (its own lens, source, screen, rays and
  * buffers) in one launch of the trace kernel. Same semantics per item as
  * fr_trace_forward / fr_trace_adjoint over all rays of the item. n_items <= 64;

@@ -676,6 +676,50 @@ void gradient_impl(const Problem& pb, uint64_t begin, uint64_t count, const doub
     for (int c = 0; c < nctrl; ++c) dLdP[c] += part[k][c];
 }
 
+// Directional derivatives dE = (dE/dP^z) dP_k of the irradiance for n_dirs
+// directions dP_k (forward mode: the same per-ray dual numbers as the gradient,
+// contracted with each direction instead of with dL/dE).
+template <int NT>
+void tangent_impl(const Problem& pb, uint64_t begin, uint64_t count, const double* dP, int n_dirs, double* dE,
+                  int nthreads) {
+  const int nctrl = (pb.d.n1 + 1) * (pb.d.n2 + 1);
+  const size_t ncell = (size_t)pb.ncol * pb.nrow;
+  const int nthr = resolve_threads(nthreads);
+  std::vector<std::vector<double>> part(nthr, std::vector<double>(ncell * n_dirs, 0.0));
+  parallel_rays(begin, count, nthr, [&](int k, uint64_t a, uint64_t b) {
+    std::vector<double>& e = part[k];
+    std::vector<double> local((size_t)n_dirs * NT);
+    for (uint64_t id = a; id < b; ++id) {
+      RayState<double> r0;
+      trace_ray<double>(pb, id, -1, -1, 0.0, &r0);
+      if (r0.status != OR_OK) continue;
+      const int si = r0.span_i - pb.d.p, sj = r0.span_j - pb.d.q;
+      bool any = false;
+      for (int q = 0; q < n_dirs; ++q)
+        for (int c = 0; c < NT; ++c) {
+          const int a2 = c / (pb.d.q + 1), b2 = c % (pb.d.q + 1);
+          const double v = a2 <= pb.d.p ? dP[(size_t)q * nctrl + (si + a2) * (pb.d.n2 + 1) + (sj + b2)] : 0.0;
+          local[(size_t)q * NT + c] = v;
+          any = any || v != 0.0;
+        }
+      if (!any) continue;
+      RayState<Dual<NT>> r;
+      trace_ray<Dual<NT>>(pb, id, si, sj, r0.t, &r);
+      if (r.status != OR_OK) continue;
+      splat<Dual<NT>>(pb, r, [&](int i, int j, const Dual<NT>& ed) {
+        for (int q = 0; q < n_dirs; ++q) {
+          double v = 0.0;
+          for (int c = 0; c < NT; ++c) v += ed.d[c] * local[(size_t)q * NT + c];
+          e[(size_t)q * ncell + (size_t)j * pb.ncol + i] += v;
+        }
+      });
+    }
+  });
+  for (size_t c = 0; c < ncell * n_dirs; ++c) dE[c] = 0.0;
+  for (int k = 0; k < nthr; ++k)
+    for (size_t c = 0; c < ncell * n_dirs; ++c) dE[c] += part[k][c];
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------
@@ -819,6 +863,19 @@ int32_t or_trace_gradient(const or_problem* prob, uint64_t begin, uint64_t count
   const int ndir = (pb.d.p + 1) * (pb.d.q + 1);
   if (ndir <= 16) gradient_impl<16>(pb, begin, count, dLdE, dLdP, nthreads);
   else if (ndir <= 36) gradient_impl<36>(pb, begin, count, dLdE, dLdP, nthreads);
+  else return -1;
+  return 0;
+}
+
+// dE_k = (dE/dP^z) dP_k over rays [begin, begin+count) for n_dirs directions
+// (dP: n_dirs x (n1+1)(n2+1); dE: n_dirs extended grids).
+int32_t or_trace_tangent(const or_problem* prob, uint64_t begin, uint64_t count, const double* dP, int32_t n_dirs,
+                         double* dE, int32_t nthreads) {
+  Problem pb;
+  if (!make_problem(prob, &pb) || n_dirs < 1) return -1;
+  const int ndir = (pb.d.p + 1) * (pb.d.q + 1);
+  if (ndir <= 16) tangent_impl<16>(pb, begin, count, dP, n_dirs, dE, nthreads);
+  else if (ndir <= 36) tangent_impl<36>(pb, begin, count, dP, n_dirs, dE, nthreads);
   else return -1;
   return 0;
 }

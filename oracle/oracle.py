@@ -84,6 +84,8 @@ def lib():
         L.or_trace_forward.restype = C.c_int32
         L.or_trace_gradient.argtypes = [pp, C.c_uint64, C.c_uint64, dp, dp, C.c_int32]
         L.or_trace_gradient.restype = C.c_int32
+        L.or_trace_tangent.argtypes = [pp, C.c_uint64, C.c_uint64, dp, C.c_int32, dp, C.c_int32]
+        L.or_trace_tangent.restype = C.c_int32
         L.or_loss_l2.argtypes = [dp, dp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, dp]
         L.or_loss_l2.restype = C.c_double
         L.or_adam_step.argtypes = [dp, dp, dp, dp, C.c_int32, C.c_double, C.c_double, C.c_double,
@@ -186,6 +188,24 @@ def trace_gradient(wl, dLdE, P=None, begin=0, count=None, nthreads=0):
     if rc != 0:
         raise ValueError("oracle rejected the problem")
     return out
+
+
+def trace_tangent(wl, dP, P=None, begin=0, count=None, nthreads=0):
+    """Directional derivatives (dE/dP^z) dP_k of the irradiance: dP of shape
+    (n_dirs, n1+1, n2+1) (or one direction (n1+1, n2+1)); returns
+    (n_dirs, rows, cols) extended grids (or one grid)."""
+    pb = OracleProblem(wl, P)
+    begin, count = _range(wl, begin, count)
+    d = _f64(dP)
+    single = d.ndim == 2
+    if single:
+        d = d[None]
+    assert d.shape[1:] == pb.P.shape
+    out = np.zeros((d.shape[0],) + pb.ext_shape)
+    rc = lib().or_trace_tangent(pb.ptr(), begin, count, _dptr(d), d.shape[0], _dptr(out), nthreads)
+    if rc != 0:
+        raise ValueError("oracle rejected the problem")
+    return out[0] if single else out
 
 
 def loss_l2(wl, E):

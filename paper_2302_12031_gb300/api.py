@@ -94,6 +94,17 @@ _SIGNATURES = {
                              C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_adam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p, C.c_void_p]),
+    "fr_loss_frobenius": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fr_reparam_tanh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,
+                                  C.c_void_p, C.c_void_p]),
+    "fr_reparam_tanh_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,
+                                          C.c_void_p, C.c_void_p]),
+    "fr_offset_spherical": (C.c_int, [C.c_void_p, C.POINTER(LensDesc), C.c_float, C.c_float, C.c_void_p,
+                                      C.c_void_p]),
+    "fr_adam_step_tanh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_trace_batch_forward": (C.c_int, [C.c_void_p, C.POINTER(BatchItem), C.c_int32, C.POINTER(Options),
                                          C.c_void_p]),
     "fr_trace_batch_adjoint": (C.c_int, [C.c_void_p, C.POINTER(BatchItem), C.c_int32, C.POINTER(Options),
@@ -214,6 +225,31 @@ def fr_loss_l2(h, E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, stream=None)
 def fr_adam_step(h, P, m, v, g, n, lr, beta1, beta2, eps, step, stream=None):
     h.check(lib().fr_adam_step(h.ptr, _ptr(P), _ptr(m), _ptr(v), _ptr(g), n, lr, beta1, beta2, eps, _ptr(step),
                                _stream(stream)))
+
+
+def fr_loss_frobenius(h, E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, stream=None):
+    h.check(lib().fr_loss_frobenius(h.ptr, _ptr(E), _ptr(E_ref), nx, ny, nu_x, nu_y, _ptr(loss_out),
+                                    _ptr(dLdE_out), _stream(stream)))
+
+
+def fr_reparam_tanh(h, theta, offset, n, z_min, z_max, P_out, stream=None):
+    h.check(lib().fr_reparam_tanh(h.ptr, _ptr(theta), _ptr(offset), n, z_min, z_max, _ptr(P_out),
+                                  _stream(stream)))
+
+
+def fr_reparam_tanh_adjoint(h, theta, dLdP, n, z_min, z_max, dLdtheta_out, stream=None):
+    h.check(lib().fr_reparam_tanh_adjoint(h.ptr, _ptr(theta), _ptr(dLdP), n, z_min, z_max, _ptr(dLdtheta_out),
+                                          _stream(stream)))
+
+
+def fr_offset_spherical(h, lens, c, R, offset_out, stream=None):
+    h.check(lib().fr_offset_spherical(h.ptr, C.byref(lens), c, R, _ptr(offset_out), _stream(stream)))
+
+
+def fr_adam_step_tanh(h, theta, m, v, dLdP, offset, n, lr, beta1, beta2, eps, z_min, z_max, step, P_out,
+                      stream=None):
+    h.check(lib().fr_adam_step_tanh(h.ptr, _ptr(theta), _ptr(m), _ptr(v), _ptr(dLdP), _ptr(offset), n, lr, beta1,
+                                    beta2, eps, z_min, z_max, _ptr(step), _ptr(P_out), _stream(stream)))
 
 
 def fr_trace_batch_forward(h, items, options=None, stream=None):

@@ -503,6 +503,85 @@ fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* 
   return FR_OK;
 }
 
+fr_status fr_loss_frobenius(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny, int32_t nu_x,
+                            int32_t nu_y, double* loss_out, float* dLdE_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || nu_x < 1 || nu_y < 1 || nu_x % 2 == 0 || nu_y % 2 == 0)
+    return set_error(h, FR_ERR_INVALID_ARG, "bad grid sizes");
+  cudaError_t e = fr::launch_loss_frobenius(E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "Frobenius loss kernel");
+  return FR_OK;
+}
+
+static fr_status check_range(fr_handle* h, int64_t n, float z_min, float z_max) {
+  if (n < 0) return set_error(h, FR_ERR_INVALID_ARG, "n < 0");
+  if (!finite(z_min) || !finite(z_max) || !(z_min < z_max))
+    return set_error(h, FR_ERR_INVALID_ARG, "need finite z_min < z_max");
+  return FR_OK;
+}
+
+fr_status fr_reparam_tanh(fr_handle* h, const float* theta, const float* offset, int64_t n, float z_min,
+                          float z_max, float* P_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!theta || !P_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  fr_status s = check_range(h, n, z_min, z_max);
+  if (s != FR_OK) return s;
+  cudaError_t e = fr::launch_reparam_tanh(theta, offset, n, z_min, z_max, P_out, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "reparametrisation kernel");
+  return FR_OK;
+}
+
+fr_status fr_reparam_tanh_adjoint(fr_handle* h, const float* theta, const float* dLdP, int64_t n, float z_min,
+                                  float z_max, float* dLdtheta_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!theta || !dLdP || !dLdtheta_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  fr_status s = check_range(h, n, z_min, z_max);
+  if (s != FR_OK) return s;
+  cudaError_t e = fr::launch_reparam_tanh_adjoint(theta, dLdP, n, z_min, z_max, dLdtheta_out, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "reparametrisation adjoint kernel");
+  return FR_OK;
+}
+
+fr_status fr_offset_spherical(fr_handle* h, const fr_lens_desc* lens, float c, float R, float* offset_out,
+                              void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!lens || !offset_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  if (lens->p != 3 || lens->q != 3) return set_error(h, FR_ERR_UNSUPPORTED, "only degrees p = q = 3");
+  if (lens->n1 < 3 || lens->n2 < 3 || lens->n1 >= fr::kMaxCtrl || lens->n2 >= fr::kMaxCtrl)
+    return set_error(h, FR_ERR_INVALID_ARG, "control net must be 4x4 .. %dx%d", fr::kMaxCtrl, fr::kMaxCtrl);
+  if (!(lens->rx > 0.0f) || !(lens->ry > 0.0f) || !finite(lens->rx) || !finite(lens->ry) || !finite(c) ||
+      !finite(R))
+    return set_error(h, FR_ERR_INVALID_ARG, "bad lens size or offset parameters");
+  const double rx = lens->rx, ry = lens->ry, Rd = R;
+  if (Rd != 0.0 && Rd * Rd < rx * rx + ry * ry)
+    return set_error(h, FR_ERR_INVALID_ARG, "sphere radius %g does not cover the control net", (double)R);
+  cudaError_t e = fr::launch_offset_spherical(lens->n1, lens->n2, lens->p, lens->q, rx, ry, c, Rd, offset_out,
+                                              as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "offset kernel");
+  return FR_OK;
+}
+
+fr_status fr_adam_step_tanh(fr_handle* h, float* theta, float* m, float* v, const float* dLdP, const float* offset,
+                            int64_t n, float lr, float beta1, float beta2, float eps, float z_min, float z_max,
+                            int32_t* step, float* P_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!theta || !m || !v || !dLdP || !step || !P_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  fr_status s = check_range(h, n, z_min, z_max);
+  if (s != FR_OK) return s;
+  if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) || !finite(lr))
+    return set_error(h, FR_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+  cudaError_t e = fr::launch_adam_tanh(theta, m, v, dLdP, offset, n, lr, beta1, beta2, eps, z_min, z_max, step, P_out,
+                                       as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "tanh Adam kernel");
+  return FR_OK;
+}
+
 static fr_status batch(fr_handle* h, const fr_batch_item* in, int32_t n_items, const fr_options* options,
                        void* stream, bool adjoint) {
   if (!h) return FR_ERR_INVALID_ARG;

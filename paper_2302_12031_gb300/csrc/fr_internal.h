@@ -89,6 +89,17 @@ cudaError_t launch_loss(const float* E, const float* Eref, int nx, int ny, int n
 cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1,
                         float b2, float eps, int32_t* step, cudaStream_t st);
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);
+cudaError_t launch_loss_frobenius(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y,
+                                  double* loss, float* dLdE, cudaStream_t st);
+cudaError_t launch_reparam_tanh(const float* theta, const float* offset, int64_t n, float z_min, float z_max,
+                                float* P, cudaStream_t st);
+cudaError_t launch_reparam_tanh_adjoint(const float* theta, const float* dLdP, int64_t n, float z_min,
+                                        float z_max, float* out, cudaStream_t st);
+cudaError_t launch_adam_tanh(float* theta, float* m, float* v, const float* dLdP, const float* offset, int64_t n,
+                             float lr, float b1, float b2, float eps, float z_min, float z_max, int32_t* step,
+                             float* P, cudaStream_t st);
+cudaError_t launch_offset_spherical(int n1, int n2, int p, int q, double rx, double ry, double c, double R,
+                                    float* out, cudaStream_t st);
 cudaError_t configure_forward(int optin);
 cudaError_t configure_adjoint(int optin);
 

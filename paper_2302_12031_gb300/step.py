@@ -1,11 +1,19 @@
 """The optimisation step (rows a1-a10) for one lens or a batch of lenses.
 
-One step = forward trace -> squared-L2 loss and dL/dE -> recompute adjoint ->
-Adam on the control heights, all on one stream. With graph=True the step is
-captured once into a CUDA graph and every later step is one graph replay.
-The control heights, Adam moments and the step counter of all lenses live in
-flat device buffers, so one Adam launch updates every lens.
+One step = forward trace -> loss and dL/dE -> recompute adjoint -> Adam, all on
+one stream. With graph=True the step is captured once into a CUDA graph and
+every later step is one graph replay. The control heights, Adam moments and the
+step counter of all lenses live in flat device buffers, so one Adam launch
+updates every lens.
+
+loss="l2" is the squared L2 distance to the target; loss="frobenius" the
+paper's normalised Frobenius loss (Sec. 2.5). With reparam=dict(z_min=...,
+z_max=..., offset=...) Adam runs on unconstrained variables theta and the
+control heights are P = offset + z_min + (tanh(theta) + 1)(z_max - z_min)/2
+(Sec. 2.4.2); offset is None, a ("sphere", c, R) cap of Table magndata, or an
+array per lens. The fused Adam kernel writes P from the new theta.
 """
+import numpy as np
 import torch
 
 from . import api
@@ -13,11 +21,15 @@ from . import api
 
 class OptimStep:
     def __init__(self, workloads, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, options=None, graph=True,
-                 device="cuda", adj_options=None):
+                 device="cuda", adj_options=None, loss="l2", reparam=None):
         """`options` apply to both traces unless `adj_options` is given for the adjoint
         (e.g. to record timing events around each trace kernel separately)."""
         if isinstance(workloads, dict):
             workloads = [workloads]
+        if loss not in ("l2", "frobenius"):
+            raise ValueError("loss must be 'l2' or 'frobenius'")
+        self.loss_kind = loss
+        self.reparam = reparam
         self.h = api.default_handle()
         self.lr, self.betas, self.eps = lr, betas, eps
         self.options = options
@@ -48,11 +60,36 @@ class OptimStep:
         for pb, sz in zip(self.problems, sizes):
             self.grads.append(self.g[at:at + sz].view(pb.ctrl_shape))
             at += sz
+        self.theta = self.offset = None
+        if reparam is not None:
+            self._init_reparam(workloads, sizes, device)
         self.n_rays = sum(pb.n_rays for pb in self.problems)
         self.batched = len(self.problems) > 1
         self.graph = None
         if graph:
             self._capture()
+
+    def _init_reparam(self, workloads, sizes, device):
+        zmin, zmax = float(self.reparam["z_min"]), float(self.reparam["z_max"])
+        if not zmin < zmax:
+            raise ValueError("need z_min < z_max")
+        off = self.reparam.get("offset")
+        self.offset = torch.zeros(self.n_params, dtype=torch.float32, device=device)
+        at = 0
+        for k, (pb, sz) in enumerate(zip(self.problems, sizes)):
+            view = self.offset[at:at + sz]
+            if isinstance(off, tuple) and off[0] == "sphere":
+                api.fr_offset_spherical(self.h, pb.lens, float(off[1]), float(off[2]), view)
+            elif off is not None:
+                arr = off[k] if isinstance(off, list) else off
+                view.copy_(torch.as_tensor(np.asarray(arr), dtype=torch.float32).reshape(-1))
+            at += sz
+        # theta from the starting heights where they lie inside the range, else its edge
+        y = (self.P - self.offset - zmin) / (0.5 * (zmax - zmin)) - 1.0
+        self.theta = torch.atanh(y.clamp(-1 + 1e-6, 1 - 1e-6)).contiguous()
+        if self.reparam.get("theta0") is not None:
+            self.theta.copy_(torch.as_tensor(self.reparam["theta0"], dtype=torch.float32).reshape(-1))
+        api.fr_reparam_tanh(self.h, self.theta, self.offset, self.n_params, zmin, zmax, self.P)
 
     def _forward(self):
         if self.batched:
@@ -64,8 +101,9 @@ class OptimStep:
                                  self.options, self.E[0])
 
     def _loss(self):
+        fn = api.fr_loss_l2 if self.loss_kind == "l2" else api.fr_loss_frobenius
         for pb, E, Er, d, L in zip(self.problems, self.E, self.E_ref, self.dLdE, self.loss):
-            api.fr_loss_l2(self.h, E, Er, pb.nx, pb.ny, pb.nu_x, pb.nu_y, L, d)
+            fn(self.h, E, Er, pb.nx, pb.ny, pb.nu_x, pb.nu_y, L, d)
 
     def _adjoint(self):
         if self.batched:
@@ -77,8 +115,13 @@ class OptimStep:
                                  self.adj_options, self.dLdE[0], self.grads[0])
 
     def _adam(self):
-        api.fr_adam_step(self.h, self.P, self.m, self.v, self.g, self.n_params, self.lr, self.betas[0],
-                         self.betas[1], self.eps, self.step_count)
+        if self.theta is None:
+            api.fr_adam_step(self.h, self.P, self.m, self.v, self.g, self.n_params, self.lr, self.betas[0],
+                             self.betas[1], self.eps, self.step_count)
+        else:
+            api.fr_adam_step_tanh(self.h, self.theta, self.m, self.v, self.g, self.offset, self.n_params, self.lr,
+                                  self.betas[0], self.betas[1], self.eps, float(self.reparam["z_min"]),
+                                  float(self.reparam["z_max"]), self.step_count, self.P)
 
     def eager_step(self):
         self._forward()
@@ -87,7 +130,8 @@ class OptimStep:
         self._adam()
 
     def _capture(self):
-        saved = [t.clone() for t in (self.P, self.m, self.v, self.step_count)]
+        state = self._state()
+        saved = [t.clone() for t in state]
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -98,9 +142,13 @@ class OptimStep:
         with torch.cuda.graph(self.graph):
             self.eager_step()
         torch.cuda.synchronize()
-        for t, v in zip((self.P, self.m, self.v, self.step_count), saved):
+        for t, v in zip(state, saved):
             t.copy_(v)
         torch.cuda.synchronize()
+
+    def _state(self):
+        st = [self.P, self.m, self.v, self.step_count]
+        return st + ([self.theta] if self.theta is not None else [])
 
     def step(self):
         if self.graph is not None:
