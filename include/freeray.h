@@ -191,6 +191,20 @@ fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_sour
                            uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
                            const float* dLdE, float* dLdP_out, fr_stats* stats_out, void* stream);
 
+/* Forward mode (the irradiance derivatives of Sec. 3.1): for n_dirs (1..32)
+ * directions dP_k in control-height space, dP device n_dirs x (n1+1)*(n2+1)
+ * (direction k at dP + k*(n1+1)*(n2+1), control-height layout), writes (or
+ * adds) the directional derivatives dE_k = sum_ij (dE/dP^z_ij) dP_k,ij of the
+ * irradiance over rays [ray_begin, ray_begin+ray_count) to dE_out (device,
+ * n_dirs extended grids, grid k at dE_out + k*(nx+nu_x-1)*(ny+nu_y-1)). The
+ * derivative map of one control point is dP = its unit vector. Same lens,
+ * source, screen and rays as fr_trace_forward; deposits use float atomics
+ * (not bit-reproducible; options.deterministic is ignored). */
+fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                           const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
+                           uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
+                           const float* dP, int32_t n_dirs, float* dE_out, fr_stats* stats_out, void* stream);
+
 /* Per-ray records of rays [ray_begin, ray_begin+ray_count) (device array of
  * ray_count records). Same path as fr_trace_forward. */
 fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,

@@ -90,6 +90,9 @@ _SIGNATURES = {
     "fr_trace_debug": (C.c_int, [C.c_void_p, C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
                                  C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
                                  C.c_void_p, C.c_void_p]),
+    "fr_trace_tangent": (C.c_int, [C.c_void_p, C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
+                                   C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
+                                   C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_loss_l2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                              C.c_void_p, C.c_void_p, C.c_void_p]),
     "fr_adam_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
@@ -215,6 +218,13 @@ def fr_trace_adjoint(h, lens, source, target, n_rays, seed, ray_begin, ray_count
 def fr_trace_debug(h, lens, source, target, n_rays, seed, ray_begin, ray_count, options, out, stream=None):
     h.check(lib().fr_trace_debug(h.ptr, C.byref(lens), C.byref(source), C.byref(target), n_rays, seed,
                                  ray_begin, ray_count, _opts(options), _ptr(out), _stream(stream)))
+
+
+def fr_trace_tangent(h, lens, source, target, n_rays, seed, ray_begin, ray_count, options, dP, n_dirs, dE_out,
+                     stats_out=None, stream=None):
+    h.check(lib().fr_trace_tangent(h.ptr, C.byref(lens), C.byref(source), C.byref(target), n_rays, seed,
+                                   ray_begin, ray_count, _opts(options), _ptr(dP), n_dirs, _ptr(dE_out),
+                                   _ptr(stats_out), _stream(stream)))
 
 
 def fr_loss_l2(h, E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, stream=None):
@@ -363,6 +373,19 @@ class Problem:
         fr_trace_adjoint(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                          options, dLdE.contiguous(), dLdP, stats)
         return dLdP
+
+    def tangent(self, dP, options=None, ray_begin=0, ray_count=ALL_RAYS, dE=None, stats=None, h=None):
+        """Directional derivatives (dE/dP^z) dP: dP of shape (n_dirs, n1+1, n2+1) or
+        (n1+1, n2+1); returns (n_dirs,) + ext_shape (or ext_shape)."""
+        h = h or default_handle()
+        dP = torch.as_tensor(dP, dtype=torch.float32, device=self.device).contiguous()
+        single = dP.dim() == 2
+        n_dirs = 1 if single else dP.shape[0]
+        if dE is None:
+            dE = torch.empty((n_dirs,) + self.ext_shape, dtype=torch.float32, device=self.device)
+        fr_trace_tangent(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
+                         options, dP, n_dirs, dE, stats)
+        return dE[0] if single else dE
 
     def debug(self, ray_begin=0, ray_count=None, options=None, h=None):
         """Per-ray records as a dict of CPU numpy arrays (one per field)."""

@@ -402,6 +402,7 @@ fr_status fr_create(fr_handle** out) {
     e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   if (e == cudaSuccess) e = fr::configure_forward(h->smem_optin);
   if (e == cudaSuccess) e = fr::configure_adjoint(h->smem_optin);
+  if (e == cudaSuccess) e = fr::configure_tangent(h->smem_optin);
   if (e != cudaSuccess) {
     delete h;
     return cuda_error(nullptr, e, "fr_create");
@@ -456,6 +457,45 @@ fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_sour
   items[0].dLdP = dLdP_out;
   items[0].stats = stats_out;
   return run_trace<1>(h, items, o, true, as_stream(stream));
+}
+
+fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
+                           const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
+                           uint64_t ray_count, const fr_options* options, const float* dP, int32_t n_dirs,
+                           float* dE_out, fr_stats* stats_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  const fr_options o = defaults(options);
+  if (!dP || !dE_out) return set_error(h, FR_ERR_INVALID_ARG, "dP or dE_out is null");
+  if (n_dirs < 1 || n_dirs > 32) return set_error(h, FR_ERR_INVALID_ARG, "n_dirs must be 1..32");
+  Item it;
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
+  if (s != FR_OK) return s;
+  it.stats = stats_out;
+  const cudaStream_t st = as_stream(stream);
+  if (!o.accumulate)
+    FR_CUDA(h, cudaMemsetAsync(dE_out, 0, (size_t)n_dirs * it.ncol * it.nrow * sizeof(float), st), "memset");
+  const int warps = o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 8) : 8;
+  schedule_item(&it, warps, o);
+  const size_t smem = fr::tan_smem_bytes(it);
+  const auto key = std::make_tuple(2, 0, 0, it.nu, 0, warps * 32, smem);
+  auto found = h->occupancy.find(key);
+  int occ;
+  if (found != h->occupancy.end()) {
+    occ = found->second;
+  } else {
+    occ = fr::tangent_occupancy(warps * 32, smem, it.nu);
+    h->occupancy[key] = occ;
+  }
+  if (occ <= 0 || smem + 1024 > (size_t)h->smem_optin)
+    return set_error(h, FR_ERR_UNSUPPORTED, "tangent kernel does not fit on an SM (%zu B shared)", smem);
+  const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
+  it.cta_begin = 0;
+  it.cta_end = std::min(std::max(1, h->sm_count * per_sm), it.max_ctas);
+  if (it.cta_end <= 0) return FR_OK;   // no rays
+  cudaError_t e = fr::launch_tangent(it, warps, it.cta_end, smem, dP, n_dirs, dE_out, st);
+  if (e != cudaSuccess) return cuda_error(h, e, "tangent kernel");
+  return FR_OK;
 }
 
 fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,

@@ -543,14 +543,15 @@ __device__ __forceinline__ bool footprint(const Item& it, float X, float Y, Foot
 // slopes, from which dL/dP^z_{k+a,l+b} = zeta N_a N_b + Zs_bar N'_a N_b
 // + Zt_bar N_a N'_b.
 // ---------------------------------------------------------------------------
-template <int NU, bool COLL>
-__device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, const RayFwd& r, const Foot<NU>& f,
-                                            const float (&G)[NU][NU], float* zeta, float* Zs_bar, float* Zt_bar) {
-  // Filter: F_a = f_a / S, dF_a/dX = (f'_a - F_a S') / S, f'_a = -2 alpha delta_a e_a / w.
-  // With nu = 1 the normalised filter is identically 1 on its pixel: dF = 0.
+// Normalised filter values on one footprint, F_a = f_a / S, and their
+// derivatives with respect to the screen hit, dF_a/dX = (f'_a - F_a S') / S with
+// f'_a = -2 alpha delta_a e_a / w. With nu = 1 the normalised filter is
+// identically 1 on its pixel: dF = 0.
+template <int NU>
+__device__ __forceinline__ void filter_grad(const Item& it, const Foot<NU>& f, float (&Fx)[NU], float (&Fy)[NU],
+                                            float (&gxa)[NU], float (&gya)[NU]) {
   const float ln2 = 0.69314718055994531f;
   const float kx = -2.0f * (it.ax * ln2) * it.inv_wx, ky = -2.0f * (it.ay * ln2) * it.inv_wy;
-  float Fx[NU], Fy[NU], gxa[NU], gya[NU];
   float Spx = 0.0f, Spy = 0.0f;
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
@@ -567,6 +568,13 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, 
     gxa[a] = NU == 1 ? 0.0f : (gxa[a] - Fx[a] * Spx) * f.rsx;
     gya[a] = NU == 1 ? 0.0f : (gya[a] - Fy[a] * Spy) * f.rsy;
   }
+}
+
+template <int NU, bool COLL>
+__device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, const RayFwd& r, const Foot<NU>& f,
+                                            const float (&G)[NU][NU], float* zeta, float* Zs_bar, float* Zt_bar) {
+  float Fx[NU], Fy[NU], gxa[NU], gya[NU];
+  filter_grad<NU>(it, f, Fx, Fy, gxa, gya);
   float wbar = 0.0f, Xs = 0.0f, Ys = 0.0f;
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
@@ -627,6 +635,45 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, 
   const float tbar = Xbar * r.dx + Ybar * r.dy + zbar * r.dz +
                      *Zs_bar * fmaf(Zss, dsdt, Zst * dtdt) + *Zt_bar * fmaf(Zst, dsdt, Ztt * dtdt);
   *zeta = -tbar / r.gp;
+}
+
+// ---------------------------------------------------------------------------
+// Forward mode of one ray (Sec. 3.1 derivative maps): the tangents of the screen
+// hit and of the weight for a tangent of the freeform hit (hx, hy, hz) and of
+// its slopes in patch coordinates (dZs, dZt), through the exit refraction,
+// Schlick and the propagation. Transposes the chain of ray_reverse.
+// ---------------------------------------------------------------------------
+struct RayTan {
+  float dX, dY, dw;
+};
+
+template <bool COLL>
+__device__ __forceinline__ RayTan ray_tangent(const Item& it, const RayFwd& r, float hx, float hy, float hz,
+                                              float dZs, float dZt) {
+  // n = m / |m|, m = (-Z_x, -Z_y, 1): dn = (dm - n (n.dm)) / |m|.
+  const float dZx = dZs * it.ku, dZy = dZt * it.kv;
+  const float ndm = -fmaf(r.nx, dZx, r.ny * dZy);
+  const float dnx = fmaf(-r.nx, ndm, -dZx) * r.invL;
+  const float dny = fmaf(-r.ny, ndm, -dZy) * r.invL;
+  const float dnz = -r.nz * ndm * r.invL;
+  // c = d.n, cs = sqrt(1 - eta^2 (1 - c^2)), a = eta c - cs, t = eta d - a n.
+  const float dc = COLL ? dnz : fmaf(r.dx, dnx, fmaf(r.dy, dny, r.dz * dnz));
+  const float eta = it.n_glass;
+  const float dcs = eta * eta * r.c * dc * fast_rcp(r.cs);
+  const float da = fmaf(eta, dc, -dcs);
+  const float dtx = fmaf(-da, r.nx, -r.a * dnx);
+  const float dty = fmaf(-da, r.ny, -r.a * dny);
+  const float dtz = fmaf(-da, r.nz, -r.a * dnz);
+  // w = omega0 T1 T2, T2 = (1-R0)(1-(1-cs)^5).
+  const float om = 1.0f - r.cs;
+  const float om2 = om * om;
+  RayTan o;
+  o.dw = it.omega0 * r.T1 * (1.0f - it.R0) * 5.0f * om2 * om2 * dcs;
+  // X = x + lam t_x, lam = (z_s - z) / t_z.
+  const float dlam = -fmaf(r.lam, dtz, hz) * fast_rcp(r.tz);
+  o.dX = fmaf(dlam, r.tx, fmaf(r.lam, dtx, hx));
+  o.dY = fmaf(dlam, r.ty, fmaf(r.lam, dty, hy));
+  return o;
 }
 
 // Ray counts by cause (FR_RAY_*): a per-thread count of deposited rays and

@@ -100,6 +100,11 @@ cudaError_t launch_adam_tanh(float* theta, float* m, float* v, const float* dLdP
                              float* P, cudaStream_t st);
 cudaError_t launch_offset_spherical(int n1, int n2, int p, int q, double rx, double ry, double c, double R,
                                     float* out, cudaStream_t st);
+size_t tan_smem_bytes(const Item& it);
+cudaError_t launch_tangent(const Item& it, int warps, int grid, size_t smem, const float* dP, int n_dirs, float* dE,
+                           cudaStream_t st);
+int tangent_occupancy(int threads, size_t smem, int nu);
+cudaError_t configure_tangent(int optin);
 cudaError_t configure_forward(int optin);
 cudaError_t configure_adjoint(int optin);
 

@@ -76,13 +76,16 @@ __global__ void __cluster_dims__(kObjCluster, 1, 1) __launch_bounds__(kObjThread
   }
   cluster_sum<2>(s, s_warp, s_sums);
   const bool ok = s[0] > 0.0 && s[1] > 0.0;
-  const double iS = ok ? 1.0 / s[0] : 0.0, iSr = ok ? 1.0 / s[1] : 0.0;
+  // I^ and I^_ref by correctly rounded division (not by a reciprocal): images
+  // equal up to a power-of-two scale then give D = 0 exactly, where the norm's
+  // gradient would otherwise point along rounding noise.
+  const double S = ok ? s[0] : 1.0, Sr = ok ? s[1] : 1.0;
 
   double d2[2] = {0.0, 0.0};          // sum D^2, sum D I^
   for (int k = tid; k < n; k += nthr) {
     const int j = k / nx, i = k - j * nx;
-    const double I = (double)E[(size_t)(j + hy) * ncol + (i + hx)] * iS;
-    const double D = I - (double)Eref[k] * iSr;
+    const double I = (double)E[(size_t)(j + hy) * ncol + (i + hx)] / S;
+    const double D = I - (double)Eref[k] / Sr;
     d2[0] = fma(D, D, d2[0]);
     d2[1] = fma(D, I, d2[1]);
   }
@@ -97,9 +100,9 @@ __global__ void __cluster_dims__(kObjCluster, 1, 1) __launch_bounds__(kObjThread
     const int i = col - hx, j = r - hy;
     float g = 0.0f;
     if (c != 0.0 && i >= 0 && i < nx && j >= 0 && j < ny) {
-      const double I = (double)E[q] * iS;
-      const double D = I - (double)Eref[(size_t)j * nx + i] * iSr;
-      g = (float)((c * D - gdot) * iS);
+      const double I = (double)E[q] / S;
+      const double D = I - (double)Eref[(size_t)j * nx + i] / Sr;
+      g = (float)((c * D - gdot) / S);
     }
     dLdE[q] = g;
   }

@@ -1,0 +1,164 @@
+// Forward-mode trace kernel: directional derivatives (dE/dP^z) dP_k of the
+// irradiance for a few directions dP_k at once — for one control point, the
+// derivative maps of Sec. 3.1.
+//
+// Each CTA builds the lens tables (as the forward kernel) and a bit mask per
+// knot-span patch of the directions that move one of its 16 control points.
+// Every lane traces an equal run of consecutive ray ids; a ray whose patch no
+// direction moves stops after the trace. For the others, the tangents of the
+// hit height and slopes, sum_ab N_a N_b dP, sum_ab N'_a N_b dP and
+// sum_ab N_a N'_b dP (for a point source also the hit's shift along the ray by
+// the implicit function theorem), go through ray_tangent, and
+//   dE_ij += (dw F_ij + w (dF_ij/dX dX + dF_ij/dY dY)) / (w_x w_y)
+// is added to the nu x nu footprint of direction k with global atomics.
+#include "fr_device.cuh"
+
+namespace fr {
+namespace {
+
+template <int NU>
+__global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item it, int warps,
+                                                    const float* __restrict__ dP, int n_dirs,
+                                                    float* __restrict__ dE) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15));
+  __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  const int nctrl = it.ncu * it.ncv;
+  for (int p = threadIdx.x; p < it.nsu * it.nsv; p += blockDim.x) {
+    const int k = p / it.nsv, l = p - k * it.nsv;
+    uint32_t m = 0u;
+    for (int q = 0; q < n_dirs; ++q) {
+      const float* P = dP + (size_t)q * nctrl + k * it.ncv + l;
+      bool any = false;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) any |= __ldg(P + a * it.ncv + b) != 0.0f;
+      if (any) m |= 1u << q;
+    }
+    s_mask[p] = m;
+  }
+  build_lens_tables(it, ls);   // ends with __syncthreads
+
+  const size_t cells = (size_t)it.ncol * it.nrow;
+  const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+  const bool coll = it.kind == FR_SOURCE_COLLIMATED;
+  RayCount cnt{0u};
+  unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+  uint64_t a0, a1;
+  lane_range(it, warps, &a0, &a1);
+  for (uint64_t id = a0; id < a1; ++id) {
+    RayFwd r;
+    if (coll) {
+      const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
+      trace_collimated(it, ls, row, col, id, inv_cols, inv_rows, r);
+    } else {
+      trace_point(it, ls, id, ls.zb[0], ls.zb[1], r);
+    }
+    cnt.add(r.status, cnt_dst);
+    if (r.status != FR_RAY_ON_SCREEN) continue;
+    uint32_t m = s_mask[r.k * it.nsv + r.l];
+    if (m == 0u) continue;
+    Foot<NU> f;
+    if (!footprint<NU>(it, r.X, r.Y, f)) continue;
+    float Nu[4], dNu[4], Nv[4], dNv[4];
+    basis_eval(ls.bu + r.k * 4, r.s, Nu, dNu);
+    basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+    float Fx[NU], Fy[NU], gx[NU], gy[NU];
+    filter_grad<NU>(it, f, Fx, Fy, gx, gy);
+    // Point source: the slopes' change along the ray (second derivatives).
+    float slope_s = 0.0f, slope_t = 0.0f, inv_gp = 0.0f;
+    if (!coll) {
+      float Zss, Zst, Ztt;
+      patch_eval2(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Zss, &Zst, &Ztt);
+      const float dsdt = r.dx * (0.5f / it.rx) * (float)it.nsu;
+      const float dtdt = r.dy * (0.5f / it.ry) * (float)it.nsv;
+      slope_s = fmaf(Zss, dsdt, Zst * dtdt);
+      slope_t = fmaf(Zst, dsdt, Ztt * dtdt);
+      inv_gp = 1.0f / r.gp;
+    }
+    const float K = r.w * it.inv_area;
+    while (m) {
+      const int q = __ffs(m) - 1;
+      m &= m - 1u;
+      const float* P = dP + (size_t)q * nctrl + r.k * it.ncv + r.l;
+      float dZ = 0.0f, dZs = 0.0f, dZt = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        float c = 0.0f, ct = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float v = __ldg(P + a * it.ncv + b);
+          c = fmaf(Nv[b], v, c);
+          ct = fmaf(dNv[b], v, ct);
+        }
+        dZ = fmaf(Nu[a], c, dZ);
+        dZs = fmaf(dNu[a], c, dZs);
+        dZt = fmaf(Nu[a], ct, dZt);
+      }
+      RayTan tg;
+      if (coll) {
+        tg = ray_tangent<true>(it, r, 0.0f, 0.0f, dZ, dZs, dZt);
+      } else {
+        // f(t*, P) = 0: dt* = -dZ / f'(t*); the hit moves along the ray.
+        const float dt = -dZ * inv_gp;
+        tg = ray_tangent<false>(it, r, r.dx * dt, r.dy * dt, r.dz * dt, fmaf(slope_s, dt, dZs),
+                                fmaf(slope_t, dt, dZt));
+      }
+      const float cw = tg.dw * it.inv_area, cx = K * tg.dX, cy = K * tg.dY;
+      float* base = dE + (size_t)q * cells + (size_t)f.je * it.ncol + f.ie;
+#pragma unroll
+      for (int b = 0; b < NU; ++b) {
+        const float rb = cw * Fy[b], sb = cx * Fy[b], tb = cy * gy[b];
+#pragma unroll
+        for (int a = 0; a < NU; ++a) {
+          const float v = fmaf(rb, Fx[a], fmaf(sb, gx[a], tb * Fx[a]));
+          if (v != 0.0f) atomicAdd(base + b * it.ncol + a, v);
+        }
+      }
+    }
+  }
+  cnt.reduce_into(cnt_dst);
+  __syncthreads();
+  RayCount::publish(s_cnt, it.stats);
+}
+
+using TanKernel = void (*)(Item, int, const float*, int, float*);
+
+TanKernel pick_tangent(int nu) {
+  return nu == 1 ? k_tangent<1> : (nu == 3 ? k_tangent<3> : k_tangent<5>);
+}
+
+}  // namespace
+
+size_t tan_smem_bytes(const Item& it) {
+  return ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15) + (size_t)it.nsu * it.nsv * 4;
+}
+
+cudaError_t launch_tangent(const Item& it, int warps, int grid, size_t smem, const float* dP, int n_dirs, float* dE,
+                           cudaStream_t st) {
+  pick_tangent(it.nu)<<<grid, warps * 32, smem, st>>>(it, warps, dP, n_dirs, dE);
+  return cudaGetLastError();
+}
+
+int tangent_occupancy(int threads, size_t smem, int nu) {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_tangent(nu), threads, smem);
+  return n;
+}
+
+cudaError_t configure_tangent(int optin) {
+  for (int nu = 1; nu <= 5; nu += 2) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, pick_tangent(nu));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(pick_tangent(nu), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)a.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fr

@@ -40,11 +40,13 @@ def test_frobenius_loss_matches_oracle(nx, ny, nu):
     E = torch.zeros(ny + nu - 1, nx + nu - 1)
     h = (nu - 1) // 2
     E[h:h + ny, h:h + nx] = torch.rand(ny, nx, generator=g)
-    E[0, :] += 3.0                                         # ghost values never enter the loss
+    if nu > 1:
+        E[0, :] += 3.0                                     # ghost values never enter the loss
     L, d = _frob_gpu(E.cuda(), Eref.cuda(), nx, ny, nu)
     L_or, d_or = O.loss_frobenius(_wl(nx, ny, nu, Eref.double().numpy()), E.double().numpy())
     if nx * ny == 1:
-        assert L == 0.0 and np.all(d == 0)
+        # one pixel: both normalised images are exactly 1
+        assert L_or == 0.0 and L == 0.0 and np.all(d == 0)
         return
     assert abs(L - L_or) <= 1e-10 * L_or
     assert np.max(np.abs(d - d_or)) <= 1e-6 * np.max(np.abs(d_or))
