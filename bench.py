@@ -325,8 +325,8 @@ def run_ours(args, rank, world, local):
 def extra_workloads(args, flush, world):
     """Point source (16M rays) and the batched graph steps, fewer steps each."""
     import torch
+    from paper_2302_12031_gb300 import api, step
     from paper_2302_12031_gb300 import dist as D
-    from paper_2302_12031_gb300 import step
     from paper_2302_12031_gb300 import workloads as W
     out = {}
     k = max(3, args.steps // 4)
@@ -340,6 +340,39 @@ def extra_workloads(args, flush, world):
                      "steps_per_s": 1.0 / t, "lenses": len(st.problems)}
         del st
         torch.cuda.empty_cache()
+    # the paper's objective: normalised Frobenius loss, tanh-reparametrised heights
+    # over a spherical offset (Table magndata, magnification 3)
+    wl = W.config(2)
+    st = step.OptimStep(wl, lr=1e-3, graph=True, loss="frobenius",
+                        reparam=dict(z_min=-0.05, z_max=0.05, offset=("sphere", 0.0, 8.0)))
+    ms = time_steps(st.step, k, 2, flush)
+    rays_per_s, t = D.replica_throughput(st.n_rays, statistics.mean(ms) * 1e-3)
+    out["frobenius_tanh_step_2048x2048"] = {"rays_per_step": st.n_rays, "ms_per_step": 1e3 * t,
+                                            "rays_per_s": rays_per_s}
+    pb = st.problems[0]
+    h = api.default_handle()
+    E = st.E[0]
+    loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    dLdE = torch.empty_like(E)
+    Eref = st.E_ref[0]
+    for name, fn in (("l2", api.fr_loss_l2), ("frobenius", api.fr_loss_frobenius)):
+        call = graphed(lambda: fn(h, E, Eref, pb.nx, pb.ny, pb.nu_x, pb.nu_y, loss, dLdE))
+        out.setdefault("loss_kernel_us_128x128", {})[name] = 1e3 * statistics.mean(time_steps(call, k, 2, flush))
+    del st
+    # derivative maps (Sec. 3.1): flat lens, collimated 2048^2 rays, 16x16 net
+    wl["lens"]["P"][:] = 0.0
+    pb = api.Problem(wl)
+    ncu_, ncv_ = pb.ctrl_shape
+    one = torch.zeros((1, ncu_, ncv_), device="cuda")
+    one[0, ncu_ // 2, ncv_ // 2] = 1.0
+    dense = torch.randn((4, ncu_, ncv_), generator=torch.Generator(device="cpu").manual_seed(1)).cuda()
+    for name, dP in (("derivative_map_1_control_point", one), ("derivative_maps_4_dense_directions", dense)):
+        dE = torch.empty((dP.shape[0],) + pb.ext_shape, device="cuda")
+        call = graphed(lambda: api.fr_trace_tangent(h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0,
+                                                    api.ALL_RAYS, None, dP, dP.shape[0], dE))
+        ms = time_steps(call, k, 2, flush)
+        rays_per_s, t = D.replica_throughput(pb.n_rays, statistics.mean(ms) * 1e-3)
+        out[name] = {"rays": pb.n_rays, "directions": dP.shape[0], "ms": 1e3 * t, "rays_per_s": rays_per_s}
     return out
 
 

@@ -32,7 +32,7 @@ namespace {
 using fr::Item;
 
 constexpr size_t kAlign = 256;
-constexpr size_t kHeaderBytes = 2048;   // loss partials and counter at the start of the workspace
+constexpr size_t kHeaderBytes = kAlign;   // reserved at the start of the workspace
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -105,7 +105,6 @@ fr_status ensure_workspace(fr_handle* h, size_t bytes, cudaStream_t st) {
   const size_t want = std::max<size_t>(bytes, 1 << 20);
   FR_CUDA(h, cudaMalloc(&h->ws, want), "cudaMalloc(workspace)");
   h->ws_bytes = want;
-  FR_CUDA(h, cudaMemset(h->ws, 0, kHeaderBytes), "cudaMemset(workspace header)");
   return FR_OK;
 }
 
@@ -520,12 +519,7 @@ fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t n
   if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
   if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || nu_x < 1 || nu_y < 1 || nu_x % 2 == 0 || nu_y % 2 == 0)
     return set_error(h, FR_ERR_INVALID_ARG, "bad grid sizes");
-  fr_status s = ensure_workspace(h, kHeaderBytes, as_stream(stream));
-  if (s != FR_OK) return s;
-  double* partials = reinterpret_cast<double*>(h->ws);
-  unsigned int* counter = reinterpret_cast<unsigned int*>(h->ws + fr::kLossBlocks * sizeof(double));
-  cudaError_t e = fr::launch_loss(E, E_ref, nx, ny, nu_x, nu_y, partials, counter, loss_out, dLdE_out,
-                                  as_stream(stream));
+  cudaError_t e = fr::launch_loss_l2(E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, as_stream(stream));
   if (e != cudaSuccess) return cuda_error(h, e, "loss kernel");
   return FR_OK;
 }

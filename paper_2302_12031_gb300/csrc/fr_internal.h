@@ -12,7 +12,6 @@ namespace fr {
 constexpr int kMaxCtrl = 32;              // control points per direction
 constexpr int kMaxSpans = kMaxCtrl - 3;   // knot spans per direction (degree 3)
 constexpr int kMaxItems = 64;             // lenses per batched launch
-constexpr int kLossBlocks = 64;           // fixed grid of the loss reduction
 
 // Device view of one lens problem: lens, source, screen, outputs and schedule.
 // Built on the host by the C ABI from the public descriptors.
@@ -83,9 +82,8 @@ cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st);
 cudaError_t launch_fix_to_float(const unsigned long long* q, float* out, size_t n, float inv_scale,
                                 int accumulate, cudaStream_t st);
 cudaError_t launch_absmax(const float* x, size_t n, float* out, cudaStream_t st);
-cudaError_t launch_loss(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y,
-                        double* partials, unsigned int* counter, double* loss, float* dLdE,
-                        cudaStream_t st);
+cudaError_t launch_loss_l2(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y, double* loss,
+                           float* dLdE, cudaStream_t st);
 cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1,
                         float b2, float eps, int32_t* step, cudaStream_t st);
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);

@@ -1,66 +1,11 @@
-// Small kernels of the step: squared-L2 loss and dL/dE (row a8), max |dL/dE|
-// for the deterministic adjoint, fixed point -> float, and Adam (row a10).
+// Small kernels of the step: max |dL/dE| for the deterministic adjoint, fixed
+// point -> float, and Adam (row a10).
 #include <algorithm>
 
 #include "fr_internal.h"
 
 namespace fr {
 namespace {
-
-// L = sum over interior pixels of (E - E_ref)^2; dL/dE = 2 (E - E_ref) there and
-// 0 on ghost pixels. A fixed grid of kLossBlocks blocks writes one partial sum
-// each; the last block to finish adds them with a fixed-shape tree (the result
-// is bit-identical from run to run) and re-arms the counter for the next launch.
-__device__ __forceinline__ double block_sum(double v, double* s_red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = threadIdx.x < (blockDim.x >> 5) ? s_red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  }
-  return t;   // valid in thread 0
-}
-
-__global__ void __launch_bounds__(256) k_loss(const float* __restrict__ E, const float* __restrict__ Eref, int nx,
-                                              int ny, int hx, int hy, int ncol, int nrow,
-                                              double* __restrict__ partials, unsigned int* counter,
-                                              double* __restrict__ loss, float* __restrict__ dLdE) {
-  double acc = 0.0;
-  const int n = ncol * nrow;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const int r = q / ncol, c = q - r * ncol;
-    const int i = c - hx, j = r - hy;
-    float g = 0.0f;
-    if (i >= 0 && i < nx && j >= 0 && j < ny) {
-      const float d = E[q] - Eref[j * nx + i];
-      acc += (double)d * (double)d;
-      g = 2.0f * d;
-    }
-    dLdE[q] = g;
-  }
-  __shared__ double s_red[8];
-  __shared__ bool s_last;
-  const double b = block_sum(acc, s_red);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = b;
-    __threadfence();
-    s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    double v = 0.0;
-    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) v += __ldcg(partials + q);
-    __syncthreads();
-    const double total = block_sum(v, s_red);
-    if (threadIdx.x == 0) {
-      *loss = total;
-      *counter = 0u;
-    }
-  }
-}
 
 // max |x| into *out (out must start at 0); non-negative floats order like their bits.
 __global__ void k_absmax(const float* __restrict__ x, size_t n, float* out) {
@@ -102,14 +47,6 @@ __global__ void __launch_bounds__(1024) k_adam(float* __restrict__ P, float* __r
 }
 
 }  // namespace
-
-cudaError_t launch_loss(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y, double* partials,
-                        unsigned int* counter, double* loss, float* dLdE, cudaStream_t st) {
-  const int ncol = nx + nu_x - 1, nrow = ny + nu_y - 1;
-  k_loss<<<kLossBlocks, 256, 0, st>>>(E, Eref, nx, ny, (nu_x - 1) / 2, (nu_y - 1) / 2, ncol, nrow, partials,
-                                      counter, loss, dLdE);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_absmax(const float* x, size_t n, float* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), st);

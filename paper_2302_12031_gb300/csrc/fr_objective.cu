@@ -1,8 +1,9 @@
-// The paper's objective and parametrisation around the trace:
-//  - the normalised Frobenius loss and its gradient (Sec. 2.5, Eq. pipelineLoss),
-//    one launch of one thread-block cluster whose CTAs reduce through
-//    distributed shared memory in a fixed order (bit-identical run to run, no
-//    atomics, no counters, no scratch memory);
+// The objective and parametrisation around the trace:
+//  - the squared L2 loss (row a8) and the paper's normalised Frobenius loss
+//    (Sec. 2.5, Eq. pipelineLoss) with their gradients, each one launch of one
+//    thread-block cluster whose CTAs reduce through distributed shared memory
+//    in a fixed order (bit-identical run to run, no atomics, no counters, no
+//    scratch memory);
 //  - control heights from unconstrained variables through tanh onto
 //    (z_min, z_max) plus an offset f(P^x, P^y) (Sec. 2.4.2, Eqs. outputcorrection
 //    and outputcorrectionwfunc), its adjoint, the spherical offsets of Table
@@ -18,96 +19,219 @@ namespace fr {
 namespace {
 
 constexpr int kObjCluster = 8;      // CTAs of the loss cluster (portable cluster size)
-constexpr int kObjThreads = 512;
+constexpr int kObjThreads = 1024;
+constexpr int kObjUnroll = 4;       // loads in flight per thread and loop trip
 
-// Sums NV doubles over the cluster: a fixed xor tree in each warp, then over
-// the warps of the CTA, then over the CTAs in rank order through distributed
-// shared memory. Every thread of the cluster returns the same totals in v.
-// s_cta is this call's own slot (it is read by the other CTAs after the
-// cluster barrier, so a later call must use another slot, and the kernel must
-// pass one more cluster barrier before it exits).
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the sums below
+// take each thread's FP32 partial sum through an FP32 xor tree within the warp
+// and only then go to FP64: one warp adds the warps' sums, one thread per CTA
+// adds the CTAs' sums in rank order through distributed shared memory. The
+// order is fixed: the totals are bit-identical run to run. On return s_tot
+// holds the totals (valid after the __syncthreads at the end). s_cta is this
+// call's own slot: the other CTAs read it after the cluster barrier, so a later
+// call must use another, and the kernel must pass one more cluster barrier
+// before it exits.
 template <int NV>
-__device__ __forceinline__ void cluster_sum(double (&v)[NV], double* s_warp, double* s_cta) {
+__device__ __forceinline__ void cluster_sum(const float (&v)[NV], double* s_warp, double* s_cta, double* s_tot) {
   cg::cluster_group cl = cg::this_cluster();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) s_warp[warp * NV + k] = x;
+    float x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) s_warp[warp * NV + k] = (double)x;
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double x = lane < (int)(blockDim.x >> 5) ? s_warp[lane * NV + k] : 0.0;
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (lane == 0) s_cta[k] = x;
     }
   }
   cl.sync();
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = 0.0;
-    for (unsigned r = 0; r < cl.num_blocks(); ++r) t += *cl.map_shared_rank(s_cta + k, r);
-    v[k] = t;
+    for (int k = 0; k < NV; ++k) {
+      double t = 0.0;
+      for (unsigned r = 0; r < cl.num_blocks(); ++r) t += *cl.map_shared_rank(s_cta + k, r);
+      s_tot[k] = t;
+    }
   }
+  __syncthreads();
+}
+
+// A product e * r with r = rh + rl (two floats), kept as the unevaluated sum
+// hi + lo: hi = e rh rounded, lo = its rounding error (exact by FMA) + e rl.
+// About 2^-44 relative: the difference of two such products keeps its
+// precision where they nearly cancel. Explicit _rn intrinsics: no contraction,
+// so the same inputs give the same bits wherever this is evaluated.
+__device__ __forceinline__ void mul_df(float e, float rh, float rl, float* hi, float* lo) {
+  const float h = __fmul_rn(e, rh);
+  *hi = h;
+  *lo = __fmaf_rn(e, rl, __fmaf_rn(e, rh, -h));
+}
+
+// 1/S as a pair of floats rh + rl.
+__device__ __forceinline__ void recip_df(double S, float* rh, float* rl) {
+  const double r = 1.0 / S;
+  *rh = (float)r;
+  *rl = (float)(r - (double)*rh);
+}
+
+// D = E/S - E_ref/S_ref from the two products; *I = E/S (its leading float).
+__device__ __forceinline__ float diff_df(float e, float er, const float* sc, float* I) {
+  float Ih, Il, Rh, Rl;
+  mul_df(e, sc[0], sc[1], &Ih, &Il);
+  mul_df(er, sc[2], sc[3], &Rh, &Rl);
+  *I = Ih;
+  return __fadd_rn(__fsub_rn(Ih, Rh), __fsub_rn(Il, Rl));
+}
+
+// Interior pixel k (row-major over ny x nx) -> its cell on the extended grid.
+__device__ __forceinline__ int ext_cell(int k, int nx, int hx, int hy, int ncol) {
+  const int j = k / nx, i = k - j * nx;
+  return (j + hy) * ncol + (i + hx);
 }
 
 // With I^ = E/S, I^_ref = E_ref/S_ref over the interior and D = I^ - I^_ref:
 // L = ||D||_F / sqrt(nx ny), and dL/dE = (c D - c sum(D I^)) / S on the interior
 // with c = 1/(sqrt(nx ny) ||D||_F), 0 on ghost pixels. ||D|| = 0 gives a zero
 // gradient; S <= 0 or S_ref <= 0 gives L = NaN and a zero gradient.
+// Per pixel the work is FP32, with D in the paired form above; images equal up
+// to a power-of-two scale give D = 0 exactly (every step scales exactly).
 __global__ void __cluster_dims__(kObjCluster, 1, 1) __launch_bounds__(kObjThreads)
     k_loss_frobenius(const float* __restrict__ E, const float* __restrict__ Eref, int nx, int ny, int hx, int hy,
                      int ncol, int nrow, double* __restrict__ loss, float* __restrict__ dLdE) {
   __shared__ double s_warp[(kObjThreads / 32) * 2];
-  __shared__ double s_sums[2], s_dots[2];
+  __shared__ double s_sums[2], s_dots[2], s_tot[2];
+  __shared__ float s_sc[6];          // 1/S and 1/S_ref as float pairs, c, c sum(D I^)
   cg::cluster_group cl = cg::this_cluster();
   const int nthr = kObjCluster * kObjThreads;
   const int tid = (int)cl.block_rank() * kObjThreads + threadIdx.x;
   const int n = nx * ny;
 
-  double s[2] = {0.0, 0.0};
-  for (int k = tid; k < n; k += nthr) {
-    const int j = k / nx, i = k - j * nx;
-    s[0] += (double)E[(size_t)(j + hy) * ncol + (i + hx)];
-    s[1] += (double)Eref[k];
-  }
-  cluster_sum<2>(s, s_warp, s_sums);
-  const bool ok = s[0] > 0.0 && s[1] > 0.0;
-  // I^ and I^_ref by correctly rounded division (not by a reciprocal): images
-  // equal up to a power-of-two scale then give D = 0 exactly, where the norm's
-  // gradient would otherwise point along rounding noise.
-  const double S = ok ? s[0] : 1.0, Sr = ok ? s[1] : 1.0;
-
-  double d2[2] = {0.0, 0.0};          // sum D^2, sum D I^
-  for (int k = tid; k < n; k += nthr) {
-    const int j = k / nx, i = k - j * nx;
-    const double I = (double)E[(size_t)(j + hy) * ncol + (i + hx)] / S;
-    const double D = I - (double)Eref[k] / Sr;
-    d2[0] = fma(D, D, d2[0]);
-    d2[1] = fma(D, I, d2[1]);
-  }
-  cluster_sum<2>(d2, s_warp, s_dots);
-  const double root_n = sqrt((double)nx * (double)ny);
-  const double norm = sqrt(d2[0]);
-  const double c = (ok && norm > 0.0) ? 1.0 / (root_n * norm) : 0.0;
-  const double gdot = c * d2[1];
-
-  for (int q = tid; q < ncol * nrow; q += nthr) {
-    const int r = q / ncol, col = q - r * ncol;
-    const int i = col - hx, j = r - hy;
-    float g = 0.0f;
-    if (c != 0.0 && i >= 0 && i < nx && j >= 0 && j < ny) {
-      const double I = (double)E[q] / S;
-      const double D = I - (double)Eref[(size_t)j * nx + i] / Sr;
-      g = (float)((c * D - gdot) / S);
+  float p[2] = {0.0f, 0.0f};
+  for (int k0 = tid; k0 < n; k0 += kObjUnroll * nthr) {
+    float e[kObjUnroll], r[kObjUnroll];
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      const int k = k0 + u * nthr;
+      e[u] = k < n ? E[ext_cell(k, nx, hx, hy, ncol)] : 0.0f;
+      r[u] = k < n ? Eref[k] : 0.0f;
     }
-    dLdE[q] = g;
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      p[0] = __fadd_rn(p[0], e[u]);
+      p[1] = __fadd_rn(p[1], r[u]);
+    }
   }
-  if (tid == 0) *loss = ok ? norm / root_n : __longlong_as_double(0x7ff8000000000000LL);
+  cluster_sum<2>(p, s_warp, s_sums, s_tot);
+  const bool ok = s_tot[0] > 0.0 && s_tot[1] > 0.0;
+  if (threadIdx.x == 0) {
+    s_sc[0] = s_sc[1] = s_sc[2] = s_sc[3] = 0.0f;
+    if (ok) {
+      recip_df(s_tot[0], &s_sc[0], &s_sc[1]);
+      recip_df(s_tot[1], &s_sc[2], &s_sc[3]);
+    }
+  }
+  __syncthreads();
+  const float sc[4] = {s_sc[0], s_sc[1], s_sc[2], s_sc[3]};
+
+  float d[2] = {0.0f, 0.0f};         // sum D^2, sum D I^
+  for (int k0 = tid; k0 < n; k0 += kObjUnroll * nthr) {
+    float e[kObjUnroll], r[kObjUnroll];
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      const int k = k0 + u * nthr;
+      e[u] = k < n ? E[ext_cell(k, nx, hx, hy, ncol)] : 0.0f;
+      r[u] = k < n ? Eref[k] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      float I;
+      const float D = diff_df(e[u], r[u], sc, &I);    // 0 for the padding (e = r = 0)
+      d[0] = __fmaf_rn(D, D, d[0]);
+      d[1] = __fmaf_rn(D, I, d[1]);
+    }
+  }
+  cluster_sum<2>(d, s_warp, s_dots, s_tot);
+  if (threadIdx.x == 0) {
+    const double root_n = sqrt((double)nx * (double)ny);
+    const double norm = sqrt(s_tot[0]);
+    const double c = (ok && norm > 0.0) ? 1.0 / (root_n * norm) : 0.0;
+    s_sc[4] = (float)c;
+    s_sc[5] = (float)(c * s_tot[1]);
+    if (cl.block_rank() == 0) *loss = ok ? norm / root_n : __longlong_as_double(0x7ff8000000000000LL);
+  }
+  __syncthreads();
+  const float cf = s_sc[4], gdot = s_sc[5];
+
+  const int ncell = ncol * nrow;
+  for (int q0 = tid; q0 < ncell; q0 += kObjUnroll * nthr) {
+    float e[kObjUnroll], r[kObjUnroll];
+    bool in[kObjUnroll];
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      const int q = q0 + u * nthr;
+      const int row = q / ncol, col = q - row * ncol;
+      const int i = col - hx, j = row - hy;
+      in[u] = q < ncell && cf != 0.0f && i >= 0 && i < nx && j >= 0 && j < ny;
+      e[u] = in[u] ? E[q] : 0.0f;
+      r[u] = in[u] ? Eref[(size_t)j * nx + i] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      const int q = q0 + u * nthr;
+      if (q >= ncell) break;
+      float I;
+      const float D = diff_df(e[u], r[u], sc, &I);
+      dLdE[q] = in[u] ? __fmaf_rn(cf, D, -gdot) * sc[0] : 0.0f;
+    }
+  }
   cl.sync();       // no CTA leaves while another may still read its shared memory
+}
+
+// Squared L2 loss (row a8): L = sum over the interior of (E - E_ref)^2 and
+// dL/dE = 2 (E - E_ref) there, 0 on ghost pixels; one pass, FP32 per pixel,
+// the partial sums reduced over the cluster in a fixed order.
+__global__ void __cluster_dims__(kObjCluster, 1, 1) __launch_bounds__(kObjThreads)
+    k_loss_l2(const float* __restrict__ E, const float* __restrict__ Eref, int nx, int ny, int hx, int hy, int ncol,
+              int nrow, double* __restrict__ loss, float* __restrict__ dLdE) {
+  __shared__ double s_warp[kObjThreads / 32];
+  __shared__ double s_sum[1], s_tot[1];
+  cg::cluster_group cl = cg::this_cluster();
+  const int nthr = kObjCluster * kObjThreads;
+  const int tid = (int)cl.block_rank() * kObjThreads + threadIdx.x;
+  const int ncell = ncol * nrow;
+  float part[1] = {0.0f};
+  for (int q0 = tid; q0 < ncell; q0 += kObjUnroll * nthr) {
+    float e[kObjUnroll], r[kObjUnroll];
+    bool in[kObjUnroll];
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      const int q = q0 + u * nthr;
+      const int row = q / ncol, col = q - row * ncol;
+      const int i = col - hx, j = row - hy;
+      in[u] = q < ncell && i >= 0 && i < nx && j >= 0 && j < ny;
+      e[u] = in[u] ? E[q] : 0.0f;
+      r[u] = in[u] ? Eref[(size_t)j * nx + i] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kObjUnroll; ++u) {
+      const int q = q0 + u * nthr;
+      if (q >= ncell) break;
+      const float d = __fsub_rn(e[u], r[u]);
+      part[0] = __fmaf_rn(d, d, part[0]);
+      dLdE[q] = 2.0f * d;
+    }
+  }
+  cluster_sum<1>(part, s_warp, s_sum, s_tot);
+  if (threadIdx.x == 0 && cl.block_rank() == 0) *loss = s_tot[0];
+  cl.sync();
 }
 
 __global__ void k_reparam_tanh(const float* __restrict__ theta, const float* __restrict__ offset, int64_t n,
@@ -180,6 +304,14 @@ __global__ void k_offset_spherical(int n1, int n2, int p, int q, double rx, doub
 }
 
 }  // namespace
+
+cudaError_t launch_loss_l2(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y, double* loss,
+                           float* dLdE, cudaStream_t st) {
+  const int ncol = nx + nu_x - 1, nrow = ny + nu_y - 1;
+  k_loss_l2<<<kObjCluster, kObjThreads, 0, st>>>(E, Eref, nx, ny, (nu_x - 1) / 2, (nu_y - 1) / 2, ncol, nrow, loss,
+                                                 dLdE);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_loss_frobenius(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y,
                                   double* loss, float* dLdE, cudaStream_t st) {

@@ -3,10 +3,13 @@ normalised Frobenius loss (Sec. 2.5), the tanh reparametrisation with its
 adjoint, the spherical offsets (Sec. 2.4.2, Table magndata), the fused Adam
 step on the unconstrained variables, and the optimisation step built from them.
 
-Tolerances: the loss kernels read the same float32 images as the oracle and
-reduce in FP64, so the scalar loss agrees to FP64 rounding (1e-10 relative);
-dL/dE and the maps are written in FP32 (1e-6 relative). Adam in FP32 against
-FP64 over a few steps: 1e-5 absolute on the unconstrained variables.
+Tolerances: the loss kernel reads the same float32 images as the oracle; per
+pixel it works in FP32 with E/S carried as a pair of floats (about 2^-44
+relative), each thread sums at most a few dozen FP32 terms and FP64 adds the
+partial sums, so the loss agrees to 1e-6 relative; dL/dE is formed in FP32 from
+FP32-rounded factors (1e-5 of its largest value). The maps are written in FP32
+(1e-6 relative). Adam in FP32 against FP64 over a few steps: 1e-5 absolute on
+the unconstrained variables.
 """
 import ctypes as C
 
@@ -45,11 +48,11 @@ def test_frobenius_loss_matches_oracle(nx, ny, nu):
     L, d = _frob_gpu(E.cuda(), Eref.cuda(), nx, ny, nu)
     L_or, d_or = O.loss_frobenius(_wl(nx, ny, nu, Eref.double().numpy()), E.double().numpy())
     if nx * ny == 1:
-        # one pixel: both normalised images are exactly 1
-        assert L_or == 0.0 and L == 0.0 and np.all(d == 0)
+        # one pixel: both normalised images are 1 (the kernel's to about 2^-44)
+        assert L_or == 0.0 and L < 1e-12 and np.abs(d).max() < 1e-10 / float(E.sum())
         return
-    assert abs(L - L_or) <= 1e-10 * L_or
-    assert np.max(np.abs(d - d_or)) <= 1e-6 * np.max(np.abs(d_or))
+    assert abs(L - L_or) <= 1e-6 * L_or
+    assert np.max(np.abs(d - d_or)) <= 1e-5 * np.max(np.abs(d_or))
     # the reduction order is fixed: bit-identical on a second call
     L2, d2 = _frob_gpu(E.cuda(), Eref.cuda(), nx, ny, nu)
     assert L2 == L and np.array_equal(d2, d)
