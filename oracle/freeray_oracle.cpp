@@ -79,6 +79,11 @@ typedef struct or_problem {
   int32_t nu_x, nu_y;        // filter sizes (odd); ghost pixels (nu-1)/2 per side
   double alpha;              // Gaussian filter coefficient, in pixel units
   int32_t scan_points;       // root scan resolution (>= 16)
+  // Point-source intersection (Sec. 2.2.2): 0 = the B-spline itself (smallest
+  // positive root of Eq. surfaceintersect); > 0 = the triangle mesh that splits
+  // every knot span product into mesh_nu x mesh_nv rectangles, two triangles each.
+  int32_t mesh_nu;
+  int32_t mesh_nv;
   int32_t pad_;
 } or_problem;
 
@@ -291,7 +296,15 @@ struct Problem {
   double Rsx, Rsy;            // effective screen radii R* with ghost pixels
   int ncol, nrow;             // extended grid: (nx+nu_x-1) columns, (ny+nu_y-1) rows
   double omega0;              // initial ray weight Phi / n_rays
+  // Triangle mesh (mesh_nu > 0): the rectangles of all knot span products form
+  // one uniform grid of NU x NV cells over [0,1]^2 (the knots are uniform);
+  // node_z[K*(NV+1)+L] = Z(K/NU, L/NV).
+  int NU = 0, NV = 0;
+  std::vector<double> node_z;
 };
+
+template <class T>
+void surface(const Problem& pb, const T& u, const T& v, int si, int sj, T* Z, T* Zu, T* Zv);
 
 bool make_problem(const or_problem* in, Problem* pb) {
   pb->d = *in;
@@ -314,6 +327,18 @@ bool make_problem(const or_problem* in, Problem* pb) {
   pb->ncol = d.nx + d.nu_x - 1;
   pb->nrow = d.ny + d.nu_y - 1;
   pb->omega0 = d.flux / (double)d.n_rays;
+  if (d.mesh_nu < 0 || d.mesh_nv < 0 || (d.mesh_nu > 0) != (d.mesh_nv > 0)) return false;
+  if (d.mesh_nu > 0) {
+    pb->NU = (d.n1 - d.p + 1) * d.mesh_nu;
+    pb->NV = (d.n2 - d.q + 1) * d.mesh_nv;
+    pb->node_z.assign((size_t)(pb->NU + 1) * (pb->NV + 1), 0.0);
+    for (int K = 0; K <= pb->NU; ++K)
+      for (int L = 0; L <= pb->NV; ++L) {
+        double Z, Zu, Zv;
+        surface<double>(*pb, (double)K / pb->NU, (double)L / pb->NV, -1, -1, &Z, &Zu, &Zv);
+        pb->node_z[(size_t)K * (pb->NV + 1) + L] = Z;
+      }
+  }
   return true;
 }
 
@@ -524,6 +549,105 @@ int find_root(const Problem& pb, const GlassRay& g, double* t_root) {
   return OR_OUT_OF_DOMAIN;  // reached the side of the domain before the freeform
 }
 
+// ----------------------------------------------------------------------------
+// Sec. 2.2.2: intersection with the triangle mesh of the freeform. Cell (K, L)
+// is [K/NU, (K+1)/NU) x [L/NV, (L+1)/NV); with local coordinates a = NU u - K,
+// b = NV v - L its lower-left triangle is {a >= 0, b >= 0, a + b < 1} and its
+// upper-right triangle {a < 1, b < 1, a + b >= 1}: the paper's closed and open
+// edges, which partition the cell. On each triangle the mesh is the plane
+// through its three vertices on the surface (Eq. trianglefuncdetermined).
+// ----------------------------------------------------------------------------
+struct MeshHit {
+  int status;
+  int K, L, upper;
+  double t;
+};
+
+// The plane of a triangle as z = c0 + ca a + cb b in the cell's local coordinates.
+template <class T>
+void tri_plane(const T& z00, const T& z10, const T& z01, const T& z11, int upper, T* c0, T* ca, T* cb) {
+  if (!upper) {
+    *c0 = z00;
+    *ca = z10 - z00;
+    *cb = z01 - z00;
+  } else {   // z = z11 + (z11 - z01)(a - 1) + (z11 - z10)(b - 1)
+    *ca = z11 - z01;
+    *cb = z11 - z10;
+    *c0 = z11 - *ca - *cb;
+  }
+}
+
+bool in_triangle(double a, double b, int upper) {
+  return upper ? (a < 1.0 && b < 1.0 && a + b >= 1.0) : (a >= 0.0 && b >= 0.0 && a + b < 1.0);
+}
+
+double node_z(const Problem& pb, int K, int L) { return pb.node_z[(size_t)K * (pb.NV + 1) + L]; }
+
+// Mesh height at (u, v) in [0,1]^2.
+double mesh_height(const Problem& pb, double u, double v) {
+  const int K = std::min(pb.NU - 1, std::max(0, (int)std::floor(u * pb.NU)));
+  const int L = std::min(pb.NV - 1, std::max(0, (int)std::floor(v * pb.NV)));
+  const double a = u * pb.NU - K, b = v * pb.NV - L;
+  double c0, ca, cb;
+  tri_plane<double>(node_z(pb, K, L), node_z(pb, K + 1, L), node_z(pb, K, L + 1), node_z(pb, K + 1, L + 1),
+                    a + b >= 1.0 ? 1 : 0, &c0, &ca, &cb);
+  return c0 + ca * a + cb * b;
+}
+
+// Where the ray (u, v, z)(t) = (ou + du t, ov + dv t, oz + dz t) meets the plane
+// of triangle (K, L, upper) with vertex heights z00, z10, z01, z11.
+template <class T>
+T tri_t(const Problem& pb, int K, int L, int upper, const T& z00, const T& z10, const T& z01, const T& z11,
+        double ou, double ov, double oz, double du, double dv, double dz) {
+  T c0, ca, cb;
+  tri_plane<T>(z00, z10, z01, z11, upper, &c0, &ca, &cb);
+  const double a0 = pb.NU * ou - K, b0 = pb.NV * ov - L, da = pb.NU * du, db = pb.NV * dv;
+  // c0 + ca (a0 + da t) + cb (b0 + db t) = oz + dz t
+  return (c0 + ca * a0 + cb * b0 - oz) / (dz - ca * da - cb * db);
+}
+
+// The first triangle the ray meets: over every triangle whose cell the ray's
+// (u,v) path crosses inside the convex-hull slab, the smallest t >= 0 whose
+// point lies in the triangle.
+MeshHit mesh_intersect(const Problem& pb, const GlassRay& g) {
+  MeshHit h{OR_OUT_OF_DOMAIN, -1, -1, 0, 0.0};
+  const double dz = g.d[2];
+  const double pad = 1e-12 * (1.0 + std::max(std::fabs(pb.zmin), std::fabs(pb.zmax)));
+  const double t_lo = std::max(0.0, (pb.zmin - pad - g.o[2]) / dz);
+  const double t_hi = (pb.zmax + pad - g.o[2]) / dz;
+  const double ou = x_to_u<double>(pb, g.o[0]), ov = y_to_v<double>(pb, g.o[1]);
+  const double du = g.d[0] / (2.0 * pb.d.rx), dv = g.d[1] / (2.0 * pb.d.ry);
+  double t_dom = INFINITY;
+  if (du > 0) t_dom = std::min(t_dom, (1.0 - ou) / du);
+  if (du < 0) t_dom = std::min(t_dom, (0.0 - ou) / du);
+  if (dv > 0) t_dom = std::min(t_dom, (1.0 - ov) / dv);
+  if (dv < 0) t_dom = std::min(t_dom, (0.0 - ov) / dv);
+  if (t_dom < t_lo) return h;
+  const double t_end = std::min(t_hi, t_dom);
+  auto clamp01 = [](double x) { return std::min(1.0, std::max(0.0, x)); };
+  if (mesh_height(pb, clamp01(ou + du * t_lo), clamp01(ov + dv * t_lo)) - (g.o[2] + dz * t_lo) < 0.0) {
+    h.status = OR_INVALID;   // freeform below the entry face here
+    return h;
+  }
+  const double u0 = ou + du * t_lo, u1 = ou + du * t_end, v0 = ov + dv * t_lo, v1 = ov + dv * t_end;
+  const int K0 = std::max(0, (int)std::floor(std::min(u0, u1) * pb.NU));
+  const int K1 = std::min(pb.NU - 1, (int)std::floor(std::max(u0, u1) * pb.NU));
+  const int L0 = std::max(0, (int)std::floor(std::min(v0, v1) * pb.NV));
+  const int L1 = std::min(pb.NV - 1, (int)std::floor(std::max(v0, v1) * pb.NV));
+  double best = INFINITY;
+  for (int K = K0; K <= K1; ++K)
+    for (int L = L0; L <= L1; ++L)
+      for (int up = 0; up < 2; ++up) {
+        const double t = tri_t<double>(pb, K, L, up, node_z(pb, K, L), node_z(pb, K + 1, L), node_z(pb, K, L + 1),
+                                       node_z(pb, K + 1, L + 1), ou, ov, g.o[2], du, dv, dz);
+        if (!(t >= 0.0) || !(t < best)) continue;
+        if (!in_triangle(pb.NU * (ou + du * t) - K, pb.NV * (ov + dv * t) - L, up)) continue;
+        best = t;
+        h = MeshHit{OR_OK, K, L, up, t};
+      }
+  return h;
+}
+
 // Trace one ray. For T = double the root is found here by find_root(); for
 // T = Dual the FP64 root `t_root_in` of an earlier double trace is reused and
 // its derivative follows from the implicit function theorem applied to
@@ -554,13 +678,35 @@ void trace_ray(const Problem& pb, uint64_t id, int si, int sj, double t_root_in,
     T1 = g.T1;
     for (int c = 0; c < 3; ++c) r->d[c] = T(g.d[c]);
     double t_root = t_root_in;
-    if (is_value) {
+    MeshHit mh{};
+    if (d.mesh_nu > 0) {
+      // Triangle mesh (Sec. 2.2.2): the triangle is found in FP64; t is the
+      // closed-form plane intersection, in T, of that triangle's vertices.
+      mh = mesh_intersect(pb, g);
+      if (mh.status != OR_OK) { r->status = mh.status; return; }
+      t_root = mh.t;
+    } else if (is_value) {
       const int st = find_root(pb, g, &t_root);
       if (st != OR_OK) { r->status = st; return; }
     }
     r->t = t_root;
     T t(t_root);
-    if (!is_value) {
+    if (d.mesh_nu > 0) {
+      r->span_i = d.p + mh.K / d.mesh_nu;   // the triangle's knot span product
+      r->span_j = d.q + mh.L / d.mesh_nv;
+      if (!is_value) {
+        T zv[4];
+        for (int c = 0; c < 4; ++c) {
+          T Zn, Zun, Zvn;
+          surface<T>(pb, T((double)(mh.K + (c & 1)) / pb.NU), T((double)(mh.L + (c >> 1)) / pb.NV), si, sj, &Zn,
+                     &Zun, &Zvn);
+          zv[c] = Zn;
+        }
+        const double ou = x_to_u<double>(pb, g.o[0]), ov = y_to_v<double>(pb, g.o[1]);
+        t = tri_t<T>(pb, mh.K, mh.L, mh.upper, zv[0], zv[1], zv[2], zv[3], ou, ov, g.o[2],
+                     g.d[0] / (2.0 * d.rx), g.d[1] / (2.0 * d.ry), g.d[2]);
+      }
+    } else if (!is_value) {
       const T u0 = x_to_u<T>(pb, T(g.o[0] + g.d[0] * t_root));
       const T v0 = y_to_v<T>(pb, T(g.o[1] + g.d[1] * t_root));
       surface<T>(pb, u0, v0, si, sj, &Z, &Zu, &Zv);
@@ -577,10 +723,12 @@ void trace_ray(const Problem& pb, uint64_t id, int si, int sj, double t_root_in,
     surface<T>(pb, r->u, r->v, si, sj, &Z, &Zu, &Zv);
   }
   // Knot span of the hit (for the derivative window and the records).
-  const double uc = std::min(1.0, std::max(0.0, val(r->u)));
-  const double vc = std::min(1.0, std::max(0.0, val(r->v)));
-  r->span_i = find_span(pb.U, d.n1, uc);
-  r->span_j = find_span(pb.V, d.n2, vc);
+  if (!(d.src_kind != 0 && d.mesh_nu > 0)) {
+    const double uc = std::min(1.0, std::max(0.0, val(r->u)));
+    const double vc = std::min(1.0, std::max(0.0, val(r->v)));
+    r->span_i = find_span(pb.U, d.n1, uc);
+    r->span_j = find_span(pb.V, d.n2, vc);
+  }
   // Normal of the height field z = Z(X^{-1}(x), Y^{-1}(y)) pointing into the air:
   // (-Z_x, -Z_y, 1) normalised, with Z_x = Z_u / (2 r_x), Z_y = Z_v / (2 r_y).
   const T mx = -Zu / (2.0 * d.rx), my = -Zv / (2.0 * d.ry);

@@ -30,7 +30,8 @@ class Problem(C.Structure):
         ("flux", C.c_double), ("n_rays", C.c_uint64), ("seed", C.c_uint64),
         ("z_screen", C.c_double), ("Rx", C.c_double), ("Ry", C.c_double),
         ("nx", C.c_int32), ("ny", C.c_int32), ("nu_x", C.c_int32), ("nu_y", C.c_int32),
-        ("alpha", C.c_double), ("scan_points", C.c_int32), ("pad_", C.c_int32),
+        ("alpha", C.c_double), ("scan_points", C.c_int32),
+        ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -140,6 +141,8 @@ class OracleProblem:
         s.nx, s.ny, s.nu_x, s.nu_y = tgt["nx"], tgt["ny"], tgt["nu_x"], tgt["nu_y"]
         s.alpha = tgt["alpha"]
         s.scan_points = scan_points
+        mesh = wl.get("mesh", (0, 0))
+        s.mesh_nu, s.mesh_nv = mesh
         self.s = s
         self.ext_shape = (tgt["ny"] + tgt["nu_y"] - 1, tgt["nx"] + tgt["nu_x"] - 1)
 

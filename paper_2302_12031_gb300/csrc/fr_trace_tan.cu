@@ -4,8 +4,9 @@
 //
 // Each CTA builds the lens tables (as the forward kernel) and a bit mask per
 // knot-span patch of the directions that move one of its 16 control points.
-// Every lane traces an equal run of consecutive ray ids; a ray whose patch no
-// direction moves stops after the trace. For the others, the tangents of the
+// Every lane takes an equal run of consecutive ray ids; a ray whose patch no
+// direction moves stops before the trace (collimated: the patch follows from
+// the ray's grid cell) or right after it (point source). For the others, the tangents of the
 // hit height and slopes, sum_ab N_a N_b dP, sum_ab N'_a N_b dP and
 // sum_ab N_a N'_b dP (for a point source also the hit's shift along the ray by
 // the implicit function theorem), go through ray_tangent, and
@@ -51,16 +52,31 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
   lane_range(it, warps, &a0, &a1);
   for (uint64_t id = a0; id < a1; ++id) {
     RayFwd r;
+    uint32_t m;
     if (coll) {
+      // A collimated ray's patch is known before the trace: rays on patches no
+      // direction moves contribute nothing and are only counted.
       const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
-      trace_collimated(it, ls, row, col, id, inv_cols, inv_rows, r);
+      float ja = 0.5f, jb = 0.5f;
+      if (it.jitter) {
+        const uint2 w = philox_ray_words(it.seed, id);
+        ja = unit23(w.x);
+        jb = unit23(w.y);
+      }
+      const float u = ((float)col + ja) * inv_cols, v = ((float)row + jb) * inv_rows;
+      locate(u, it.nsu, &r.k, &r.s);
+      locate(v, it.nsv, &r.l, &r.t);
+      m = s_mask[r.k * it.nsv + r.l];
+      if (m == 0u && !cnt_dst) continue;
+      float Z, Zs, Zt;
+      patch_eval(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Z, &Zs, &Zt);
+      collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zs, Zt, r);
     } else {
       trace_point(it, ls, id, ls.zb[0], ls.zb[1], r);
+      m = r.status == FR_RAY_ON_SCREEN ? s_mask[r.k * it.nsv + r.l] : 0u;
     }
     cnt.add(r.status, cnt_dst);
-    if (r.status != FR_RAY_ON_SCREEN) continue;
-    uint32_t m = s_mask[r.k * it.nsv + r.l];
-    if (m == 0u) continue;
+    if (r.status != FR_RAY_ON_SCREEN || m == 0u) continue;
     Foot<NU> f;
     if (!footprint<NU>(it, r.X, r.Y, f)) continue;
     float Nu[4], dNu[4], Nv[4], dNv[4];
