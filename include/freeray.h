@@ -123,7 +123,11 @@ typedef struct fr_options {
   void* event_begin;        /* optional cudaEvent_t, recorded on the stream right before the
                                trace kernel (not the prep or conversion kernels) */
   void* event_end;          /* optional cudaEvent_t, recorded right after the trace kernel */
-  int32_t reserved[8];
+  int32_t mesh_nu;          /* point sources: 0 -> Newton on the B-spline (Sec. 2.2.1); n > 0 ->
+                               the triangle mesh of Sec. 2.2.2 with mesh_nu x mesh_nv rectangles
+                               (two triangles each) per knot span product; 1..64 */
+  int32_t mesh_nv;          /* 0 with mesh_nu = 0, else 1..64 */
+  int32_t reserved[6];
 } fr_options;
 
 /* Per-cause ray counts (device, uint64). Kernels add to it; zero it first. */

@@ -218,6 +218,16 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   }
   it->newton_max = o.newton_max_iter;
   it->newton_tol = o.newton_tol;
+  if (o.mesh_nu < 0 || o.mesh_nu > 64 || o.mesh_nv < 0 || o.mesh_nv > 64 || (o.mesh_nu > 0) != (o.mesh_nv > 0))
+    return set_error(h, FR_ERR_INVALID_ARG, "mesh_nu, mesh_nv must both be 0 or both 1..64");
+  if (it->kind == FR_SOURCE_POINT && o.mesh_nu > 0) {
+    it->mesh_nu = o.mesh_nu;
+    it->mesh_nv = o.mesh_nv;
+    it->NU = it->nsu * o.mesh_nu;
+    it->NV = it->nsv * o.mesh_nv;
+    it->inv_mnu = 1.0f / (float)o.mesh_nu;
+    it->inv_mnv = 1.0f / (float)o.mesh_nv;
+  }
   return FR_OK;
 }
 

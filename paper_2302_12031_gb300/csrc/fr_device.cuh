@@ -268,6 +268,8 @@ struct RayFwd {
   float lam;            // distance parameter to the screen
   float X, Y;           // screen hit
   float tstar, gp;      // point source: ray parameter of the hit and df/dt there
+  int mK, mL, mup;      // triangle mesh: cell and triangle (0 lower-left, 1 upper-right) of the hit
+  float ma, mb;         // triangle mesh: the hit in the cell's local coordinates
 };
 
 // Exit face: normal, Snell glass -> air, TIR, Schlick, propagation (a5, a6).
@@ -412,6 +414,172 @@ __device__ __forceinline__ void f_eval(const Item& it, const LensSmem& ls, float
   *fp = fmaf(r.Zs, du * (float)it.nsu, fmaf(r.Zt, dv * (float)it.nsv, -dz));
 }
 
+// ---------------------------------------------------------------------------
+// Sec. 2.2.2: the triangle mesh. Knot span product (k, l) is split into
+// mesh_nu x mesh_nv rectangles; with uniform knots all rectangles form one grid
+// of NU x NV cells over [0,1]^2. With local coordinates a = NU u - K,
+// b = NV v - L, cell (K, L) has a lower-left triangle {a >= 0, b >= 0,
+// a + b < 1} and an upper-right one {a < 1, b < 1, a + b >= 1}; on each the
+// mesh is the plane through its three vertices, which lie on the surface
+// (Eq. trianglefuncdetermined).
+// ---------------------------------------------------------------------------
+
+// Heights of the four corners of cell (K, L) from the power form of its patch.
+__device__ __forceinline__ void cell_nodes(const Item& it, const LensSmem& ls, int K, int L, float* z00, float* z10,
+                                           float* z01, float* z11) {
+  const int k = K / it.mesh_nu, l = L / it.mesh_nv;
+  const float s0 = (float)(K - k * it.mesh_nu) * it.inv_mnu, s1 = s0 + it.inv_mnu;
+  const float t0 = (float)(L - l * it.mesh_nv) * it.inv_mnv, t1 = t0 + it.inv_mnv;
+  const float4* q = ls.patch + (size_t)(k * it.nsv + l) * 4;
+  float r0[4], r1[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float4 c = q[e];
+    r0[e] = fmaf(t0, fmaf(t0, fmaf(t0, c.w, c.z), c.y), c.x);
+    r1[e] = fmaf(t1, fmaf(t1, fmaf(t1, c.w, c.z), c.y), c.x);
+  }
+  *z00 = fmaf(s0, fmaf(s0, fmaf(s0, r0[3], r0[2]), r0[1]), r0[0]);
+  *z10 = fmaf(s1, fmaf(s1, fmaf(s1, r0[3], r0[2]), r0[1]), r0[0]);
+  *z01 = fmaf(s0, fmaf(s0, fmaf(s0, r1[3], r1[2]), r1[1]), r1[0]);
+  *z11 = fmaf(s1, fmaf(s1, fmaf(s1, r1[3], r1[2]), r1[1]), r1[0]);
+}
+
+// The plane of a triangle as z = c0 + ca a + cb b.
+__device__ __forceinline__ void tri_plane(float z00, float z10, float z01, float z11, int upper, float* c0, float* ca,
+                                          float* cb) {
+  if (!upper) {
+    *ca = z10 - z00;
+    *cb = z01 - z00;
+    *c0 = z00;
+  } else {   // z11 + (z11 - z01)(a - 1) + (z11 - z10)(b - 1)
+    *ca = z11 - z01;
+    *cb = z11 - z10;
+    *c0 = z11 - *ca - *cb;
+  }
+}
+
+// Mesh height at (u, v) in [0,1]^2.
+__device__ __forceinline__ float mesh_height(const Item& it, const LensSmem& ls, float u, float v) {
+  const int K = min(max((int)floorf(u * (float)it.NU), 0), it.NU - 1);
+  const int L = min(max((int)floorf(v * (float)it.NV), 0), it.NV - 1);
+  const float a = fmaf(u, (float)it.NU, -(float)K), b = fmaf(v, (float)it.NV, -(float)L);
+  float z00, z10, z01, z11, c0, ca, cb;
+  cell_nodes(it, ls, K, L, &z00, &z10, &z01, &z11);
+  tri_plane(z00, z10, z01, z11, a + b >= 1.0f ? 1 : 0, &c0, &ca, &cb);
+  return fmaf(ca, a, fmaf(cb, b, c0));
+}
+
+// First triangle along the ray (u, v, z)(t) = (ou + du t, ov + dv t, oz + dz t)
+// for t in [ta, tb]: the cells its (u,v) path crosses are visited in order of
+// t (a grid walk), each cell's two triangles tested; the first cell with a hit
+// holds the first hit. The inside test has a margin of 1e-4 cell widths so that
+// FP32 rounding cannot let a ray slip between two triangles; near an edge both
+// may accept and the smaller t is kept. At most NU + NV cells are visited. On
+// a hit fills tstar, gp (= dg/dt of g = mesh - ray height), the cell,
+// triangle and local coordinates, and the cell count in iters.
+__device__ __forceinline__ bool mesh_intersect(const Item& it, const LensSmem& ls, float ou, float ov, float du,
+                                               float dv, float oz, float dz, float ta, float tb, RayFwd& r) {
+  const float fNU = (float)it.NU, fNV = (float)it.NV;
+  int K = min(max((int)floorf(fmaf(du, ta, ou) * fNU), 0), it.NU - 1);
+  int L = min(max((int)floorf(fmaf(dv, ta, ov) * fNV), 0), it.NV - 1);
+  const float da = du * fNU, db = dv * fNV;      // d(a)/dt, d(b)/dt
+  const int sK = du > 0.0f ? 1 : -1, sL = dv > 0.0f ? 1 : -1;
+  float tK = INFINITY, tL = INFINITY, dtK = INFINITY, dtL = INFINITY;
+  if (du != 0.0f) {
+    tK = ((float)(K + (du > 0.0f ? 1 : 0)) / fNU - ou) / du;
+    dtK = 1.0f / fabsf(da);
+  }
+  if (dv != 0.0f) {
+    tL = ((float)(L + (dv > 0.0f ? 1 : 0)) / fNV - ov) / dv;
+    dtL = 1.0f / fabsf(db);
+  }
+  constexpr float eps = 1e-4f;
+  const int max_cells = it.NU + it.NV;
+  for (int n = 0; n < max_cells; ++n) {
+    float z00, z10, z01, z11;
+    cell_nodes(it, ls, K, L, &z00, &z10, &z01, &z11);
+    const float a0 = fmaf(fNU, ou, -(float)K), b0 = fmaf(fNV, ov, -(float)L);
+    float best = INFINITY;
+#pragma unroll
+    for (int up = 0; up < 2; ++up) {
+      float c0, ca, cb;
+      tri_plane(z00, z10, z01, z11, up, &c0, &ca, &cb);
+      // c0 + ca (a0 + da t) + cb (b0 + db t) = oz + dz t
+      const float den = dz - fmaf(ca, da, cb * db);
+      const float t = (fmaf(ca, a0, fmaf(cb, b0, c0)) - oz) / den;
+      if (!(t >= 0.0f) || !(t < best)) continue;
+      const float a = fmaf(da, t, a0), b = fmaf(db, t, b0);
+      const bool in = up ? (a <= 1.0f + eps && b <= 1.0f + eps && a + b >= 1.0f - eps)
+                         : (a >= -eps && b >= -eps && a + b <= 1.0f + eps);
+      if (!in) continue;
+      best = t;
+      r.tstar = t;
+      r.gp = -den;
+      r.mK = K;
+      r.mL = L;
+      r.mup = up;
+      r.ma = a;
+      r.mb = b;
+    }
+    if (best < INFINITY) {
+      r.iters = n + 1;
+      return true;
+    }
+    if (tK < tL) {
+      if (tK > tb) break;
+      K += sK;
+      tK += dtK;
+      if (K < 0 || K >= it.NU) break;
+    } else {
+      if (!(tL <= tb)) break;
+      L += sL;
+      tL += dtL;
+      if (L < 0 || L >= it.NV) break;
+    }
+  }
+  r.iters = max_cells;
+  return false;
+}
+
+// Weights of the hit height in the control heights: on the mesh the hit lies on
+// the triangle's plane, z = sum_v lambda_v Z(u_v, v_v), so
+// dz/dP_{kt+a,lt+b} = sum_v lambda_v N_a(u_v) N_b(v_v) over the triangle's three
+// vertices (barycentric lambda_v) in the triangle's patch (kt, lt); W[a][b]
+// returns that sum. (Within the inside test's margin the triangle's patch can
+// be the neighbour of the hit's own.)
+__device__ __forceinline__ void mesh_vertex_weights(const Item& it, const LensSmem& ls, const RayFwd& r,
+                                                    float (&W)[4][4], int* kt, int* lt) {
+  const int k = r.mK / it.mesh_nu, l = r.mL / it.mesh_nv;
+  *kt = k;
+  *lt = l;
+  const float s0 = (float)(r.mK - k * it.mesh_nu) * it.inv_mnu, s1 = s0 + it.inv_mnu;
+  const float t0 = (float)(r.mL - l * it.mesh_nv) * it.inv_mnv, t1 = t0 + it.inv_mnv;
+  float Nu0[4], Nu1[4], Nv0[4], Nv1[4], tmp[4];
+  basis_eval(ls.bu + k * 4, s0, Nu0, tmp);
+  basis_eval(ls.bu + k * 4, s1, Nu1, tmp);
+  basis_eval(ls.bv + l * 4, t0, Nv0, tmp);
+  basis_eval(ls.bv + l * 4, t1, Nv1, tmp);
+  // lower-left: (1-a-b) z00 + a z10 + b z01; upper-right: (a+b-1) z11 + (1-a) z01 + (1-b) z10
+  const float a = r.ma, b = r.mb;
+  float l00 = 0.0f, l10, l01, l11 = 0.0f;
+  if (!r.mup) {
+    l00 = 1.0f - a - b;
+    l10 = a;
+    l01 = b;
+  } else {
+    l11 = a + b - 1.0f;
+    l01 = 1.0f - a;
+    l10 = 1.0f - b;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float p0 = l00 * Nu0[i], p1 = l10 * Nu1[i];
+    const float q0 = l01 * Nu0[i], q1 = l11 * Nu1[i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) W[i][j] = fmaf(p0 + p1, Nv0[j], (q0 + q1) * Nv1[j]);
+  }
+}
+
 // Point source (a1, a2, a4-a6): Philox direction uniform in the cone, flat
 // entry face, Snell + Schlick into the glass, safeguarded Newton on f(t)
 // bracketed by the convex hull of the control heights (Sec. 2.1.2).
@@ -459,6 +627,30 @@ __device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, 
   if (t_dom < ta) { r.status = FR_RAY_OUT_OF_DOMAIN; return; }
   float tb = fminf(t_hi, t_dom);
   float f, fp;
+  if (it.mesh_nu > 0) {
+    // Triangle mesh (Sec. 2.2.2) instead of Newton; the normal is still the
+    // B-spline's at the hit.
+    if (ta == 0.0f && mesh_height(it, ls, fminf(fmaxf(ou, 0.0f), 1.0f), fminf(fmaxf(ov, 0.0f), 1.0f)) < oz) {
+      r.status = FR_RAY_INVALID;
+      return;
+    }
+    if (!mesh_intersect(it, ls, ou, ov, du, dv, oz, r.dz, ta, tb, r)) {
+      r.status = FR_RAY_OUT_OF_DOMAIN;
+      return;
+    }
+    const float t = r.tstar;
+    r.u = fmaf(du, t, ou);
+    r.v = fmaf(dv, t, ov);
+    r.x = fmaf(r.dx, t, ox);
+    r.y = fmaf(r.dy, t, oy);
+    r.z = fmaf(r.dz, t, oz);
+    locate(r.u, it.nsu, &r.k, &r.s);   // the normal is the B-spline's at the hit itself
+    locate(r.v, it.nsv, &r.l, &r.t);
+    float Z;
+    patch_eval(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Z, &r.Zs, &r.Zt);
+    exit_and_propagate<false>(it, r);
+    return;
+  }
   if (tb < t_hi) {
     f_eval(it, ls, ou, ov, du, dv, oz, r.dz, tb, r, &f, &fp);
     if (f > 0.0f) { r.status = FR_RAY_OUT_OF_DOMAIN; return; }   // leaves the side first

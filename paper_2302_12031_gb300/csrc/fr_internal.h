@@ -55,6 +55,11 @@ struct Item {
   // Newton (Sec. 2.2.1 intersection, point sources).
   int newton_max;
   float newton_tol;
+  // Triangle mesh instead of Newton (Sec. 2.2.2, point sources): mesh_nu x
+  // mesh_nv rectangles per knot span product, NU = nsu mesh_nu by NV = nsv
+  // mesh_nv cells over [0,1]^2; mesh_nu = 0: Newton.
+  int mesh_nu, mesh_nv, NU, NV;
+  float inv_mnu, inv_mnv;       // 1/mesh_nu, 1/mesh_nv
   // Schedule: the item's rays are split evenly over the lanes of CTAs
   // [cta_begin, cta_end) of the launch (lane_range in fr_device.cuh).
   int max_ctas;                 // CTAs worth launching (every lane gets a minimum run)

@@ -89,6 +89,36 @@ __device__ __forceinline__ void adjoint_ray(const Item& it, const LensSmem& ls, 
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc.g[a][b] = 0;
   }
+  if (!COLL && it.mesh_nu > 0) {
+    // Triangle mesh: the hit height follows the triangle's vertices, the
+    // normal the B-spline at the hit.
+    float W[4][4];
+    int kt, lt;
+    mesh_vertex_weights(it, ls, r, W, &kt, &lt);
+    const bool same = kt == r.k && lt == r.l;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float A = Zsb * dNu[a], B = Ztb * Nu[a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float c = fmaf(same ? zeta : 0.0f, W[a][b], fmaf(A, Nv[b], B * dNv[b]));
+        if constexpr (DET) acc.g[a][b] += __float2ll_rn(c * go.fixP);
+        else acc.g[a][b] += c;
+      }
+    }
+    if (!same) {   // rare: the triangle lies in the neighbouring patch
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float c = zeta * W[a][b];
+          const int idx = (kt + a) * it.ncv + lt + b;
+          if constexpr (DET) atomicAdd(go.sg_q + idx, (unsigned long long)__float2ll_rn(c * go.fixP));
+          else atomicAdd(go.sg_f + idx, c);
+        }
+    }
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const float A = fmaf(zeta, Nu[a], Zsb * dNu[a]);

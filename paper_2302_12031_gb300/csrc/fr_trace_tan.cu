@@ -73,7 +73,11 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zs, Zt, r);
     } else {
       trace_point(it, ls, id, ls.zb[0], ls.zb[1], r);
-      m = r.status == FR_RAY_ON_SCREEN ? s_mask[r.k * it.nsv + r.l] : 0u;
+      m = 0u;
+      if (r.status == FR_RAY_ON_SCREEN) {
+        m = s_mask[r.k * it.nsv + r.l];
+        if (it.mesh_nu > 0) m |= s_mask[(r.mK / it.mesh_nu) * it.nsv + r.mL / it.mesh_nv];
+      }
     }
     cnt.add(r.status, cnt_dst);
     if (r.status != FR_RAY_ON_SCREEN || m == 0u) continue;
@@ -95,6 +99,9 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       slope_t = fmaf(Zst, dsdt, Ztt * dtdt);
       inv_gp = 1.0f / r.gp;
     }
+    float W[4][4];
+    int kt = 0, lt = 0;
+    if (!coll && it.mesh_nu > 0) mesh_vertex_weights(it, ls, r, W, &kt, &lt);
     const float K = r.w * it.inv_area;
     while (m) {
       const int q = __ffs(m) - 1;
@@ -118,7 +125,16 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       if (coll) {
         tg = ray_tangent<true>(it, r, 0.0f, 0.0f, dZ, dZs, dZt);
       } else {
-        // f(t*, P) = 0: dt* = -dZ / f'(t*); the hit moves along the ray.
+        // f(t*, P) = 0: dt* = -dZ / f'(t*); the hit moves along the ray. On the
+        // triangle mesh the hit height moves with the triangle's vertices.
+        if (it.mesh_nu > 0) {
+          const float* Pt = dP + (size_t)q * nctrl + kt * it.ncv + lt;
+          dZ = 0.0f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) dZ = fmaf(W[a][b], __ldg(Pt + a * it.ncv + b), dZ);
+        }
         const float dt = -dZ * inv_gp;
         tg = ray_tangent<false>(it, r, r.dx * dt, r.dy * dt, r.dz * dt, fmaf(slope_s, dt, dZs),
                                 fmaf(slope_t, dt, dZt));

@@ -23,10 +23,15 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def options_for(wl, **kw):
+    """fr_options matching the workload's intersection (wl["mesh"] for the oracle)."""
+    return api.make_options(mesh=tuple(wl.get("mesh", (0, 0))), **kw)
+
+
 def compare_records(wl, begin, count, min_agree=0.999):
     """GPU debug records vs oracle records on rays [begin, begin+count)."""
     pb = api.Problem(wl)
-    g = pb.debug(begin, count)
+    g = pb.debug(begin, count, options=options_for(wl))
     o = O.trace_records(wl, begin=begin, count=count)
     agree = g["status"] == o["status"]
     assert agree.mean() >= min_agree, (agree.mean(), np.unique(g["status"][~agree]), np.unique(o["status"][~agree]))
@@ -64,6 +69,8 @@ def forward_both(wl, begin=0, count=None, options=None):
     stats = api.new_stats()
     if count is None:
         count = wl["n_rays"] - begin
+    if options is None:
+        options = options_for(wl)
     E = pb.forward(options, ray_begin=begin, ray_count=count, stats=stats).cpu().numpy().astype(np.float64)
     E_or, counts = O.trace_forward(wl, begin=begin, count=count)
     if wl["target"]["nu_x"] == 1 and count > 0:
@@ -83,7 +90,7 @@ def ambiguous_rays(wl, begin, count, eps_px=1e-4):
     is checked on the other rays: those whose status differs between the two
     sides, or whose hit lies within eps_px pixels of a pixel edge.
     """
-    g = api.Problem(wl).debug(begin, count)
+    g = api.Problem(wl).debug(begin, count, options=options_for(wl))
     o = O.trace_records(wl, begin=begin, count=count)
     t = wl["target"]
     wx, wy = 2 * t["Rx"] / t["nx"], 2 * t["Ry"] / t["ny"]
@@ -92,6 +99,15 @@ def ambiguous_rays(wl, begin, count, eps_px=1e-4):
     fy = (o["Y"] + t["Ry"] + hy * wy) / wy
     near = lambda f: np.minimum(f - np.floor(f), np.ceil(f) - f) < eps_px
     amb = (g["status"] != o["status"]) | ((o["status"] == 0) & (near(fx) | near(fy)))
+    mesh = wl.get("mesh", (0, 0))
+    if mesh[0] > 0 and wl["source"]["kind"] == "point":
+        # on the triangle mesh t*(P) has a kink on every triangle edge
+        lens = wl["lens"]
+        NU, NV = (lens["n1"] - 2) * mesh[0], (lens["n2"] - 2) * mesh[1]
+        a, b = o["u"] * NU, o["v"] * NV
+        a, b = a - np.floor(a), b - np.floor(b)
+        edge = np.minimum.reduce([a, 1 - a, b, 1 - b, np.abs(a + b - 1)]) < 1e-4
+        amb |= (o["status"] == 0) & edge
     return begin + np.nonzero(amb)[0]
 
 
@@ -101,6 +117,8 @@ def adjoint_both(wl, dLdE, begin=0, count=None, options=None, exclude_ambiguous=
     pb = api.Problem(wl)
     if count is None:
         count = wl["n_rays"] - begin
+    if options is None:
+        options = options_for(wl)
     d = torch.as_tensor(dLdE, dtype=torch.float32, device="cuda")
     g = pb.adjoint(d, options, ray_begin=begin, ray_count=count).cpu().numpy().astype(np.float64)
     g_or = O.trace_gradient(wl, dLdE, begin=begin, count=count)

@@ -13,7 +13,7 @@ import torch
 from oracle import oracle as O
 from paper_2302_12031_gb300 import api
 from paper_2302_12031_gb300 import workloads as W
-from tests.gpu_helpers import TOL_GRAD, ambiguous_rays, random_dLdE, rel_l2
+from tests.gpu_helpers import TOL_GRAD, ambiguous_rays, options_for, random_dLdE, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -22,12 +22,13 @@ def tangent_both(wl, dP, begin=0, count=None):
     pb = api.Problem(wl)
     if count is None:
         count = wl["n_rays"] - begin
-    g = pb.tangent(dP, ray_begin=begin, ray_count=count).cpu().numpy().astype(np.float64)
+    opt = options_for(wl)
+    g = pb.tangent(dP, opt, ray_begin=begin, ray_count=count).cpu().numpy().astype(np.float64)
     o = O.trace_tangent(wl, dP, begin=begin, count=count)
     amb = ambiguous_rays(wl, begin, count)
     assert len(amb) <= max(3, 2e-3 * count), len(amb)
     for rid in amb:
-        g -= pb.tangent(dP, ray_begin=int(rid), ray_count=1).cpu().numpy()
+        g -= pb.tangent(dP, opt, ray_begin=int(rid), ray_count=1).cpu().numpy()
         o -= O.trace_tangent(wl, dP, begin=int(rid), count=1)
     return g, o
 
