@@ -340,6 +340,25 @@ def extra_workloads(args, flush, world):
                      "steps_per_s": 1.0 / t, "lenses": len(st.problems)}
         del st
         torch.cuda.empty_cache()
+    # triangle mesh (Sec. 2.2.2) against Newton on the 16M-ray point source:
+    # step time, and the freeform hits' distance to Newton's on 2^16 rays
+    wl3 = W.config(3)
+    pb3 = api.Problem(wl3)
+    newton = pb3.debug(0, 1 << 16)
+    mesh_out = {}
+    for n in (1, 2, 4, 8):
+        opt = api.make_options(mesh=(n, n))
+        st = step.OptimStep(wl3, lr=1e-3, graph=True, options=opt)
+        ms = time_steps(st.step, k, 2, flush)
+        rays_per_s, t = D.replica_throughput(st.n_rays, statistics.mean(ms) * 1e-3)
+        m = pb3.debug(0, 1 << 16, options=opt)
+        ok = (m["status"] == 0) & (newton["status"] == 0)
+        dz = abs(m["z"][ok].astype("float64") - newton["z"][ok])
+        mesh_out["%dx%d" % (n, n)] = {"ms_per_step": 1e3 * t, "rays_per_s": rays_per_s,
+                                      "hit_dz_max": float(dz.max()), "hit_dz_rms": float((dz ** 2).mean() ** 0.5),
+                                      "status_agree": float((m["status"] == newton["status"]).mean())}
+        del st
+    out["point_16M_triangle_mesh"] = mesh_out
     # the paper's objective: normalised Frobenius loss, tanh-reparametrised heights
     # over a spherical offset (Table magndata, magnification 3)
     wl = W.config(2)

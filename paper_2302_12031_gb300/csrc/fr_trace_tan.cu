@@ -41,18 +41,66 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
     }
     s_mask[p] = m;
   }
+  // Collimated rays without per-cause counts: only the grid cells over the
+  // bounding box of the patches that some direction moves are traced, split
+  // evenly over all lanes (so a direction local to a few patches costs only
+  // their rays). The box is the same in every CTA.
+  __shared__ int s_box[4];
+  const bool coll = it.kind == FR_SOURCE_COLLIMATED;
+  const bool boxed = coll && !it.stats;
+  if (boxed) {
+    if (threadIdx.x == 0) {
+      s_box[0] = s_box[2] = 1 << 30;
+      s_box[1] = s_box[3] = -1;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < it.nsu * it.nsv; p += blockDim.x) {
+      if (s_mask[p]) {
+        const int k = p / it.nsv, l = p - k * it.nsv;
+        atomicMin(&s_box[0], k);
+        atomicMax(&s_box[1], k);
+        atomicMin(&s_box[2], l);
+        atomicMax(&s_box[3], l);
+      }
+    }
+  }
   build_lens_tables(it, ls);   // ends with __syncthreads
 
   const size_t cells = (size_t)it.ncol * it.nrow;
   const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
-  const bool coll = it.kind == FR_SOURCE_COLLIMATED;
   RayCount cnt{0u};
   unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
   uint64_t a0, a1;
-  lane_range(it, warps, &a0, &a1);
-  for (uint64_t id = a0; id < a1; ++id) {
+  uint32_t c0 = 0, bw = 1, r0 = 0;
+  if (boxed) {
+    if (s_box[1] < 0) return;   // no direction moves any patch: dE = 0
+    // grid cells [c0, c1) x [r0, r1) whose u (v) interval meets the box's patches
+    c0 = (uint32_t)(((uint64_t)s_box[0] * it.cols) / it.nsu);
+    const uint64_t c1w = ((uint64_t)(s_box[1] + 1) * it.cols + it.nsu - 1) / it.nsu;
+    const uint32_t c1 = (uint32_t)(c1w < (uint64_t)it.cols ? c1w : (uint64_t)it.cols);
+    r0 = (uint32_t)(((uint64_t)s_box[2] * it.rows) / it.nsv);
+    const uint64_t r1w = ((uint64_t)(s_box[3] + 1) * it.rows + it.nsv - 1) / it.nsv;
+    const uint32_t r1 = (uint32_t)(r1w < (uint64_t)it.rows ? r1w : (uint64_t)it.rows);
+    bw = c1 - c0;
+    const uint64_t V = (uint64_t)bw * (r1 - r0);
+    const uint64_t W = (uint64_t)(it.cta_end - it.cta_begin) * (uint64_t)warps;
+    const uint64_t gw = (uint64_t)((int)blockIdx.x - it.cta_begin) * (uint64_t)warps + (threadIdx.x >> 5);
+    const uint64_t w0 = V * gw / W, w1 = V * (gw + 1) / W;
+    const uint64_t lane = threadIdx.x & 31;
+    a0 = w0 + (w1 - w0) * lane / 32;
+    a1 = w0 + (w1 - w0) * (lane + 1) / 32;
+  } else {
+    lane_range(it, warps, &a0, &a1);
+  }
+  for (uint64_t j = a0; j < a1; ++j) {
     RayFwd r;
     uint32_t m;
+    uint64_t id = j;
+    if (boxed) {
+      const uint64_t rr = j / bw;
+      id = (uint64_t)(r0 + rr) * it.cols + (c0 + (j - rr * bw));
+      if (id < it.ray_begin || id >= it.ray_end) continue;
+    }
     if (coll) {
       // A collimated ray's patch is known before the trace: rays on patches no
       // direction moves contribute nothing and are only counted.
