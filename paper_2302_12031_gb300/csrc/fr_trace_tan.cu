@@ -11,11 +11,25 @@
 // sum_ab N_a N'_b dP (for a point source also the hit's shift along the ray by
 // the implicit function theorem), go through ray_tangent, and
 //   dE_ij += (dw F_ij + w (dF_ij/dX dX + dF_ij/dY dY)) / (w_x w_y)
-// is added to the nu x nu footprint of direction k with global atomics.
+// is added to the nu x nu footprint of direction k with global atomics (for a
+// single direction summed first in registers while a lane's footprint stays).
 #include "fr_device.cuh"
 
 namespace fr {
 namespace {
+
+// Adds a lane's register footprint to the map (one direction) and clears it.
+template <int NU>
+__device__ __forceinline__ void flush_acc(float (&acc)[NU][NU], int ie, int je, float* dE, int ncol) {
+  if (ie < 0) return;
+#pragma unroll
+  for (int b = 0; b < NU; ++b)
+#pragma unroll
+    for (int a = 0; a < NU; ++a) {
+      if (acc[b][a] != 0.0f) atomicAdd(dE + (size_t)(je + b) * ncol + ie + a, acc[b][a]);
+      acc[b][a] = 0.0f;
+    }
+}
 
 template <int NU>
 __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item it, int warps,
@@ -92,6 +106,12 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
   } else {
     lane_range(it, warps, &a0, &a1);
   }
+  float acc[NU][NU];
+#pragma unroll
+  for (int b = 0; b < NU; ++b)
+#pragma unroll
+    for (int a = 0; a < NU; ++a) acc[b][a] = 0.0f;
+  int acc_ie = -1, acc_je = -1;
   for (uint64_t j = a0; j < a1; ++j) {
     RayFwd r;
     uint32_t m;
@@ -188,6 +208,22 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
                                 fmaf(slope_t, dt, dZt));
       }
       const float cw = tg.dw * it.inv_area, cx = K * tg.dX, cy = K * tg.dY;
+      if (n_dirs == 1) {
+        // One direction: consecutive rays of a lane mostly share a footprint;
+        // sum them in registers and flush when the footprint moves.
+        if (f.ie != acc_ie || f.je != acc_je) {
+          flush_acc<NU>(acc, acc_ie, acc_je, dE, it.ncol);
+          acc_ie = f.ie;
+          acc_je = f.je;
+        }
+#pragma unroll
+        for (int b = 0; b < NU; ++b) {
+          const float rb = cw * Fy[b], sb = cx * Fy[b], tb = cy * gy[b];
+#pragma unroll
+          for (int a = 0; a < NU; ++a) acc[b][a] += fmaf(rb, Fx[a], fmaf(sb, gx[a], tb * Fx[a]));
+        }
+        continue;
+      }
       float* base = dE + (size_t)q * cells + (size_t)f.je * it.ncol + f.ie;
 #pragma unroll
       for (int b = 0; b < NU; ++b) {
@@ -200,6 +236,7 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       }
     }
   }
+  flush_acc<NU>(acc, acc_ie, acc_je, dE, it.ncol);
   cnt.reduce_into(cnt_dst);
   __syncthreads();
   RayCount::publish(s_cnt, it.stats);
