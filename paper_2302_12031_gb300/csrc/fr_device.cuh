@@ -114,8 +114,23 @@ struct LensSmem {
   float4* patch;   // [nsu*nsv][4]: row e holds C[e][0..3] of Z = sum_{e,f} C[e][f] s^e t^f
   float4* bu;      // [nsu][4]: coefficients of N_{k+a}(s) in powers of s
   float4* bv;      // [nsv][4]
-  float* zb;       // [2]: min and max control height (convex hull, Sec. 2.1.2)
+  int* zkey;       // [2]: min and max control height (convex hull, Sec. 2.1.2) as
+                   // order-preserving integer keys (point sources only; see zbounds)
 };
+
+// Float <-> int key with the same order (for shared-memory atomicMin/Max).
+__device__ __forceinline__ int float_key(float f) {
+  const int b = __float_as_int(f);
+  return b ^ ((b >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+
+// The convex-hull bounds of the control heights (valid after build_lens_tables
+// for point-source items).
+__device__ __forceinline__ void zbounds(const LensSmem& s, float* zmin, float* zmax) {
+  *zmin = key_float(s.zkey[0]);
+  *zmax = key_float(s.zkey[1]);
+}
 
 __host__ __device__ inline size_t lens_smem_bytes(int nsu, int nsv) {
   return (size_t)(nsu * nsv + nsu + nsv) * 4 * sizeof(float4) + 16;
@@ -126,14 +141,21 @@ __device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv) {
   s.patch = reinterpret_cast<float4*>(base);
   s.bu = s.patch + nsu * nsv * 4;
   s.bv = s.bu + nsu * 4;
-  s.zb = reinterpret_cast<float*>(s.bv + nsv * 4);
+  s.zkey = reinterpret_cast<int*>(s.bv + nsv * 4);
   return s;
 }
 
 // Every thread of the CTA takes part; ends with __syncthreads.
 //   Z(s,t) = sum_{a,b} N_{k+a}(s) N_{l+b}(t) P^z_{k+a,l+b} = sum_{e,f} C[e][f] s^e t^f,
 //   C[e][f] = sum_a sum_b Bu[a][e] Bv[b][f] P^z_{k+a,l+b}.
+// For point sources the min and max control height come out of the same
+// loads (every control point lies in some patch's 4x4 window).
 __device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
+  const bool bounds = it.kind == FR_SOURCE_POINT;
+  if (bounds && threadIdx.x == 0) {
+    s.zkey[0] = 0x7fffffff;
+    s.zkey[1] = (int)0x80000000;
+  }
   for (int q = threadIdx.x; q < it.nsu + it.nsv; q += blockDim.x) {
     const bool isu = q < it.nsu;
     const int k = isu ? q : q - it.nsu;
@@ -143,25 +165,9 @@ __device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) dst[a] = B[a];
   }
-  if (threadIdx.x < 32) {
-    float zmn = INFINITY, zmx = -INFINITY;
-    for (int q = threadIdx.x; q < it.ncu * it.ncv; q += 32) {
-      const float z = __ldg(it.ctrl + q);
-      zmn = fminf(zmn, z);
-      zmx = fmaxf(zmx, z);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      zmn = fminf(zmn, __shfl_xor_sync(0xffffffffu, zmn, o));
-      zmx = fmaxf(zmx, __shfl_xor_sync(0xffffffffu, zmx, o));
-    }
-    if (threadIdx.x == 0) {
-      s.zb[0] = zmn;
-      s.zb[1] = zmx;
-    }
-  }
   __syncthreads();
   const int npatch = it.nsu * it.nsv;
+  float zmn = INFINITY, zmx = -INFINITY;
   for (int p = threadIdx.x; p < npatch; p += blockDim.x) {
     const int k = p / it.nsv, l = p - k * it.nsv;
     float T[4][4];   // T[a][f] = sum_b P[k+a][l+b] Bv_l[b][f]
@@ -171,6 +177,8 @@ __device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const float P = __ldg(it.ctrl + (k + a) * it.ncv + (l + b));
+        zmn = fminf(zmn, P);
+        zmx = fmaxf(zmx, P);
         const float4 q = s.bv[l * 4 + b];
         c0 = fmaf(P, q.x, c0);
         c1 = fmaf(P, q.y, c1);
@@ -190,6 +198,17 @@ __device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
       for (int f = 0; f < 4; ++f)
         c[f] = fmaf(ue[e][0], T[0][f], fmaf(ue[e][1], T[1][f], fmaf(ue[e][2], T[2][f], ue[e][3] * T[3][f])));
       out[e] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+  }
+  if (bounds) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      zmn = fminf(zmn, __shfl_xor_sync(0xffffffffu, zmn, o));
+      zmx = fmaxf(zmx, __shfl_xor_sync(0xffffffffu, zmx, o));
+    }
+    if ((threadIdx.x & 31) == 0 && zmn <= zmx) {
+      atomicMin(&s.zkey[0], float_key(zmn));
+      atomicMax(&s.zkey[1], float_key(zmx));
     }
   }
   __syncthreads();

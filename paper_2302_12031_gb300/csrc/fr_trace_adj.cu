@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(const __grid_constant__ Laun
     if (unit > 0.0f) frexpf(unit, &e);
     go.fixP = unit > 0.0f ? ldexpf(1.0f, 40 - e) : 1.0f;
   }
-  const float zmin = ls.zb[0], zmax = ls.zb[1];
+  float zmin = 0.0f, zmax = 0.0f;
+  if (it.kind == FR_SOURCE_POINT) zbounds(ls, &zmin, &zmax);
   uint64_t a, b;
   lane_range(it, L.warps, &a, &b);
   RayCount cnt;

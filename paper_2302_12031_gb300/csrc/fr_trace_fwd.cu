@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
   if (threadIdx.x < 4) s_bb[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
   build_lens_tables(it, ls);   // ends with __syncthreads
-  const float zmin = ls.zb[0], zmax = ls.zb[1];
+  float zmin = 0.0f, zmax = 0.0f;
+  if (it.kind == FR_SOURCE_POINT) zbounds(ls, &zmin, &zmax);
   RayCount cnt;
   cnt.on_screen = 0u;
   unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
@@ -248,7 +249,9 @@ __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, 
     const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
     trace_collimated(it, ls, row, col, id, 1.0f / (float)it.cols, 1.0f / (float)it.rows, r);
   } else {
-    trace_point(it, ls, id, ls.zb[0], ls.zb[1], r);
+    float zmin, zmax;
+    zbounds(ls, &zmin, &zmax);
+    trace_point(it, ls, id, zmin, zmax, r);
   }
   fr_ray_record rec;
   rec.status = r.status;

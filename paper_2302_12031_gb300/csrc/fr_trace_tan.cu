@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       patch_eval(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Z, &Zs, &Zt);
       collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zs, Zt, r);
     } else {
-      trace_point(it, ls, id, ls.zb[0], ls.zb[1], r);
+      float zmin, zmax;
+      zbounds(ls, &zmin, &zmax);
+      trace_point(it, ls, id, zmin, zmax, r);
       m = 0u;
       if (r.status == FR_RAY_ON_SCREEN) {
         m = s_mask[r.k * it.nsv + r.l];
