@@ -85,6 +85,11 @@ typedef struct or_problem {
   int32_t mesh_nu;
   int32_t mesh_nv;
   int32_t pad_;
+  // Optional freeform entry face (both faces optimised, Sec. 4): heights
+  // P_in (n1_in+1) x (n2_in+1) of a second B-spline height field of degrees
+  // (p,q) over the same aperture; NULL = the flat entry face z = z_in.
+  const double* P_in;
+  int32_t n1_in, n2_in;
 } or_problem;
 
 typedef struct or_record {
@@ -292,6 +297,9 @@ struct Problem {
   or_problem d;
   std::vector<double> U, V;   // knot vectors in u and v
   double zmin, zmax;          // convex-hull bounds of Z (Sec. 2.1.2)
+  bool two_face = false;      // freeform entry face
+  std::vector<double> Uin, Vin;
+  double zmin_in = 0.0, zmax_in = 0.0;
   double wx, wy;              // pixel size (Sec. 2.3)
   double Rsx, Rsy;            // effective screen radii R* with ghost pixels
   int ncol, nrow;             // extended grid: (nx+nu_x-1) columns, (ny+nu_y-1) rows
@@ -304,7 +312,7 @@ struct Problem {
 };
 
 template <class T>
-void surface(const Problem& pb, const T& u, const T& v, int si, int sj, T* Z, T* Zu, T* Zv);
+void surface(const Problem& pb, const T& u, const T& v, int si, int sj, T* Z, T* Zu, T* Zv, int face = 0);
 
 bool make_problem(const or_problem* in, Problem* pb) {
   pb->d = *in;
@@ -327,6 +335,17 @@ bool make_problem(const or_problem* in, Problem* pb) {
   pb->ncol = d.nx + d.nu_x - 1;
   pb->nrow = d.ny + d.nu_y - 1;
   pb->omega0 = d.flux / (double)d.n_rays;
+  if (d.P_in) {
+    if (d.n1_in < d.p || d.n2_in < d.q || d.mesh_nu > 0) return false;
+    pb->two_face = true;
+    pb->Uin = clamped_uniform_knots(d.n1_in, d.p);
+    pb->Vin = clamped_uniform_knots(d.n2_in, d.q);
+    pb->zmin_in = pb->zmax_in = d.P_in[0];
+    for (int k = 0; k < (d.n1_in + 1) * (d.n2_in + 1); ++k) {
+      pb->zmin_in = std::min(pb->zmin_in, d.P_in[k]);
+      pb->zmax_in = std::max(pb->zmax_in, d.P_in[k]);
+    }
+  }
   if (d.mesh_nu < 0 || d.mesh_nv < 0 || (d.mesh_nu > 0) != (d.mesh_nv > 0)) return false;
   if (d.mesh_nu > 0) {
     pb->NU = (d.n1 - d.p + 1) * d.mesh_nu;
@@ -342,28 +361,33 @@ bool make_problem(const or_problem* in, Problem* pb) {
   return true;
 }
 
-// Control height P^z_ij as a T; inside the seeded (p+1)x(q+1) window starting at
-// (si, sj) it carries the unit derivative direction (i-si)*(q+1) + (j-sj).
+// Control height P^z_ij of face `face` (0 exit, 1 entry) as a T; inside the
+// seeded (p+1)x(q+1) window starting at (si, sj) it carries the unit derivative
+// direction (i-si)*(q+1) + (j-sj), offset by (p+1)(q+1) for the entry face.
 template <class T>
-T ctrl(const Problem& pb, int i, int j, int si, int sj) {
-  T c(pb.d.P[i * (pb.d.n2 + 1) + j]);
+T ctrl(const Problem& pb, int i, int j, int si, int sj, int face = 0) {
+  const int n2 = face ? pb.d.n2_in : pb.d.n2;
+  T c((face ? pb.d.P_in : pb.d.P)[i * (n2 + 1) + j]);
   const int a = i - si, b = j - sj;
-  if (si >= 0 && a >= 0 && a <= pb.d.p && b >= 0 && b <= pb.d.q) seed_dir(c, a * (pb.d.q + 1) + b);
+  if (si >= 0 && a >= 0 && a <= pb.d.p && b >= 0 && b <= pb.d.q)
+    seed_dir(c, face * (pb.d.p + 1) * (pb.d.q + 1) + a * (pb.d.q + 1) + b);
   return c;
 }
 
-// Eq. Bsplinesurfacedef for the z coordinate, summed over every control point,
-// with the first partial derivatives in u and v.
+// Eq. Bsplinesurfacedef for the z coordinate of face `face`, summed over every
+// control point, with the first partial derivatives in u and v.
 template <class T>
-void surface(const Problem& pb, const T& u, const T& v, int si, int sj, T* Z, T* Zu, T* Zv) {
-  const int n1 = pb.d.n1, n2 = pb.d.n2, p = pb.d.p, q = pb.d.q;
+void surface(const Problem& pb, const T& u, const T& v, int si, int sj, T* Z, T* Zu, T* Zv, int face) {
+  const int n1 = face ? pb.d.n1_in : pb.d.n1, n2 = face ? pb.d.n2_in : pb.d.n2, p = pb.d.p, q = pb.d.q;
+  const std::vector<double>& U = face ? pb.Uin : pb.U;
+  const std::vector<double>& V = face ? pb.Vin : pb.V;
   std::vector<T> Nu(n1 + 1), dNu(n1 + 1), Nv(n2 + 1), dNv(n2 + 1);
-  for (int i = 0; i <= n1; ++i) { Nu[i] = basis(pb.U, i, p, u); dNu[i] = basis_deriv(pb.U, i, p, u); }
-  for (int j = 0; j <= n2; ++j) { Nv[j] = basis(pb.V, j, q, v); dNv[j] = basis_deriv(pb.V, j, q, v); }
+  for (int i = 0; i <= n1; ++i) { Nu[i] = basis(U, i, p, u); dNu[i] = basis_deriv(U, i, p, u); }
+  for (int j = 0; j <= n2; ++j) { Nv[j] = basis(V, j, q, v); dNv[j] = basis_deriv(V, j, q, v); }
   T z(0.0), zu(0.0), zv(0.0);
   for (int i = 0; i <= n1; ++i) {
     for (int j = 0; j <= n2; ++j) {
-      const T P = ctrl<T>(pb, i, j, si, sj);
+      const T P = ctrl<T>(pb, i, j, si, sj, face);
       z = z + Nu[i] * Nv[j] * P;
       zu = zu + dNu[i] * Nv[j] * P;
       zv = zv + Nu[i] * dNv[j] * P;
@@ -444,6 +468,8 @@ template <class T>
 struct RayState {
   int status = OR_OK;
   int span_i = -1, span_j = -1;
+  int span_in_i = -1, span_in_j = -1;   // freeform entry face: knot span of the entry point
+  double t_in = 0.0;                     // point source, freeform entry: ray parameter of the entry point
   T u, v, x, y, z;
   T d[3];       // in-glass direction
   T tdir[3];    // direction after the freeform
@@ -460,27 +486,15 @@ struct GlassRay {
   double T1;     // Schlick transmission at the entry face
 };
 
+// The ray of a point source: origin S (the source of the grid that emits it)
+// and unit direction d0, uniform in the cone (Sec. 2.2.1).
+void source_ray(const Problem& pb, uint64_t id, double S[3], double d0[3]);
+
 GlassRay point_ray_in_glass(const Problem& pb, uint64_t id) {
   const or_problem& d = pb.d;
   GlassRay g{};
-  double xi1, xi2;
-  ray_uniforms(d.seed, id, &xi1, &xi2);
-  // Which point source of the grid emits this ray (rays split evenly).
-  const uint64_t n_src = (uint64_t)d.grid_nx * (uint64_t)d.grid_ny;
-  const uint64_t per_src = d.n_rays / n_src;
-  uint64_t s = id / per_src;
-  if (s >= n_src) s = n_src - 1;
-  const int sx = (int)(s % (uint64_t)d.grid_nx), sy = (int)(s / (uint64_t)d.grid_nx);
-  double S[3] = {d.src_pos[0], d.src_pos[1], d.src_pos[2]};
-  if (d.grid_nx > 1) S[0] += -0.5 * d.grid_w + sx * d.grid_w / (d.grid_nx - 1);
-  if (d.grid_ny > 1) S[1] += -0.5 * d.grid_h + sy * d.grid_h / (d.grid_ny - 1);
-  // Uniform sampling of the spherical cap: theta ~ U[0,2pi), cos phi = 1-(1-cos phi_max) a.
-  const double pi = 3.14159265358979323846;
-  const double theta = 2.0 * pi * xi1;
-  const double one_minus_cos = (1.0 - std::cos(d.half_angle)) * xi2;
-  const double cos_phi = 1.0 - one_minus_cos;
-  const double sin_phi = std::sqrt(one_minus_cos * (2.0 - one_minus_cos));
-  const double d0[3] = {std::cos(theta) * sin_phi, std::sin(theta) * sin_phi, cos_phi};
+  double S[3], d0[3];
+  source_ray(pb, id, S, d0);
   // Flat entry face z = z_in.
   const double tau = (d.z_in - S[2]) / d0[2];
   g.o[0] = S[0] + tau * d0[0];
@@ -496,6 +510,32 @@ GlassRay point_ray_in_glass(const Problem& pb, uint64_t id) {
   g.T1 = schlick_transmission<double>(1.0, d.n_glass, d0[2]);  // cos in air = incident angle
   g.status = OR_OK;
   return g;
+}
+
+void source_ray(const Problem& pb, uint64_t id, double S[3], double d0[3]) {
+  const or_problem& d = pb.d;
+  double xi1, xi2;
+  ray_uniforms(d.seed, id, &xi1, &xi2);
+  // Which point source of the grid emits this ray (rays split evenly).
+  const uint64_t n_src = (uint64_t)d.grid_nx * (uint64_t)d.grid_ny;
+  const uint64_t per_src = d.n_rays / n_src;
+  uint64_t s = id / per_src;
+  if (s >= n_src) s = n_src - 1;
+  const int sx = (int)(s % (uint64_t)d.grid_nx), sy = (int)(s / (uint64_t)d.grid_nx);
+  S[0] = d.src_pos[0];
+  S[1] = d.src_pos[1];
+  S[2] = d.src_pos[2];
+  if (d.grid_nx > 1) S[0] += -0.5 * d.grid_w + sx * d.grid_w / (d.grid_nx - 1);
+  if (d.grid_ny > 1) S[1] += -0.5 * d.grid_h + sy * d.grid_h / (d.grid_ny - 1);
+  // Uniform sampling of the spherical cap: theta ~ U[0,2pi), cos phi = 1-(1-cos phi_max) a.
+  const double pi = 3.14159265358979323846;
+  const double theta = 2.0 * pi * xi1;
+  const double one_minus_cos = (1.0 - std::cos(d.half_angle)) * xi2;
+  const double cos_phi = 1.0 - one_minus_cos;
+  const double sin_phi = std::sqrt(one_minus_cos * (2.0 - one_minus_cos));
+  d0[0] = std::cos(theta) * sin_phi;
+  d0[1] = std::sin(theta) * sin_phi;
+  d0[2] = cos_phi;
 }
 
 // f(t) = Z(o_uv + d_uv t) - d_z t - o_z (Eq. surfaceintersect).
@@ -648,36 +688,176 @@ MeshHit mesh_intersect(const Problem& pb, const GlassRay& g) {
   return h;
 }
 
-// Trace one ray. For T = double the root is found here by find_root(); for
-// T = Dual the FP64 root `t_root_in` of an earlier double trace is reused and
-// its derivative follows from the implicit function theorem applied to
-// Eq. surfaceintersect: dt/dP = -(df/dP)/(df/dt), evaluated at the root.
+// A freeform entry face seen from a point source: f_in(t) = Z_in(S_uv + d0_uv t)
+// - S_z - d0_z t. The entry point is its smallest positive root over the entry
+// net's convex-hull slab; the ray must be over the domain [0,1]^2 at the bottom
+// of the slab and stay over it until the root, else it misses the aperture (or
+// meets the side of the lens first).
+double f_entry(const Problem& pb, const double S[3], const double d0[3], double t) {
+  double u = x_to_u<double>(pb, S[0] + d0[0] * t);
+  double v = y_to_v<double>(pb, S[1] + d0[1] * t);
+  u = std::min(1.0, std::max(0.0, u));
+  v = std::min(1.0, std::max(0.0, v));
+  double Z, Zu, Zv;
+  surface<double>(pb, u, v, -1, -1, &Z, &Zu, &Zv, 1);
+  return Z - d0[2] * t - S[2];
+}
+
+int find_entry_root(const Problem& pb, const double S[3], const double d0[3], double* t_root) {
+  const double pad = 1e-12 * (1.0 + std::max(std::fabs(pb.zmin_in), std::fabs(pb.zmax_in)));
+  const double t_lo = std::max(0.0, (pb.zmin_in - pad - S[2]) / d0[2]);
+  const double t_hi = (pb.zmax_in + pad - S[2]) / d0[2];
+  const double u0 = x_to_u<double>(pb, S[0] + d0[0] * t_lo), v0 = y_to_v<double>(pb, S[1] + d0[1] * t_lo);
+  if (!(u0 >= 0.0 && u0 <= 1.0 && v0 >= 0.0 && v0 <= 1.0)) return OR_APERTURE_MISS;
+  const double ou = x_to_u<double>(pb, S[0]), ov = y_to_v<double>(pb, S[1]);
+  const double du = d0[0] / (2.0 * pb.d.rx), dv = d0[1] / (2.0 * pb.d.ry);
+  double t_dom = INFINITY;
+  if (du > 0) t_dom = std::min(t_dom, (1.0 - ou) / du);
+  if (du < 0) t_dom = std::min(t_dom, (0.0 - ou) / du);
+  if (dv > 0) t_dom = std::min(t_dom, (1.0 - ov) / dv);
+  if (dv < 0) t_dom = std::min(t_dom, (0.0 - ov) / dv);
+  const double t_end = std::min(t_hi, t_dom);
+  double f_prev = f_entry(pb, S, d0, t_lo);
+  if (f_prev < 0.0) return OR_INVALID;   // the source lies above the entry face here
+  if (f_prev == 0.0) { *t_root = t_lo; return OR_OK; }
+  const int M = std::max(16, pb.d.scan_points);
+  double t_prev = t_lo;
+  for (int k = 1; k <= M; ++k) {
+    const double t = (k == M) ? t_end : t_lo + (t_end - t_lo) * k / M;
+    const double f = f_entry(pb, S, d0, t);
+    if (f <= 0.0) {
+      double a = t_prev, b = t;
+      for (int it = 0; it < 200 && b - a > 1e-15 * std::max(1.0, b); ++it) {
+        const double m = 0.5 * (a + b);
+        if (f_entry(pb, S, d0, m) > 0.0) a = m; else b = m;
+      }
+      *t_root = 0.5 * (a + b);
+      return OR_OK;
+    }
+    t_prev = t;
+  }
+  return OR_APERTURE_MISS;   // left the domain through the side before entering
+}
+
+// Refraction air -> glass at a freeform entry face with slopes (Zu, Zv): the
+// normal (-Z_x, -Z_y, 1)/|.| points into the glass; Schlick takes the incident
+// cosine (the one in air). Never total internal reflection (into the denser medium).
 template <class T>
-void trace_ray(const Problem& pb, uint64_t id, int si, int sj, double t_root_in, RayState<T>* r) {
+void entry_refract(const Problem& pb, const T d0[3], const T& Zu, const T& Zv, T dg[3], T* T1) {
+  const T mx = -Zu / (2.0 * pb.d.rx), my = -Zv / (2.0 * pb.d.ry);
+  const T len = sqrt(mx * mx + my * my + 1.0);
+  const T nrm[3] = {mx / len, my / len, 1.0 / len};
+  const T ci = d0[0] * nrm[0] + d0[1] * nrm[1] + d0[2] * nrm[2];
+  T cos_t;
+  refract<T>(d0, nrm, 1.0 / pb.d.n_glass, dg, &cos_t);
+  *T1 = schlick_transmission<T>(1.0, pb.d.n_glass, ci);
+}
+
+// Where a seeded pass starts from: the derivative windows of both faces and
+// the FP64 roots of an earlier double pass of the same ray.
+struct Seeds {
+  int si = -1, sj = -1, si_in = -1, sj_in = -1;
+  double t = 0.0, t_in = 0.0;
+};
+
+template <class T>
+Seeds seeds_of(const Problem& pb, const RayState<T>& r) {
+  Seeds s;
+  s.si = r.span_i - pb.d.p;
+  s.sj = r.span_j - pb.d.q;
+  if (pb.two_face) {
+    s.si_in = r.span_in_i - pb.d.p;
+    s.sj_in = r.span_in_j - pb.d.q;
+  }
+  s.t = r.t;
+  s.t_in = r.t_in;
+  return s;
+}
+
+// Trace one ray. For T = double every root is found here (find_root,
+// find_entry_root, mesh_intersect); for T = Dual the FP64 roots of an earlier
+// double trace (in `sd`) are reused and their derivatives follow from the
+// implicit function theorem applied at the root (one Newton step in dual
+// arithmetic from an exact root gives dt/dP = -(df/dP)/(df/dt)).
+template <class T>
+void trace_ray(const Problem& pb, uint64_t id, const Seeds& sd, RayState<T>* r) {
   const or_problem& d = pb.d;
   constexpr bool is_value = std::is_same<T, double>::value;
-  double T1;
+  T T1;
   T Z, Zu, Zv;
+  T o[3], dg[3];            // the ray inside the glass: origin and direction
+  bool exit_root = true;    // false: a collimated ray through the flat entry face meets the exit face at (u,v)
+  GlassRay g{};
   if (d.src_kind == 0) {
-    // Collimated (Sec. 2.2.1): sample (u,v) on a square grid, d = (0,0,1); the
-    // ray starts on the freeform, so its hit is (X(u), Y(v), Z(u,v)).
+    // Collimated (Sec. 2.2.1): (u,v) on a square grid, direction (0,0,1).
     const uint64_t ix = id % (uint64_t)d.cols, iy = id / (uint64_t)d.cols;
     double a = 0.5, b = 0.5;
     if (d.jitter) ray_uniforms(d.seed, id, &a, &b);
-    r->u = T(((double)ix + a) / d.cols);
-    r->v = T(((double)iy + b) / d.rows);
-    r->x = (2.0 * r->u - 1.0) * d.rx;   // Eq. linearX
-    r->y = (2.0 * r->v - 1.0) * d.ry;   // Eq. linearY
-    r->d[0] = T(0.0); r->d[1] = T(0.0); r->d[2] = T(1.0);
-    T1 = schlick_transmission<double>(1.0, d.n_glass, 1.0);  // normal incidence on the flat face
-    surface<T>(pb, r->u, r->v, si, sj, &Z, &Zu, &Zv);
-    r->z = Z;
-  } else {
-    const GlassRay g = point_ray_in_glass(pb, id);
+    const double u = ((double)ix + a) / d.cols, v = ((double)iy + b) / d.rows;
+    if (!pb.two_face) {
+      // The ray starts on the freeform: its hit is (X(u), Y(v), Z(u,v)).
+      r->u = T(u);
+      r->v = T(v);
+      r->x = (2.0 * r->u - 1.0) * d.rx;   // Eq. linearX
+      r->y = (2.0 * r->v - 1.0) * d.ry;   // Eq. linearY
+      r->d[0] = T(0.0); r->d[1] = T(0.0); r->d[2] = T(1.0);
+      T1 = T(schlick_transmission<double>(1.0, d.n_glass, 1.0));  // normal incidence on the flat face
+      surface<T>(pb, r->u, r->v, sd.si, sd.sj, &Z, &Zu, &Zv, 0);
+      r->z = Z;
+      exit_root = false;
+    } else {
+      // Freeform entry face: the ray meets it at (X(u), Y(v), Z_in(u,v)).
+      T Zi, Ziu, Ziv;
+      surface<T>(pb, T(u), T(v), sd.si_in, sd.sj_in, &Zi, &Ziu, &Ziv, 1);
+      r->span_in_i = find_span(pb.Uin, d.n1_in, u);
+      r->span_in_j = find_span(pb.Vin, d.n2_in, v);
+      o[0] = T((2.0 * u - 1.0) * d.rx);
+      o[1] = T((2.0 * v - 1.0) * d.ry);
+      o[2] = Zi;
+      const T d0[3] = {T(0.0), T(0.0), T(1.0)};
+      entry_refract<T>(pb, d0, Ziu, Ziv, dg, &T1);
+    }
+  } else if (!pb.two_face) {
+    g = point_ray_in_glass(pb, id);
     if (g.status != OR_OK) { r->status = g.status; return; }
-    T1 = g.T1;
-    for (int c = 0; c < 3; ++c) r->d[c] = T(g.d[c]);
-    double t_root = t_root_in;
+    T1 = T(g.T1);
+    for (int c = 0; c < 3; ++c) {
+      o[c] = T(g.o[c]);
+      dg[c] = T(g.d[c]);
+    }
+  } else {
+    double S[3], d0[3];
+    source_ray(pb, id, S, d0);
+    double t_in = sd.t_in;
+    if (is_value) {
+      const int st = find_entry_root(pb, S, d0, &t_in);
+      if (st != OR_OK) { r->status = st; return; }
+    }
+    r->t_in = t_in;
+    T ti(t_in);
+    T Zi, Ziu, Ziv;
+    if (!is_value) {
+      const T u0 = x_to_u<T>(pb, T(S[0] + d0[0] * t_in)), v0 = y_to_v<T>(pb, T(S[1] + d0[1] * t_in));
+      surface<T>(pb, u0, v0, sd.si_in, sd.sj_in, &Zi, &Ziu, &Ziv, 1);
+      const T f = Zi - d0[2] * t_in - S[2];
+      const double dfdt = val(Ziu) * d0[0] / (2.0 * d.rx) + val(Ziv) * d0[1] / (2.0 * d.ry) - d0[2];
+      ti = T(t_in) - f / dfdt;
+    }
+    for (int c = 0; c < 3; ++c) o[c] = S[c] + d0[c] * ti;
+    const T ue = x_to_u<T>(pb, o[0]), ve = y_to_v<T>(pb, o[1]);
+    r->span_in_i = find_span(pb.Uin, d.n1_in, std::min(1.0, std::max(0.0, val(ue))));
+    r->span_in_j = find_span(pb.Vin, d.n2_in, std::min(1.0, std::max(0.0, val(ve))));
+    surface<T>(pb, ue, ve, sd.si_in, sd.sj_in, &Zi, &Ziu, &Ziv, 1);
+    const T d0t[3] = {T(d0[0]), T(d0[1]), T(d0[2])};
+    entry_refract<T>(pb, d0t, Ziu, Ziv, dg, &T1);
+  }
+  if (exit_root) {
+    for (int c = 0; c < 3; ++c) {
+      r->d[c] = dg[c];
+      g.o[c] = val(o[c]);
+      g.d[c] = val(dg[c]);
+    }
+    double t_root = sd.t;
     MeshHit mh{};
     if (d.mesh_nu > 0) {
       // Triangle mesh (Sec. 2.2.2): the triangle is found in FP64; t is the
@@ -698,8 +878,8 @@ void trace_ray(const Problem& pb, uint64_t id, int si, int sj, double t_root_in,
         T zv[4];
         for (int c = 0; c < 4; ++c) {
           T Zn, Zun, Zvn;
-          surface<T>(pb, T((double)(mh.K + (c & 1)) / pb.NU), T((double)(mh.L + (c >> 1)) / pb.NV), si, sj, &Zn,
-                     &Zun, &Zvn);
+          surface<T>(pb, T((double)(mh.K + (c & 1)) / pb.NU), T((double)(mh.L + (c >> 1)) / pb.NV), sd.si, sd.sj,
+                     &Zn, &Zun, &Zvn, 0);
           zv[c] = Zn;
         }
         const double ou = x_to_u<double>(pb, g.o[0]), ov = y_to_v<double>(pb, g.o[1]);
@@ -707,20 +887,20 @@ void trace_ray(const Problem& pb, uint64_t id, int si, int sj, double t_root_in,
                      g.d[0] / (2.0 * d.rx), g.d[1] / (2.0 * d.ry), g.d[2]);
       }
     } else if (!is_value) {
-      const T u0 = x_to_u<T>(pb, T(g.o[0] + g.d[0] * t_root));
-      const T v0 = y_to_v<T>(pb, T(g.o[1] + g.d[1] * t_root));
-      surface<T>(pb, u0, v0, si, sj, &Z, &Zu, &Zv);
-      const T f = Z - g.d[2] * t_root - g.o[2];
+      const T u0 = x_to_u<T>(pb, o[0] + dg[0] * t_root);
+      const T v0 = y_to_v<T>(pb, o[1] + dg[1] * t_root);
+      surface<T>(pb, u0, v0, sd.si, sd.sj, &Z, &Zu, &Zv, 0);
+      const T f = Z - dg[2] * t_root - o[2];
       const double dfdt = val(Zu) * g.d[0] / (2.0 * d.rx) + val(Zv) * g.d[1] / (2.0 * d.ry) - g.d[2];
       t = T(t_root) - f / dfdt;
     }
     // The hit is on the ray: o + d t.
-    r->x = g.o[0] + g.d[0] * t;
-    r->y = g.o[1] + g.d[1] * t;
-    r->z = g.o[2] + g.d[2] * t;
+    r->x = o[0] + dg[0] * t;
+    r->y = o[1] + dg[1] * t;
+    r->z = o[2] + dg[2] * t;
     r->u = x_to_u<T>(pb, r->x);
     r->v = y_to_v<T>(pb, r->y);
-    surface<T>(pb, r->u, r->v, si, sj, &Z, &Zu, &Zv);
+    surface<T>(pb, r->u, r->v, sd.si, sd.sj, &Z, &Zu, &Zv, 0);
   }
   // Knot span of the hit (for the derivative window and the records).
   if (!(d.src_kind != 0 && d.mesh_nu > 0)) {
@@ -789,23 +969,40 @@ void parallel_rays(uint64_t begin, uint64_t count, int nthreads, Body body) {
   for (auto& th : pool) th.join();
 }
 
+// The control heights as one parameter vector: the exit net's (n1+1)(n2+1)
+// heights, then (with a freeform entry face) the entry net's.
+int n_params(const Problem& pb) {
+  return (pb.d.n1 + 1) * (pb.d.n2 + 1) + (pb.two_face ? (pb.d.n1_in + 1) * (pb.d.n2_in + 1) : 0);
+}
+
+// Parameter index of derivative direction c of a ray traced with seeds sd
+// (directions: the exit window, then the entry window); -1 for unused ones.
+int param_index(const Problem& pb, const Seeds& sd, int c) {
+  const int w = (pb.d.p + 1) * (pb.d.q + 1);
+  const int face = c / w, cc = c % w;
+  if (face > (pb.two_face ? 1 : 0)) return -1;
+  const int a2 = cc / (pb.d.q + 1), b2 = cc % (pb.d.q + 1);
+  if (face == 0) return (sd.si + a2) * (pb.d.n2 + 1) + (sd.sj + b2);
+  return (pb.d.n1 + 1) * (pb.d.n2 + 1) + (sd.si_in + a2) * (pb.d.n2_in + 1) + (sd.sj_in + b2);
+}
+
 // Gradient of sum_ij dLdE_ij E_ij(P) with respect to P, with NT derivative
-// directions (NT >= (p+1)(q+1)).
+// directions (NT >= (p+1)(q+1), twice that with a freeform entry face).
 template <int NT>
 void gradient_impl(const Problem& pb, uint64_t begin, uint64_t count, const double* dLdE,
                    double* dLdP, int nthreads) {
-  const int nctrl = (pb.d.n1 + 1) * (pb.d.n2 + 1);
+  const int nctrl = n_params(pb);
   const int nthr = resolve_threads(nthreads);
   std::vector<std::vector<double>> part(nthr, std::vector<double>(nctrl, 0.0));
   parallel_rays(begin, count, nthr, [&](int k, uint64_t a, uint64_t b) {
     std::vector<double>& g = part[k];
     for (uint64_t id = a; id < b; ++id) {
       RayState<double> r0;
-      trace_ray<double>(pb, id, -1, -1, 0.0, &r0);
+      trace_ray<double>(pb, id, Seeds(), &r0);
       if (r0.status != OR_OK) continue;
-      const int si = r0.span_i - pb.d.p, sj = r0.span_j - pb.d.q;
+      const Seeds sd = seeds_of(pb, r0);
       RayState<Dual<NT>> r;
-      trace_ray<Dual<NT>>(pb, id, si, sj, r0.t, &r);
+      trace_ray<Dual<NT>>(pb, id, sd, &r);
       if (r.status != OR_OK) continue;
       double acc[NT];
       for (int c = 0; c < NT; ++c) acc[c] = 0.0;
@@ -814,9 +1011,10 @@ void gradient_impl(const Problem& pb, uint64_t begin, uint64_t count, const doub
         if (gbar == 0.0) return;
         for (int c = 0; c < NT; ++c) acc[c] += gbar * e.d[c];
       });
-      for (int a2 = 0; a2 <= pb.d.p; ++a2)
-        for (int b2 = 0; b2 <= pb.d.q; ++b2)
-          g[(si + a2) * (pb.d.n2 + 1) + (sj + b2)] += acc[a2 * (pb.d.q + 1) + b2];
+      for (int c = 0; c < NT; ++c) {
+        const int pi = param_index(pb, sd, c);
+        if (pi >= 0) g[pi] += acc[c];
+      }
     }
   });
   for (int c = 0; c < nctrl; ++c) dLdP[c] = 0.0;
@@ -830,7 +1028,7 @@ void gradient_impl(const Problem& pb, uint64_t begin, uint64_t count, const doub
 template <int NT>
 void tangent_impl(const Problem& pb, uint64_t begin, uint64_t count, const double* dP, int n_dirs, double* dE,
                   int nthreads) {
-  const int nctrl = (pb.d.n1 + 1) * (pb.d.n2 + 1);
+  const int nctrl = n_params(pb);
   const size_t ncell = (size_t)pb.ncol * pb.nrow;
   const int nthr = resolve_threads(nthreads);
   std::vector<std::vector<double>> part(nthr, std::vector<double>(ncell * n_dirs, 0.0));
@@ -839,20 +1037,20 @@ void tangent_impl(const Problem& pb, uint64_t begin, uint64_t count, const doubl
     std::vector<double> local((size_t)n_dirs * NT);
     for (uint64_t id = a; id < b; ++id) {
       RayState<double> r0;
-      trace_ray<double>(pb, id, -1, -1, 0.0, &r0);
+      trace_ray<double>(pb, id, Seeds(), &r0);
       if (r0.status != OR_OK) continue;
-      const int si = r0.span_i - pb.d.p, sj = r0.span_j - pb.d.q;
+      const Seeds sd = seeds_of(pb, r0);
       bool any = false;
       for (int q = 0; q < n_dirs; ++q)
         for (int c = 0; c < NT; ++c) {
-          const int a2 = c / (pb.d.q + 1), b2 = c % (pb.d.q + 1);
-          const double v = a2 <= pb.d.p ? dP[(size_t)q * nctrl + (si + a2) * (pb.d.n2 + 1) + (sj + b2)] : 0.0;
+          const int pi = param_index(pb, sd, c);
+          const double v = pi >= 0 ? dP[(size_t)q * nctrl + pi] : 0.0;
           local[(size_t)q * NT + c] = v;
           any = any || v != 0.0;
         }
       if (!any) continue;
       RayState<Dual<NT>> r;
-      trace_ray<Dual<NT>>(pb, id, si, sj, r0.t, &r);
+      trace_ray<Dual<NT>>(pb, id, sd, &r);
       if (r.status != OR_OK) continue;
       splat<Dual<NT>>(pb, r, [&](int i, int j, const Dual<NT>& ed) {
         for (int q = 0; q < n_dirs; ++q) {
@@ -949,7 +1147,7 @@ int32_t or_trace_records(const or_problem* prob, uint64_t begin, uint64_t count,
   parallel_rays(begin, count, resolve_threads(nthreads), [&](int, uint64_t a, uint64_t b) {
     for (uint64_t id = a; id < b; ++id) {
       RayState<double> r;
-      trace_ray<double>(pb, id, -1, -1, 0.0, &r);
+      trace_ray<double>(pb, id, Seeds(), &r);
       or_record& o = out[id - begin];
       std::memset(&o, 0, sizeof o);
       o.status = r.status;
@@ -985,7 +1183,7 @@ int32_t or_trace_forward(const or_problem* prob, uint64_t begin, uint64_t count,
     std::vector<double>& e = part[k];
     for (uint64_t id = a; id < b; ++id) {
       RayState<double> r;
-      trace_ray<double>(pb, id, -1, -1, 0.0, &r);
+      trace_ray<double>(pb, id, Seeds(), &r);
       st[k].counts[r.status] += 1;
       if (r.status != OR_OK) continue;
       splat<double>(pb, r, [&](int i, int j, double c) { e[(size_t)j * pb.ncol + i] += c; });
@@ -1008,7 +1206,7 @@ int32_t or_trace_gradient(const or_problem* prob, uint64_t begin, uint64_t count
                           double* dLdP, int32_t nthreads) {
   Problem pb;
   if (!make_problem(prob, &pb)) return -1;
-  const int ndir = (pb.d.p + 1) * (pb.d.q + 1);
+  const int ndir = (pb.d.p + 1) * (pb.d.q + 1) * (pb.two_face ? 2 : 1);
   if (ndir <= 16) gradient_impl<16>(pb, begin, count, dLdE, dLdP, nthreads);
   else if (ndir <= 36) gradient_impl<36>(pb, begin, count, dLdE, dLdP, nthreads);
   else return -1;
@@ -1021,7 +1219,7 @@ int32_t or_trace_tangent(const or_problem* prob, uint64_t begin, uint64_t count,
                          double* dE, int32_t nthreads) {
   Problem pb;
   if (!make_problem(prob, &pb) || n_dirs < 1) return -1;
-  const int ndir = (pb.d.p + 1) * (pb.d.q + 1);
+  const int ndir = (pb.d.p + 1) * (pb.d.q + 1) * (pb.two_face ? 2 : 1);
   if (ndir <= 16) tangent_impl<16>(pb, begin, count, dP, n_dirs, dE, nthreads);
   else if (ndir <= 36) tangent_impl<36>(pb, begin, count, dP, n_dirs, dE, nthreads);
   else return -1;

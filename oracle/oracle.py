@@ -32,6 +32,7 @@ class Problem(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("nu_x", C.c_int32), ("nu_y", C.c_int32),
         ("alpha", C.c_double), ("scan_points", C.c_int32),
         ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32), ("pad_", C.c_int32),
+        ("P_in", C.POINTER(C.c_double)), ("n1_in", C.c_int32), ("n2_in", C.c_int32),
     ]
 
 
@@ -118,7 +119,7 @@ class OracleProblem:
     `P` overrides the workload's control heights (e.g. for finite differences).
     """
 
-    def __init__(self, wl, P=None, scan_points=1024):
+    def __init__(self, wl, P=None, scan_points=1024, P_in=None):
         lens, src, tgt = wl["lens"], wl["source"], wl["target"]
         self.P = _f64(lens["P"] if P is None else P).reshape(lens["n1"] + 1, lens["n2"] + 1)
         s = Problem()
@@ -143,6 +144,12 @@ class OracleProblem:
         s.scan_points = scan_points
         mesh = wl.get("mesh", (0, 0))
         s.mesh_nu, s.mesh_nv = mesh
+        # optional freeform entry face; P_in overrides its heights
+        self.P_in = None
+        if lens.get("P_in") is not None or P_in is not None:
+            self.P_in = _f64(lens["P_in"] if P_in is None else P_in).reshape(lens["n1_in"] + 1, lens["n2_in"] + 1)
+            s.P_in = _dptr(self.P_in)
+            s.n1_in, s.n2_in = lens["n1_in"], lens["n2_in"]
         self.s = s
         self.ext_shape = (tgt["ny"] + tgt["nu_y"] - 1, tgt["nx"] + tgt["nu_x"] - 1)
 
@@ -156,9 +163,9 @@ def _range(wl, begin, count):
     return int(begin), int(count)
 
 
-def trace_forward(wl, P=None, begin=0, count=None, nthreads=0):
+def trace_forward(wl, P=None, begin=0, count=None, nthreads=0, P_in=None):
     """(E on the extended grid, counts per status) for rays [begin, begin+count)."""
-    pb = OracleProblem(wl, P)
+    pb = OracleProblem(wl, P, P_in=P_in)
     begin, count = _range(wl, begin, count)
     E = np.zeros(pb.ext_shape)
     st = Stats()
@@ -168,9 +175,9 @@ def trace_forward(wl, P=None, begin=0, count=None, nthreads=0):
     return E, np.array(st.counts[:], dtype=np.int64)
 
 
-def trace_records(wl, P=None, begin=0, count=None, nthreads=0):
+def trace_records(wl, P=None, begin=0, count=None, nthreads=0, P_in=None):
     """Per-ray records (structured array, fields of RECORD_DTYPE)."""
-    pb = OracleProblem(wl, P)
+    pb = OracleProblem(wl, P, P_in=P_in)
     begin, count = _range(wl, begin, count)
     out = np.zeros(count, dtype=RECORD_DTYPE)
     rc = lib().or_trace_records(pb.ptr(), begin, count,
@@ -180,17 +187,21 @@ def trace_records(wl, P=None, begin=0, count=None, nthreads=0):
     return out
 
 
-def trace_gradient(wl, dLdE, P=None, begin=0, count=None, nthreads=0):
-    """dL/dP^z (shape (n1+1, n2+1)) for an upstream dL/dE on the extended grid."""
-    pb = OracleProblem(wl, P)
+def trace_gradient(wl, dLdE, P=None, begin=0, count=None, nthreads=0, P_in=None):
+    """dL/dP^z (shape (n1+1, n2+1)) for an upstream dL/dE on the extended grid;
+    with a freeform entry face the pair (dL/dP^z exit, dL/dP^z entry)."""
+    pb = OracleProblem(wl, P, P_in=P_in)
     begin, count = _range(wl, begin, count)
     g = _f64(dLdE)
     assert g.shape == pb.ext_shape
-    out = np.zeros_like(pb.P)
+    n_out = pb.P.size
+    out = np.zeros(n_out + (pb.P_in.size if pb.P_in is not None else 0))
     rc = lib().or_trace_gradient(pb.ptr(), begin, count, _dptr(g), _dptr(out), nthreads)
     if rc != 0:
         raise ValueError("oracle rejected the problem")
-    return out
+    if pb.P_in is None:
+        return out.reshape(pb.P.shape)
+    return out[:n_out].reshape(pb.P.shape), out[n_out:].reshape(pb.P_in.shape)
 
 
 def trace_tangent(wl, dP, P=None, begin=0, count=None, nthreads=0):
@@ -200,10 +211,16 @@ def trace_tangent(wl, dP, P=None, begin=0, count=None, nthreads=0):
     pb = OracleProblem(wl, P)
     begin, count = _range(wl, begin, count)
     d = _f64(dP)
-    single = d.ndim == 2
-    if single:
-        d = d[None]
-    assert d.shape[1:] == pb.P.shape
+    if pb.P_in is None:
+        single = d.ndim == 2
+        if single:
+            d = d[None]
+        assert d.shape[1:] == pb.P.shape
+    else:   # directions over the exit heights followed by the entry heights
+        single = d.ndim == 1
+        if single:
+            d = d[None]
+        assert d.shape[1] == pb.P.size + pb.P_in.size
     out = np.zeros((d.shape[0],) + pb.ext_shape)
     rc = lib().or_trace_tangent(pb.ptr(), begin, count, _dptr(d), d.shape[0], _dptr(out), nthreads)
     if rc != 0:

@@ -64,6 +64,18 @@ def _lens(n_ctrl, sigma, seed, base, z_in):
             "rx": 0.5, "ry": 0.5, "z_in": z_in, "n_glass": 1.5}
 
 
+def with_entry_face(wl, n_ctrl, sigma, seed):
+    """The workload with a freeform entry face (both faces optimised): a second
+    bicubic net of n_ctrl x n_ctrl heights z_in + N(0, sigma^2) over the same
+    aperture in place of the flat face z = z_in. Returns a new dict."""
+    out = dict(wl)
+    lens = dict(wl["lens"])
+    lens["n1_in"] = lens["n2_in"] = n_ctrl - 1
+    lens["P_in"] = control_heights(n_ctrl, n_ctrl, sigma, seed, lens["z_in"])
+    out["lens"] = lens
+    return out
+
+
 def _target(z_screen, R, bins):
     return {"z_screen": z_screen, "Rx": R, "Ry": R, "nx": bins, "ny": bins,
             "nu_x": 3, "nu_y": 3, "alpha": 1.0}
