@@ -83,6 +83,15 @@ typedef struct fr_lens_desc {
   float rx, ry;          /* half-widths of the lens */
   float z_in;            /* entry face; P^z > z_in keeps the lens valid (Sec. 2.1.2) */
   float n_glass;         /* refractive index of the lens; air outside */
+  /* Optional freeform entry face (both faces optimised, as the paper's
+   * conclusion proposes): NULL = the flat face z = z_in; else device,
+   * (entry_n1+1)*(entry_n2+1) heights of a second bicubic net over the same
+   * aperture (same layout as ctrl_z). The lens is valid where the entry face
+   * lies below the exit face. With an entry face, dL/dP outputs hold the exit
+   * net's gradient followed by the entry net's. Single-lens calls only (not
+   * in batches, not with the triangle mesh, not for fr_trace_tangent). */
+  const float* entry_ctrl_z;
+  int32_t entry_n1, entry_n2;
 } fr_lens_desc;
 
 /* Source (Sec. 2.2.1). Rays are numbered 0..n_rays-1; the initial weight of
@@ -188,7 +197,8 @@ fr_status fr_trace_forward(fr_handle* h, const fr_lens_desc* lens, const fr_sour
 
 /* Adjoint (reverse mode of the forward trace, Sec. 2.5): given dL/dE on the
  * extended grid (device), writes (or adds) dL/dP^z to dLdP_out (device,
- * (n1+1)*(n2+1)). Each ray's path is recomputed from its id and seed, not read
+ * (n1+1)*(n2+1), followed by (entry_n1+1)*(entry_n2+1) for a freeform entry
+ * face). Each ray's path is recomputed from its id and seed, not read
  * back; the arguments must equal those of the forward call. */
 fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
                            const fr_target_desc* target, uint64_t n_rays, uint64_t seed,

@@ -29,7 +29,8 @@ ALL_RAYS = 0xFFFFFFFFFFFFFFFF
 class LensDesc(C.Structure):
     _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("p", C.c_int32), ("q", C.c_int32),
                 ("ctrl_z", C.c_void_p), ("rx", C.c_float), ("ry", C.c_float),
-                ("z_in", C.c_float), ("n_glass", C.c_float)]
+                ("z_in", C.c_float), ("n_glass", C.c_float),
+                ("entry_ctrl_z", C.c_void_p), ("entry_n1", C.c_int32), ("entry_n2", C.c_int32)]
 
 
 class SourceDesc(C.Structure):
@@ -322,6 +323,14 @@ class Problem:
         assert self.ctrl_z.dtype == torch.float32 and self.ctrl_z.is_cuda
         self.lens = LensDesc(lens["n1"], lens["n2"], lens["p"], lens["q"], self.ctrl_z.data_ptr(),
                              lens["rx"], lens["ry"], lens["z_in"], lens["n_glass"])
+        # optional freeform entry face: its heights follow the exit heights in dL/dP
+        self.entry_z = None
+        self.entry_shape = None
+        if lens.get("P_in") is not None:
+            self.entry_z = torch.as_tensor(lens["P_in"], dtype=torch.float32, device=device).contiguous()
+            self.entry_shape = (lens["n1_in"] + 1, lens["n2_in"] + 1)
+            self.lens.entry_ctrl_z = self.entry_z.data_ptr()
+            self.lens.entry_n1, self.lens.entry_n2 = lens["n1_in"], lens["n2_in"]
         s = SourceDesc()
         if src["kind"] == "collimated":
             s.kind = FR_SOURCE_COLLIMATED
@@ -368,13 +377,23 @@ class Problem:
                          options, E, stats)
         return E
 
+    def n_params(self):
+        n = self.ctrl_shape[0] * self.ctrl_shape[1]
+        return n + (self.entry_shape[0] * self.entry_shape[1] if self.entry_shape else 0)
+
     def adjoint(self, dLdE, options=None, ray_begin=0, ray_count=ALL_RAYS, dLdP=None, stats=None, h=None):
+        """dL/dP (ctrl_shape); with a freeform entry face the pair (exit, entry)."""
         h = h or default_handle()
         if dLdP is None:
-            dLdP = torch.empty(self.ctrl_shape, dtype=torch.float32, device=self.device)
+            shape = self.ctrl_shape if self.entry_shape is None else (self.n_params(),)
+            dLdP = torch.empty(shape, dtype=torch.float32, device=self.device)
         fr_trace_adjoint(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                          options, dLdE.contiguous(), dLdP, stats)
-        return dLdP
+        if self.entry_shape is None:
+            return dLdP
+        flat = dLdP.reshape(-1)
+        n = self.ctrl_shape[0] * self.ctrl_shape[1]
+        return flat[:n].view(self.ctrl_shape), flat[n:].view(self.entry_shape)
 
     def tangent(self, dP, options=None, ray_begin=0, ray_count=ALL_RAYS, dE=None, stats=None, h=None):
         """Directional derivatives (dE/dP^z) dP: dP of shape (n_dirs, n1+1, n2+1) or

@@ -81,7 +81,7 @@ ItemWs plan(const Item& it, size_t at, bool det_fwd, bool det_adj) {
   w.efix = at;
   if (det_fwd) at = align_up(at + (size_t)it.ncol * it.nrow * sizeof(unsigned long long));
   w.pfix = at;
-  if (det_adj) at = align_up(at + (size_t)it.ncu * it.ncv * sizeof(unsigned long long));
+  if (det_adj) at = align_up(at + (size_t)it.nparam * sizeof(unsigned long long));
   w.gmax = at;
   at = align_up(at + sizeof(float));
   w.end = at;
@@ -148,6 +148,22 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   it->kv = (float)it->nsv / (2.0f * L->ry);
   const double nr = (L->n_glass - 1.0) / (L->n_glass + 1.0);
   it->R0 = (float)(nr * nr);
+  it->nparam = it->ncu * it->ncv;
+  if (L->entry_ctrl_z) {
+    if (L->entry_n1 < 3 || L->entry_n2 < 3 || L->entry_n1 + 1 > fr::kMaxCtrl || L->entry_n2 + 1 > fr::kMaxCtrl)
+      return set_error(h, FR_ERR_UNSUPPORTED, "entry net must be between 4x4 and %dx%d", fr::kMaxCtrl,
+                       fr::kMaxCtrl);
+    if (o.mesh_nu > 0) return set_error(h, FR_ERR_UNSUPPORTED, "the triangle mesh takes a flat entry face");
+    it->two_face = 1;
+    it->ctrl_in = L->entry_ctrl_z;
+    it->ncu_in = L->entry_n1 + 1;
+    it->ncv_in = L->entry_n2 + 1;
+    it->nsu_in = it->ncu_in - 3;
+    it->nsv_in = it->ncv_in - 3;
+    it->ku_in = (float)it->nsu_in / (2.0f * L->rx);
+    it->kv_in = (float)it->nsv_in / (2.0f * L->ry);
+    it->nparam += it->ncu_in * it->ncv_in;
+  }
   // Source.
   it->kind = S->kind;
   it->seed = seed;
@@ -293,7 +309,7 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     for (auto& it : items) any_smem |= want_smem_hist(it, o, false);
     det = !any_smem;
   }
-  const int warps = pick_warps(o, adjoint, items.size() == 1 ? items[0].kind : FR_SOURCE_POINT);
+  const int warps = pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind : FR_SOURCE_POINT);
   // Workspace.
   size_t at = kHeaderBytes;
   std::vector<ItemWs> ws(items.size());
@@ -321,11 +337,11 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
       else if (!o.accumulate) FR_CUDA(h, cudaMemsetAsync(it.E, 0, (size_t)it.ncol * it.nrow * 4, st), "memset");
     } else {
       if (det) {
-        FR_CUDA(h, cudaMemsetAsync(it.Pfix, 0, (size_t)it.ncu * it.ncv * 8, st), "memset");
+        FR_CUDA(h, cudaMemsetAsync(it.Pfix, 0, (size_t)it.nparam * 8, st), "memset");
         cudaError_t e = fr::launch_absmax(it.dLdE, (size_t)it.ncol * it.nrow, const_cast<float*>(it.gmax), st);
         if (e != cudaSuccess) return cuda_error(h, e, "absmax kernel");
       } else if (!o.accumulate) {
-        FR_CUDA(h, cudaMemsetAsync(it.dLdP, 0, (size_t)it.ncu * it.ncv * 4, st), "memset");
+        FR_CUDA(h, cudaMemsetAsync(it.dLdP, 0, (size_t)it.nparam * 4, st), "memset");
       }
     }
   }
@@ -336,7 +352,10 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   for (auto& it : items)
     if (it.nu != items[0].nu)
       return set_error(h, FR_ERR_UNSUPPORTED, "the items of a batch must have the same filter size");
-  const int kinds = items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2;
+  const int kinds = items[0].two_face ? 4 : (items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
+  if (batch)
+    for (auto& it : items)
+      if (it.two_face) return set_error(h, FR_ERR_UNSUPPORTED, "two-face lenses are traced one per call");
   const auto key = std::make_tuple((int)adjoint, (int)det, (int)batch, items[0].nu, kinds, threads, smem);
   auto found = h->occupancy.find(key);
   int occ;
@@ -480,6 +499,7 @@ fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_sour
   Item it;
   fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
   if (s != FR_OK) return s;
+  if (it.two_face) return set_error(h, FR_ERR_UNSUPPORTED, "derivative maps take a flat entry face");
   it.stats = stats_out;
   const cudaStream_t st = as_stream(stream);
   if (!o.accumulate)

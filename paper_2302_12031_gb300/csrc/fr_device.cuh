@@ -136,6 +136,13 @@ __host__ __device__ inline size_t lens_smem_bytes(int nsu, int nsv) {
   return (size_t)(nsu * nsv + nsu + nsv) * 4 * sizeof(float4) + 16;
 }
 
+// Bytes of all lens tables of an item (the exit net's, then the entry net's).
+__host__ __device__ inline size_t tables_bytes(const Item& it) {
+  size_t b = (lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15;
+  if (it.two_face) b += (lens_smem_bytes(it.nsu_in, it.nsv_in) + 15) & ~(size_t)15;
+  return b;
+}
+
 __device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv) {
   LensSmem s;
   s.patch = reinterpret_cast<float4*>(base);
@@ -150,33 +157,33 @@ __device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv) {
 //   C[e][f] = sum_a sum_b Bu[a][e] Bv[b][f] P^z_{k+a,l+b}.
 // For point sources the min and max control height come out of the same
 // loads (every control point lies in some patch's 4x4 window).
-__device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
-  const bool bounds = it.kind == FR_SOURCE_POINT;
+__device__ inline void build_net_tables(const float* ctrl, int ncv, int nsu, int nsv, bool bounds,
+                                        const LensSmem& s) {
   if (bounds && threadIdx.x == 0) {
     s.zkey[0] = 0x7fffffff;
     s.zkey[1] = (int)0x80000000;
   }
-  for (int q = threadIdx.x; q < it.nsu + it.nsv; q += blockDim.x) {
-    const bool isu = q < it.nsu;
-    const int k = isu ? q : q - it.nsu;
+  for (int q = threadIdx.x; q < nsu + nsv; q += blockDim.x) {
+    const bool isu = q < nsu;
+    const int k = isu ? q : q - nsu;
     float4 B[4];
-    span_basis(k, isu ? it.nsu : it.nsv, B);
+    span_basis(k, isu ? nsu : nsv, B);
     float4* dst = (isu ? s.bu : s.bv) + k * 4;
 #pragma unroll
     for (int a = 0; a < 4; ++a) dst[a] = B[a];
   }
   __syncthreads();
-  const int npatch = it.nsu * it.nsv;
+  const int npatch = nsu * nsv;
   float zmn = INFINITY, zmx = -INFINITY;
   for (int p = threadIdx.x; p < npatch; p += blockDim.x) {
-    const int k = p / it.nsv, l = p - k * it.nsv;
+    const int k = p / nsv, l = p - k * nsv;
     float T[4][4];   // T[a][f] = sum_b P[k+a][l+b] Bv_l[b][f]
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const float P = __ldg(it.ctrl + (k + a) * it.ncv + (l + b));
+        const float P = __ldg(ctrl + (k + a) * ncv + (l + b));
         zmn = fminf(zmn, P);
         zmx = fmaxf(zmx, P);
         const float4 q = s.bv[l * 4 + b];
@@ -212,6 +219,22 @@ __device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
     }
   }
   __syncthreads();
+}
+
+// The exit net's tables (bounds for point sources and two-face lenses).
+__device__ inline void build_lens_tables(const Item& it, const LensSmem& s) {
+  build_net_tables(it.ctrl, it.ncv, it.nsu, it.nsv, it.kind == FR_SOURCE_POINT || it.two_face, s);
+}
+
+// Both nets' tables of a two-face item (the entry net's in `e`).
+__device__ inline void build_two_face_tables(const Item& it, const LensSmem& s, const LensSmem& e) {
+  build_net_tables(it.ctrl, it.ncv, it.nsu, it.nsv, true, s);
+  build_net_tables(it.ctrl_in, it.ncv_in, it.nsu_in, it.nsv_in, true, e);
+}
+
+// The entry net's tables follow the exit net's.
+__device__ inline LensSmem carve_entry(unsigned char* base, const Item& it) {
+  return carve_lens(base + ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15), it.nsu_in, it.nsv_in);
 }
 
 __device__ __forceinline__ void locate(float u, int ns, int* k, float* s) {
@@ -599,37 +622,38 @@ __device__ __forceinline__ void mesh_vertex_weights(const Item& it, const LensSm
   }
 }
 
-// Point source (a1, a2, a4-a6): Philox direction uniform in the cone, flat
-// entry face, Snell + Schlick into the glass, safeguarded Newton on f(t)
-// bracketed by the convex hull of the control heights (Sec. 2.1.2).
-__device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, uint64_t id, float zmin, float zmax,
-                                            RayFwd& r) {
-  r.iters = 0;
+// Point source ray (a1): origin (sx, sy, pz) of the emitting source of the
+// grid and a direction uniform in the cone; omc = 1 - cos(phi), sphi = sin(phi).
+__device__ __forceinline__ void source_ray(const Item& it, uint64_t id, float* sx, float* sy, float* d0x, float* d0y,
+                                           float* d0z, float* omc, float* sphi) {
   const uint2 w = philox_ray_words(it.seed, id);
   const float xi1 = unit23(w.x), xi2 = unit23(w.y);
-  float sx = it.px, sy = it.py;
+  float x = it.px, y = it.py;
   if (it.gnx * it.gny > 1) {
     uint32_t src = (uint32_t)(id / it.per_src);
     src = min(src, (uint32_t)(it.gnx * it.gny - 1));
     const uint32_t gx = src % (uint32_t)it.gnx, gy = src / (uint32_t)it.gnx;
-    sx += fmaf((float)gx, it.gdx, it.gx0);
-    sy += fmaf((float)gy, it.gdy, it.gy0);
+    x += fmaf((float)gx, it.gdx, it.gx0);
+    y += fmaf((float)gy, it.gdy, it.gy0);
   }
+  *sx = x;
+  *sy = y;
   float sn, cn;
   sincospif(2.0f * xi1, &sn, &cn);
-  const float omc = it.omc_max * xi2;            // 1 - cos(phi)
-  const float sphi = sqrtf(omc * (2.0f - omc));
-  const float d0x = cn * sphi, d0y = sn * sphi, d0z = 1.0f - omc;
-  const float tau = (it.z_in - it.pz) * fast_rcp(d0z);
-  const float ox = fmaf(tau, d0x, sx), oy = fmaf(tau, d0y, sy), oz = it.z_in;
-  if (!(tau > 0.0f) || fabsf(ox) > it.rx || fabsf(oy) > it.ry) { r.status = FR_RAY_APERTURE_MISS; return; }
-  // Snell air -> glass at the flat face, normal (0,0,1).
-  const float eta1 = 1.0f / it.n_glass;
-  r.dx = eta1 * d0x;
-  r.dy = eta1 * d0y;
-  r.dz = sqrtf(fmaf(-eta1 * eta1, sphi * sphi, 1.0f));
-  const float om2 = omc * omc;
-  r.T1 = (1.0f - it.R0) * fmaf(-om2 * om2, omc, 1.0f);
+  const float o = it.omc_max * xi2;            // 1 - cos(phi)
+  const float sp = sqrtf(o * (2.0f - o));
+  *d0x = cn * sp;
+  *d0y = sn * sp;
+  *d0z = 1.0f - o;
+  *omc = o;
+  *sphi = sp;
+}
+
+// The ray inside the glass, from (ox, oy, oz) along (r.dx, r.dy, r.dz), meets
+// the exit freeform (a4): safeguarded Newton on f(t) bracketed by the convex
+// hull of the control heights (Sec. 2.1.2), or the triangle mesh; then a5-a6.
+__device__ __forceinline__ void exit_hit(const Item& it, const LensSmem& ls, float ox, float oy, float oz, float zmin,
+                                         float zmax, RayFwd& r) {
   // Bracket: the slab zmin <= z <= zmax, widened a little for FP32 rounding,
   // cut where the ray leaves the domain [0,1]^2 (the side of the lens).
   const float pad = 1e-6f * (1.0f + fmaxf(fabsf(zmin), fabsf(zmax)));
@@ -687,7 +711,9 @@ __device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, 
   bool converged = (f == 0.0f);
   for (int n = 0; n < it.newton_max && !converged; ++n) {
     float tn = t - __fdividef(f, fp);
-    if (!(fp < 0.0f) || !(tn > ta && tn < tb)) tn = 0.5f * (ta + tb);
+    // The bracket is closed: an exact root on its edge (Newton landing on the
+    // root leaves f within rounding of 0 on either side) is kept, not bisected.
+    if (!(fp < 0.0f) || !(tn >= ta && tn <= tb)) tn = 0.5f * (ta + tb);
     const float step = fabsf(tn - t);
     t = tn;
     f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
@@ -704,6 +730,152 @@ __device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, 
   r.y = fmaf(r.dy, t, oy);
   r.z = fmaf(r.dz, t, oz);
   exit_and_propagate<false>(it, r);
+}
+
+// Point source (a1, a2, a4-a6): Philox direction uniform in the cone, flat
+// entry face, Snell + Schlick into the glass, then the exit freeform.
+__device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, uint64_t id, float zmin, float zmax,
+                                            RayFwd& r) {
+  r.iters = 0;
+  float sx, sy, d0x, d0y, d0z, omc, sphi;
+  source_ray(it, id, &sx, &sy, &d0x, &d0y, &d0z, &omc, &sphi);
+  const float tau = (it.z_in - it.pz) * fast_rcp(d0z);
+  const float ox = fmaf(tau, d0x, sx), oy = fmaf(tau, d0y, sy), oz = it.z_in;
+  if (!(tau > 0.0f) || fabsf(ox) > it.rx || fabsf(oy) > it.ry) { r.status = FR_RAY_APERTURE_MISS; return; }
+  // Snell air -> glass at the flat face, normal (0,0,1).
+  const float eta1 = 1.0f / it.n_glass;
+  r.dx = eta1 * d0x;
+  r.dy = eta1 * d0y;
+  r.dz = sqrtf(fmaf(-eta1 * eta1, sphi * sphi, 1.0f));
+  const float om2 = omc * omc;
+  r.T1 = (1.0f - it.R0) * fmaf(-om2 * om2, omc, 1.0f);
+  exit_hit(it, ls, ox, oy, oz, zmin, zmax, r);
+}
+
+// ---------------------------------------------------------------------------
+// Freeform entry face (both faces optimised, Sec. 4): the ray meets a second
+// B-spline height field over the same aperture, refracts into the glass there,
+// and the glass ray meets the exit freeform as a point-source ray does.
+// ---------------------------------------------------------------------------
+struct RayIn {
+  int k, l;             // entry patch
+  float s, t;           // patch coordinates of the entry point
+  float ox, oy, oz;     // entry point
+  float d0x, d0y, d0z;  // direction in air
+  float Zs, Zt;         // entry slopes in patch coordinates
+  float nx, ny, nz;     // entry normal, into the glass
+  float invL;
+  float c, cs, a;       // d0.n, transmitted cosine, c/n_glass - cs
+  float tin, gpin;      // point source: ray parameter of the entry point, df_in/dt there
+};
+
+// f_in(t) = Z_in(o_uv + d_uv t) - o_z - d_z t on the entry net and df_in/dt.
+__device__ __forceinline__ void f_eval_in(const Item& it, const LensSmem& li, float ou, float ov, float du, float dv,
+                                          float oz, float dz, float t, RayIn& e, float* f, float* fp) {
+  locate(fmaf(du, t, ou), it.nsu_in, &e.k, &e.s);
+  locate(fmaf(dv, t, ov), it.nsv_in, &e.l, &e.t);
+  float Z;
+  patch_eval(li.patch + (size_t)(e.k * it.nsv_in + e.l) * 4, e.s, e.t, &Z, &e.Zs, &e.Zt);
+  *f = Z - fmaf(dz, t, oz);
+  *fp = fmaf(e.Zs, du * (float)it.nsu_in, fmaf(e.Zt, dv * (float)it.nsv_in, -dz));
+}
+
+// One ray through a two-face lens. Collimated rays (row, col) meet the entry
+// face at (X(u), Y(v), Z_in(u,v)); point-source rays at the smallest root of
+// f_in over the entry net's convex-hull slab, found by the same safeguarded
+// Newton as the exit (the ray must be over the domain at the bottom of the slab
+// and stay over it until the root: else it misses the aperture).
+__device__ __forceinline__ void trace_two_face(const Item& it, const LensSmem& ls, const LensSmem& li, uint64_t id,
+                                               uint32_t row, uint32_t col, RayFwd& r, RayIn& e) {
+  r.iters = 0;
+  if (it.kind == FR_SOURCE_COLLIMATED) {
+    float ja = 0.5f, jb = 0.5f;
+    if (it.jitter) {
+      const uint2 w = philox_ray_words(it.seed, id);
+      ja = unit23(w.x);
+      jb = unit23(w.y);
+    }
+    const float u = ((float)col + ja) / (float)it.cols, v = ((float)row + jb) / (float)it.rows;
+    e.d0x = 0.0f;
+    e.d0y = 0.0f;
+    e.d0z = 1.0f;
+    locate(u, it.nsu_in, &e.k, &e.s);
+    locate(v, it.nsv_in, &e.l, &e.t);
+    float Z;
+    patch_eval(li.patch + (size_t)(e.k * it.nsv_in + e.l) * 4, e.s, e.t, &Z, &e.Zs, &e.Zt);
+    e.ox = fmaf(2.0f, u, -1.0f) * it.rx;
+    e.oy = fmaf(2.0f, v, -1.0f) * it.ry;
+    e.oz = Z;
+  } else {
+    float sx, sy, omc, sphi;
+    source_ray(it, id, &sx, &sy, &e.d0x, &e.d0y, &e.d0z, &omc, &sphi);
+    float zmin, zmax;
+    zbounds(li, &zmin, &zmax);
+    const float pad = 1e-6f * (1.0f + fmaxf(fabsf(zmin), fabsf(zmax)));
+    const float inv_dz = fast_rcp(e.d0z);
+    float ta = fmaxf(0.0f, (zmin - pad - it.pz) * inv_dz);
+    const float t_hi = (zmax + pad - it.pz) * inv_dz;
+    const float ou = fmaf(0.5f / it.rx, sx, 0.5f), ov = fmaf(0.5f / it.ry, sy, 0.5f);
+    const float du = e.d0x * (0.5f / it.rx), dv = e.d0y * (0.5f / it.ry);
+    const float ua = fmaf(du, ta, ou), va = fmaf(dv, ta, ov);
+    if (!(ua >= 0.0f && ua <= 1.0f && va >= 0.0f && va <= 1.0f)) { r.status = FR_RAY_APERTURE_MISS; return; }
+    float t_dom = INFINITY;
+    if (du > 0.0f) t_dom = fminf(t_dom, (1.0f - ou) / du);
+    if (du < 0.0f) t_dom = fminf(t_dom, -ou / du);
+    if (dv > 0.0f) t_dom = fminf(t_dom, (1.0f - ov) / dv);
+    if (dv < 0.0f) t_dom = fminf(t_dom, -ov / dv);
+    float tb = fminf(t_hi, t_dom);
+    float f, fp;
+    if (tb < t_hi) {
+      f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, tb, e, &f, &fp);
+      if (f > 0.0f) { r.status = FR_RAY_APERTURE_MISS; return; }   // leaves through the side first
+    }
+    if (ta == 0.0f) {
+      f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, 0.0f, e, &f, &fp);
+      if (f < 0.0f) { r.status = FR_RAY_INVALID; return; }
+    }
+    float t = 0.5f * (ta + tb);
+    f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, t, e, &f, &fp);
+    if (f > 0.0f) ta = t; else tb = t;
+    bool converged = (f == 0.0f);
+    for (int n = 0; n < it.newton_max && !converged; ++n) {
+      float tn = t - __fdividef(f, fp);
+      if (!(fp < 0.0f) || !(tn >= ta && tn <= tb)) tn = 0.5f * (ta + tb);   // closed, as in exit_hit
+      const float step = fabsf(tn - t);
+      t = tn;
+      f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, t, e, &f, &fp);
+      if (f > 0.0f) ta = t; else tb = t;
+      if (step <= it.newton_tol || f == 0.0f) converged = true;
+    }
+    if (!converged) { r.status = FR_RAY_NEWTON_FAIL; return; }
+    e.tin = t;
+    e.gpin = fp;
+    e.ox = fmaf(e.d0x, t, sx);
+    e.oy = fmaf(e.d0y, t, sy);
+    e.oz = fmaf(e.d0z, t, it.pz);
+  }
+  // Snell air -> glass at the entry normal (-Z_x, -Z_y, 1)/|.|; Schlick with
+  // the incident cosine (in air).
+  const float Zx = e.Zs * it.ku_in, Zy = e.Zt * it.kv_in;
+  const float invL = rsqrtf(fmaf(Zx, Zx, fmaf(Zy, Zy, 1.0f)));
+  e.invL = invL;
+  e.nx = -Zx * invL;
+  e.ny = -Zy * invL;
+  e.nz = invL;
+  const float c = fmaf(e.d0x, e.nx, fmaf(e.d0y, e.ny, e.d0z * e.nz));
+  e.c = c;
+  const float eta1 = 1.0f / it.n_glass;
+  const float k = fmaf(-eta1 * eta1, fmaf(-c, c, 1.0f), 1.0f);   // > 0: into the denser medium
+  e.cs = k * rsqrtf(k);
+  e.a = fmaf(eta1, c, -e.cs);
+  r.dx = fmaf(eta1, e.d0x, -e.a * e.nx);
+  r.dy = fmaf(eta1, e.d0y, -e.a * e.ny);
+  r.dz = fmaf(eta1, e.d0z, -e.a * e.nz);
+  const float omc = 1.0f - c, om2 = omc * omc;
+  r.T1 = (1.0f - it.R0) * fmaf(-om2 * om2, omc, 1.0f);
+  float zmin, zmax;
+  zbounds(ls, &zmin, &zmax);
+  exit_hit(it, ls, e.ox, e.oy, e.oz, zmin, zmax, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -885,6 +1057,113 @@ __device__ __forceinline__ RayTan ray_tangent(const Item& it, const RayFwd& r, f
   o.dX = fmaf(dlam, r.tx, fmaf(r.lam, dtx, hx));
   o.dY = fmaf(dlam, r.ty, fmaf(r.lam, dty, hy));
   return o;
+}
+
+// Reverse mode of one ray through a two-face lens: the exit net's adjoints
+// (zeta, Zs_bar, Zt_bar at the exit hit, as ray_reverse) and the entry net's
+// (zeta_in, Zs_bar_in, Zt_bar_in at the entry point). The glass ray's origin o
+// and direction d now depend on the entry net: their adjoints gather from the
+// exit refraction, the exit hit h = o + d t* and the implicit function theorem
+// on f(t*; o, d, P) = 0 (df/do = (Z_x, Z_y, -1), df/dd = t* df/do), and go back
+// through Snell at the entry face (with Schlick's T1 of the incident cosine),
+// the entry normal and the entry point (for a point source, its own implicit
+// function theorem on f_in).
+template <int NU>
+__device__ __forceinline__ void ray_reverse_two(const Item& it, const LensSmem& ls, const LensSmem& li, const RayFwd& r,
+                                                const RayIn& e, const Foot<NU>& f, const float (&G)[NU][NU],
+                                                float* zeta, float* Zs_bar, float* Zt_bar, float* zeta_in,
+                                                float* Zs_bar_in, float* Zt_bar_in) {
+  float Fx[NU], Fy[NU], gxa[NU], gya[NU];
+  filter_grad<NU>(it, f, Fx, Fy, gxa, gya);
+  float wbar = 0.0f, Xs = 0.0f, Ys = 0.0f;
+#pragma unroll
+  for (int a = 0; a < NU; ++a) {
+    float A = 0.0f, B = 0.0f;
+#pragma unroll
+    for (int b = 0; b < NU; ++b) {
+      A = fmaf(G[b][a], Fy[b], A);
+      B = fmaf(G[b][a], gya[b], B);
+    }
+    wbar = fmaf(A, Fx[a], wbar);
+    Xs = fmaf(A, gxa[a], Xs);
+    Ys = fmaf(B, Fx[a], Ys);
+  }
+  const float K = r.w * it.inv_area;
+  wbar *= it.inv_area;
+  const float Xbar = K * Xs, Ybar = K * Ys;
+  // Propagation X = h + lam t, lam = (z_s - h_z)/t_z.
+  const float txb = r.lam * Xbar, tyb = r.lam * Ybar;
+  const float lamb = fmaf(Xbar, r.tx, Ybar * r.ty);
+  const float inv_tz = fast_rcp(r.tz);
+  const float tzb = -lamb * r.lam * inv_tz;
+  const float hzb0 = -lamb * inv_tz;
+  // Weight w = omega0 T1 T2.
+  const float om = 1.0f - r.cs, om2 = om * om;
+  float csb = wbar * it.omega0 * r.T1 * (1.0f - it.R0) * 5.0f * om2 * om2;
+  const float T1b = wbar * it.omega0 * r.T2;
+  // Exit refraction t = eta d - a n, a = eta c - cs, c = d.n.
+  const float eta = it.n_glass;
+  const float abar = -(txb * r.nx + tyb * r.ny + tzb * r.nz);
+  float nbx = -r.a * txb, nby = -r.a * tyb, nbz = -r.a * tzb;
+  float dbx = eta * txb, dby = eta * tyb, dbz = eta * tzb;
+  float cbar = eta * abar;
+  csb -= abar;
+  cbar = fmaf(csb * eta * eta * r.c, fast_rcp(r.cs), cbar);
+  nbx = fmaf(cbar, r.dx, nbx);
+  nby = fmaf(cbar, r.dy, nby);
+  nbz = fmaf(cbar, r.dz, nbz);
+  dbx = fmaf(cbar, r.nx, dbx);
+  dby = fmaf(cbar, r.ny, dby);
+  dbz = fmaf(cbar, r.nz, dbz);
+  // Exit normal n = m/|m|, m = (-Z_x, -Z_y, 1).
+  const float ndot = nbx * r.nx + nby * r.ny + nbz * r.nz;
+  const float zsb = -((nbx - ndot * r.nx) * r.invL) * it.ku;
+  const float ztb = -((nby - ndot * r.ny) * r.invL) * it.kv;
+  *Zs_bar = zsb;
+  *Zt_bar = ztb;
+  // Exit hit h = o + d t*; the slopes are taken at h.
+  float Zss, Zst, Ztt;
+  patch_eval2(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Zss, &Zst, &Ztt);
+  const float hbx = fmaf(it.ku, fmaf(zsb, Zss, ztb * Zst), Xbar);
+  const float hby = fmaf(it.kv, fmaf(zsb, Zst, ztb * Ztt), Ybar);
+  const float hbz = hzb0;
+  const float tbar = fmaf(hbx, r.dx, fmaf(hby, r.dy, hbz * r.dz));
+  const float z = -tbar / r.gp;
+  *zeta = z;
+  const float fx = r.Zs * it.ku, fy = r.Zt * it.kv;
+  float obx = fmaf(z, fx, hbx), oby = fmaf(z, fy, hby), obz = hbz - z;
+  const float zt = z * r.tstar;
+  dbx = fmaf(hbx, r.tstar, fmaf(zt, fx, dbx));
+  dby = fmaf(hby, r.tstar, fmaf(zt, fy, dby));
+  dbz = fmaf(hbz, r.tstar, fmaf(-zt, 1.0f, dbz));
+  // Entry refraction d = eta1 d0 - a1 m, a1 = eta1 c1 - cs1, c1 = d0.m; T1(c1).
+  const float eta1 = 1.0f / it.n_glass;
+  const float a1b = -(dbx * e.nx + dby * e.ny + dbz * e.nz);
+  float mbx = -e.a * dbx, mby = -e.a * dby, mbz = -e.a * dbz;
+  float c1b = eta1 * a1b;
+  c1b = fmaf(-a1b * eta1 * eta1 * e.c, fast_rcp(e.cs), c1b);
+  const float om1 = 1.0f - e.c, om1_2 = om1 * om1;
+  c1b = fmaf(T1b * (1.0f - it.R0) * 5.0f, om1_2 * om1_2, c1b);
+  mbx = fmaf(c1b, e.d0x, mbx);
+  mby = fmaf(c1b, e.d0y, mby);
+  mbz = fmaf(c1b, e.d0z, mbz);
+  // Entry normal.
+  const float nd = mbx * e.nx + mby * e.ny + mbz * e.nz;
+  const float zsbi = -((mbx - nd * e.nx) * e.invL) * it.ku_in;
+  const float ztbi = -((mby - nd * e.ny) * e.invL) * it.kv_in;
+  *Zs_bar_in = zsbi;
+  *Zt_bar_in = ztbi;
+  if (it.kind == FR_SOURCE_COLLIMATED) {
+    *zeta_in = obz;   // the entry point's height at a fixed (u, v)
+    return;
+  }
+  // Point source: the entry point moves along the source ray with t_in.
+  float Sss, Sst, Stt;
+  patch_eval2(li.patch + (size_t)(e.k * it.nsv_in + e.l) * 4, e.s, e.t, &Sss, &Sst, &Stt);
+  obx = fmaf(it.ku_in, fmaf(zsbi, Sss, ztbi * Sst), obx);
+  oby = fmaf(it.kv_in, fmaf(zsbi, Sst, ztbi * Stt), oby);
+  const float tinb = fmaf(obx, e.d0x, fmaf(oby, e.d0y, obz * e.d0z));
+  *zeta_in = -tinb / e.gpin;
 }
 
 // Ray counts by cause (FR_RAY_*): a per-thread count of deposited rays and

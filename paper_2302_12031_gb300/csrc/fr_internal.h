@@ -23,6 +23,13 @@ struct Item {
   float rx, ry, z_in, n_glass;
   float ku, kv;                 // d(span coordinate)/dx = nsu/(2 rx), likewise kv
   float R0;                     // ((n-1)/(n+1))^2
+  // Optional freeform entry face (both faces optimised): a second net over the
+  // same aperture; two_face = 0: the flat face z = z_in.
+  int two_face;
+  const float* ctrl_in;
+  int ncu_in, ncv_in, nsu_in, nsv_in;
+  float ku_in, kv_in;
+  int nparam;                   // control heights: ncu ncv (+ ncu_in ncv_in); dL/dP has this many
   // Source (Sec. 2.2.1).
   int kind, jitter, cols, rows;
   float px, py, pz;             // source position (grid centre)

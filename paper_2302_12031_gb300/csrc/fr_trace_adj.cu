@@ -201,10 +201,87 @@ __device__ __forceinline__ void adjoint_ray_moments(const Item& it, const LensSm
   m.Q3 = fmaf(Ztb, s3, m.Q3);
 }
 
-// KINDS: bit 0 = the kernel handles collimated items, bit 1 = point-source items.
+// dL/dP_{k+a,l+b} += zeta N_a N_b + Zs_bar N'_a N_b + Zt_bar N_a N'_b at (s, t)
+// of patch (k, l) of a net whose tables are `tab`, summed in `acc`.
+template <bool DET>
+__device__ __forceinline__ void grad_add(const LensSmem& tab, int k, int l, float s, float t, float zeta, float Zsb,
+                                         float Ztb, int ncv, GradAcc<DET>& acc, float* sg_f,
+                                         unsigned long long* sg_q, float fixP) {
+  float Nu[4], dNu[4], Nv[4], dNv[4];
+  basis_eval(tab.bu + k * 4, s, Nu, dNu);
+  basis_eval(tab.bv + l * 4, t, Nv, dNv);
+  if (k != acc.k || l != acc.l) {
+    grad_flush<DET>(acc, ncv, sg_f, sg_q);
+    acc.k = k;
+    acc.l = l;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc.g[a][b] = 0;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float A = fmaf(zeta, Nu[a], Zsb * dNu[a]);
+    const float B = Ztb * Nu[a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float c = fmaf(A, Nv[b], B * dNv[b]);
+      if constexpr (DET) acc.g[a][b] += __float2ll_rn(c * fixP);
+      else acc.g[a][b] += c;
+    }
+  }
+}
+
+// Two-face lens: both nets' gradients; the entry net's follow the exit net's
+// in dL/dP.
+template <int NU, bool DET>
+__device__ void run_adjoint_lane_two(const Item& it, const LensSmem& ls, const LensSmem& li, uint64_t a, uint64_t b,
+                                     const GradOut& go, RayCount& cnt, unsigned int* s_cnt) {
+  GradAcc<DET> acc, acc_in;
+  acc.k = acc_in.k = -1;
+  GCache<NU> gc;
+  gc.ie = gc.je = -1;
+  const int nout = it.ncu * it.ncv;
+  float* sgi_f = go.sg_f + nout;
+  unsigned long long* sgi_q = go.sg_q + nout;
+  for (uint64_t id = a; id < b; ++id) {
+    RayFwd r;
+    RayIn e;
+    const uint32_t row = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id / (uint64_t)it.cols) : 0u;
+    const uint32_t col = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id % (uint64_t)it.cols) : 0u;
+    trace_two_face(it, ls, li, id, row, col, r, e);
+    cnt.add(r.status, s_cnt);
+    if (r.status != FR_RAY_ON_SCREEN) continue;
+    Foot<NU> f;
+    if (!footprint<NU>(it, r.X, r.Y, f)) continue;
+    if (f.ie != gc.ie || f.je != gc.je) {
+#pragma unroll
+      for (int bb = 0; bb < NU; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < NU; ++aa) gc.G[bb][aa] = __ldg(it.dLdE + (size_t)(f.je + bb) * it.ncol + f.ie + aa);
+      gc.ie = f.ie;
+      gc.je = f.je;
+    }
+    float z, zs, zt, zi, zsi, zti;
+    ray_reverse_two<NU>(it, ls, li, r, e, f, gc.G, &z, &zs, &zt, &zi, &zsi, &zti);
+    grad_add<DET>(ls, r.k, r.l, r.s, r.t, z, zs, zt, it.ncv, acc, go.sg_f, go.sg_q, go.fixP);
+    grad_add<DET>(li, e.k, e.l, e.s, e.t, zi, zsi, zti, it.ncv_in, acc_in, sgi_f, sgi_q, go.fixP);
+  }
+  grad_flush<DET>(acc, it.ncv, go.sg_f, go.sg_q);
+  grad_flush<DET>(acc_in, it.ncv_in, sgi_f, sgi_q);
+}
+
+// KINDS: bit 0 = the kernel handles collimated items, bit 1 = point-source
+// items, bit 2 = two-face lenses (entry tables in li).
 template <int NU, bool DET, int KINDS>
-__device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, uint64_t a, uint64_t b, float zmin, float zmax,
-                                 const GradOut& go, RayCount& cnt, unsigned int* s_cnt) {
+__device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, const LensSmem& li, uint64_t a, uint64_t b,
+                                 float zmin, float zmax, const GradOut& go, RayCount& cnt, unsigned int* s_cnt) {
+  if constexpr ((KINDS & 4) != 0) {
+    if (it.two_face) {
+      run_adjoint_lane_two<NU, DET>(it, ls, li, a, b, go, cnt, s_cnt);
+      return;
+    }
+  }
   GradAcc<DET> acc;
   acc.k = -1;
   GCache<NU> gc;
@@ -292,18 +369,20 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(const __grid_constant__ Laun
   const Item& it = L.items[ii];
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
-  unsigned char* grad_raw = smem + align16(lens_smem_bytes(it.nsu, it.nsv));
+  const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;
+  unsigned char* grad_raw = smem + tables_bytes(it);
   GradOut go;
   go.sg_f = reinterpret_cast<float*>(grad_raw);
   go.sg_q = reinterpret_cast<unsigned long long*>(grad_raw);
-  const int nctrl = it.ncu * it.ncv;
+  const int nctrl = it.nparam;
   for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
     if constexpr (DET) go.sg_q[q] = 0ull;
     else go.sg_f[q] = 0.0f;
   }
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
-  build_lens_tables(it, ls);   // ends with __syncthreads
+  if ((KINDS & 4) && it.two_face) build_two_face_tables(it, ls, li);   // ends with __syncthreads
+  else build_lens_tables(it, ls);
   go.fixP = 0.0f;
   if constexpr (DET) {
     // Fixed-point scale 2^40 / (max|dL/dE| * flux / pixel area), a power of two.
@@ -319,7 +398,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(const __grid_constant__ Laun
   RayCount cnt;
   cnt.on_screen = 0u;
   unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
-  run_adjoint_lane<NU, DET, KINDS>(it, ls, a, b, zmin, zmax, go, cnt, cnt_dst);
+  run_adjoint_lane<NU, DET, KINDS>(it, ls, li, a, b, zmin, zmax, go, cnt, cnt_dst);
   cnt.reduce_into(cnt_dst);
   __syncthreads();
   for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
@@ -338,7 +417,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(const __grid_constant__ Laun
 // adjoint kernel used (recomputed from the same device value).
 __global__ void k_grad_fix_to_float(const __grid_constant__ Item it, int accumulate) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= it.ncu * it.ncv) return;
+  if (q >= it.nparam) return;
   const float unit = *it.gmax * it.fixP_unit;
   int e = 0;
   if (unit > 0.0f) frexpf(unit, &e);
@@ -350,7 +429,7 @@ __global__ void k_grad_fix_to_float(const __grid_constant__ Item it, int accumul
 }  // namespace
 
 size_t adj_smem_bytes(const Item& it, bool det) {
-  return ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15) + (size_t)it.ncu * it.ncv * (det ? 8 : 4);
+  return tables_bytes(it) + (size_t)it.nparam * (det ? 8 : 4);
 }
 
 template <int CAP>
@@ -366,6 +445,7 @@ AdjKernel<CAP> pick_adjoint(bool det, int nu, int kinds);
 template <>
 AdjKernel<1> pick_adjoint<1>(bool det, int nu, int kinds) {
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
+  if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
   return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
 }
 template <>
@@ -376,7 +456,7 @@ AdjKernel<kMaxItems> pick_adjoint<kMaxItems>(bool det, int nu, int) {
 template <int CAP>
 cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
   const int threads = 32 * L.warps;
-  const int kinds = L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2;
+  const int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
   pick_adjoint<CAP>(det, L.items[0].nu, kinds)<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
@@ -384,7 +464,7 @@ template cudaError_t launch_adjoint<1>(const Launch<1>&, int, size_t, bool, cuda
 template cudaError_t launch_adjoint<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t);
 
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st) {
-  const int n = it.ncu * it.ncv;
+  const int n = it.nparam;
   k_grad_fix_to_float<<<(n + 255) / 256, 256, 0, st>>>(it, accumulate);
   return cudaGetLastError();
 }
@@ -408,7 +488,7 @@ cudaError_t configure_adjoint(int optin) {
   cudaError_t e;
   for (int det = 0; det < 2; ++det)
     for (int nu = 1; nu <= 5; nu += 2) {
-      for (int kinds = 1; kinds <= 2; ++kinds)
+      for (int kinds = 1; kinds <= 4; kinds *= 2)
         if ((e = allow_max_smem(pick_adjoint<1>(det != 0, nu, kinds), optin))) return e;
       if ((e = allow_max_smem(pick_adjoint<kMaxItems>(det != 0, nu, 3), optin))) return e;
     }

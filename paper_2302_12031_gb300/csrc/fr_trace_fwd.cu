@@ -108,11 +108,27 @@ __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const T
 }
 
 // KINDS: bit 0 = the kernel handles collimated items, bit 1 = point-source items.
+// KINDS bit 2: the kernel also handles two-face lenses (entry tables in li).
 template <int NU, bool DET, int KINDS>
-__device__ void run_lane(const Item& it, const LensSmem& ls, const Target& tg, uint64_t a, uint64_t b, float zmin,
-                         float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb) {
+__device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li, const Target& tg, uint64_t a,
+                         uint64_t b, float zmin, float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb) {
   FootAcc<NU, DET> acc;
   acc.ie = -1;
+  if constexpr ((KINDS & 4) != 0) {
+    if (it.two_face) {
+      for (uint64_t id = a; id < b; ++id) {
+        RayFwd r;
+        RayIn e;
+        const uint32_t row = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id / (uint64_t)it.cols) : 0u;
+        const uint32_t col = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id % (uint64_t)it.cols) : 0u;
+        trace_two_face(it, ls, li, id, row, col, r, e);
+        cnt.add(r.status, s_cnt);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+      }
+      acc_flush<NU, DET>(acc, tg, bb);
+      return;
+    }
+  }
   if (a < b) {
     if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
       const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
@@ -159,7 +175,8 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
   const Item& it = L.items[ii];
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
-  unsigned char* hist_raw = smem + align16(lens_smem_bytes(it.nsu, it.nsv));
+  const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;
+  unsigned char* hist_raw = smem + tables_bytes(it);
   const int ncell = it.ncol * it.nrow;
   uint64_t a, b;
   lane_range(it, L.warps, &a, &b);
@@ -191,14 +208,15 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < 4) s_bb[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
-  build_lens_tables(it, ls);   // ends with __syncthreads
+  if ((KINDS & 4) && it.two_face) build_two_face_tables(it, ls, li);   // ends with __syncthreads
+  else build_lens_tables(it, ls);
   float zmin = 0.0f, zmax = 0.0f;
   if (it.kind == FR_SOURCE_POINT) zbounds(ls, &zmin, &zmax);
   RayCount cnt;
   cnt.on_screen = 0u;
   unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
   Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
-  run_lane<NU, DET, KINDS>(it, ls, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
+  run_lane<NU, DET, KINDS>(it, ls, li, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
   cnt.reduce_into(cnt_dst);
   if (tg.smem) {
     // Touched window: warp reductions, then one shared atomic per warp.
@@ -235,7 +253,9 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
 __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
-  build_lens_tables(it, ls);
+  const LensSmem li = it.two_face ? carve_entry(smem, it) : ls;
+  if (it.two_face) build_two_face_tables(it, ls, li);
+  else build_lens_tables(it, ls);
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t id = it.ray_begin + i;
   if (id >= it.ray_end) return;
@@ -245,7 +265,12 @@ __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, 
   r.u = r.v = r.s = r.t = r.x = r.y = r.z = r.dx = r.dy = r.dz = 0.0f;
   r.tx = r.ty = r.tz = r.w = r.X = r.Y = r.tstar = 0.0f;
   r.iters = 0;
-  if (it.kind == FR_SOURCE_COLLIMATED) {
+  if (it.two_face) {
+    RayIn e;
+    const uint32_t row = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id / (uint64_t)it.cols) : 0u;
+    const uint32_t col = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id % (uint64_t)it.cols) : 0u;
+    trace_two_face(it, ls, li, id, row, col, r, e);
+  } else if (it.kind == FR_SOURCE_COLLIMATED) {
     const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
     trace_collimated(it, ls, row, col, id, 1.0f / (float)it.cols, 1.0f / (float)it.rows, r);
   } else {
@@ -279,7 +304,7 @@ __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, 
 }  // namespace
 
 size_t fwd_smem_bytes(const Item& it, bool det) {
-  size_t b = (lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15;
+  size_t b = tables_bytes(it);
   if (it.smem_hist) b += (size_t)it.ncol * it.nrow * (det ? 8 : 4);
   return b;
 }
@@ -298,6 +323,7 @@ FwdKernel<CAP> pick_forward(bool det, int nu, int kinds);
 template <>
 FwdKernel<1> pick_forward<1>(bool det, int nu, int kinds) {
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
+  if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
   return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
 }
 template <>
@@ -308,7 +334,7 @@ FwdKernel<kMaxItems> pick_forward<kMaxItems>(bool det, int nu, int) {
 template <int CAP>
 cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
   const int threads = 32 * L.warps;
-  const int kinds = L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2;
+  const int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
   pick_forward<CAP>(det, L.items[0].nu, kinds)<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
@@ -320,7 +346,7 @@ cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int threads = 128;
   const unsigned int blocks = (unsigned int)((n + threads - 1) / threads);
-  k_debug<<<blocks, threads, lens_smem_bytes(it.nsu, it.nsv), st>>>(it, out);
+  k_debug<<<blocks, threads, tables_bytes(it), st>>>(it, out);
   return cudaGetLastError();
 }
 
@@ -346,7 +372,7 @@ cudaError_t configure_forward(int optin) {
   if ((e = allow_max_smem(k_debug, optin))) return e;
   for (int det = 0; det < 2; ++det)
     for (int nu = 1; nu <= 5; nu += 2) {
-      for (int kinds = 1; kinds <= 2; ++kinds)
+      for (int kinds = 1; kinds <= 4; kinds *= 2)
         if ((e = allow_max_smem(pick_forward<1>(det != 0, nu, kinds), optin))) return e;
       if ((e = allow_max_smem(pick_forward<kMaxItems>(det != 0, nu, 3), optin))) return e;
     }
