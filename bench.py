@@ -378,6 +378,17 @@ def extra_workloads(args, flush, world):
                                       "status_agree": float((m["status"] == newton["status"]).mean())}
         del st
     out["point_16M_triangle_mesh"] = mesh_out
+    # both lens faces as freeforms (the paper's proposed extension): the step
+    # optimises both nets (16x16 entry net for the collimated beam, 24x24 for
+    # the point source)
+    for name, wl2 in (("two_face_collimated_2048x2048", W.with_entry_face(W.config(2), 16, 0.01, 7)),
+                      ("two_face_point_16M", W.with_entry_face(W.config(3), 24, 0.01, 8))):
+        st = step.OptimStep(wl2, lr=1e-3, graph=True)
+        ms = time_steps(st.step, k, 2, flush)
+        rays_per_s, t = D.replica_throughput(st.n_rays, statistics.mean(ms) * 1e-3)
+        out[name] = {"rays_per_step": st.n_rays, "ms_per_step": 1e3 * t, "rays_per_s": rays_per_s,
+                     "parameters": st.n_params}
+        del st
     # the paper's objective: normalised Frobenius loss, tanh-reparametrised heights
     # over a spherical offset (Table magndata, magnification 3)
     wl = W.config(2)

@@ -315,7 +315,7 @@ class Problem:
     a float32 CUDA tensor of shape (n1+1, n2+1), by default the workload's.
     """
 
-    def __init__(self, wl, ctrl_z=None, device="cuda"):
+    def __init__(self, wl, ctrl_z=None, device="cuda", entry_z=None):
         lens, src, tgt = wl["lens"], wl["source"], wl["target"]
         if ctrl_z is None:
             ctrl_z = torch.as_tensor(lens["P"], dtype=torch.float32, device=device)
@@ -327,7 +327,10 @@ class Problem:
         self.entry_z = None
         self.entry_shape = None
         if lens.get("P_in") is not None:
-            self.entry_z = torch.as_tensor(lens["P_in"], dtype=torch.float32, device=device).contiguous()
+            if entry_z is None:
+                entry_z = torch.as_tensor(lens["P_in"], dtype=torch.float32, device=device)
+            self.entry_z = entry_z.contiguous()
+            assert self.entry_z.dtype == torch.float32 and self.entry_z.is_cuda
             self.entry_shape = (lens["n1_in"] + 1, lens["n2_in"] + 1)
             self.lens.entry_ctrl_z = self.entry_z.data_ptr()
             self.lens.entry_n1, self.lens.entry_n2 = lens["n1_in"], lens["n2_in"]

@@ -34,7 +34,11 @@ class OptimStep:
         self.lr, self.betas, self.eps = lr, betas, eps
         self.options = options
         self.adj_options = adj_options if adj_options is not None else options
-        sizes = [(w["lens"]["n1"] + 1) * (w["lens"]["n2"] + 1) for w in workloads]
+        # per lens: the exit heights, then (two-face lenses) the entry heights
+        n_out = [(w["lens"]["n1"] + 1) * (w["lens"]["n2"] + 1) for w in workloads]
+        n_in = [(w["lens"]["n1_in"] + 1) * (w["lens"]["n2_in"] + 1) if w["lens"].get("P_in") is not None else 0
+                for w in workloads]
+        sizes = [a + b for a, b in zip(n_out, n_in)]
         n = sum(sizes)
         self.n_params = n
         self.P = torch.empty(n, dtype=torch.float32, device=device)
@@ -44,11 +48,15 @@ class OptimStep:
         self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
         self.problems, self.E, self.dLdE, self.E_ref, self.loss = [], [], [], [], []
         at = 0
-        for w, sz in zip(workloads, sizes):
+        for w, sz, no in zip(workloads, sizes, n_out):
             shape = (w["lens"]["n1"] + 1, w["lens"]["n2"] + 1)
-            view = self.P[at:at + sz].view(shape)
+            view = self.P[at:at + no].view(shape)
             view.copy_(torch.as_tensor(w["lens"]["P"], dtype=torch.float32))
-            pb = api.Problem(w, ctrl_z=view, device=device)
+            entry = None
+            if sz > no:
+                entry = self.P[at + no:at + sz].view(w["lens"]["n1_in"] + 1, w["lens"]["n2_in"] + 1)
+                entry.copy_(torch.as_tensor(w["lens"]["P_in"], dtype=torch.float32))
+            pb = api.Problem(w, ctrl_z=view, device=device, entry_z=entry)
             self.problems.append(pb)
             self.E.append(torch.zeros(pb.ext_shape, dtype=torch.float32, device=device))
             self.dLdE.append(torch.zeros(pb.ext_shape, dtype=torch.float32, device=device))
@@ -58,7 +66,8 @@ class OptimStep:
         self.grads = []
         at = 0
         for pb, sz in zip(self.problems, sizes):
-            self.grads.append(self.g[at:at + sz].view(pb.ctrl_shape))
+            g = self.g[at:at + sz]
+            self.grads.append(g.view(pb.ctrl_shape) if pb.entry_shape is None else g)
             at += sz
         self.theta = self.offset = None
         if reparam is not None:

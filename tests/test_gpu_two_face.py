@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from oracle import oracle as O
-from paper_2302_12031_gb300 import api
+from paper_2302_12031_gb300 import api, step
 from paper_2302_12031_gb300 import workloads as W
 from tests.gpu_helpers import (TOL_E, TOL_GRAD, ambiguous_rays, compare_records, forward_both, random_dLdE,
                                rel_l2)
@@ -101,3 +101,28 @@ def test_two_face_unsupported_combinations_are_refused():
     E = torch.zeros(pb.ext_shape, device="cuda")
     with pytest.raises(api.FreerayError):
         api.fr_trace_batch_forward(api.default_handle(), [pb.batch_item(E=E), pb.batch_item(E=E)])
+
+
+def test_two_face_optimisation_step():
+    wl = _wl("collimated")
+    wl["E_ref"] = W.gaussian_mixture_target(32, 32, 1.0, 1.0, 2, 0.9216)
+    sg = step.OptimStep(wl, lr=1e-3, graph=True, options=api.make_options(deterministic=True))
+    se = step.OptimStep(wl, lr=1e-3, graph=False, options=api.make_options(deterministic=True))
+    n_out, n_in = wl["lens"]["P"].size, wl["lens"]["P_in"].size
+    assert sg.n_params == n_out + n_in
+    P0 = sg.P.double().cpu().numpy().copy()
+    sg.step()
+    se.step()
+    torch.cuda.synchronize()
+    # the first step's gradient over both nets against the oracle's
+    E_or, _ = O.trace_forward(wl)
+    _, d_or = O.loss_l2(wl, E_or)
+    g_or = _cat(O.trace_gradient(wl, d_or))
+    assert rel_l2(sg.g.cpu().numpy(), g_or) < TOL_GRAD
+    for _ in range(3):
+        sg.step()
+        se.step()
+    torch.cuda.synchronize()
+    assert torch.equal(sg.P, se.P)                       # graph replay = eager, bit for bit
+    moved = np.abs(sg.P.double().cpu().numpy() - P0)
+    assert moved[:n_out].max() > 0 and moved[n_out:].max() > 0   # both faces are optimised
