@@ -295,6 +295,24 @@ fr_status fr_trace_batch_forward(fr_handle* h, const fr_batch_item* items, int32
 fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32_t n_items,
                                  const fr_options* options, void* stream);
 
+/* Programmatic dependent launch for this handle's later calls: when enabled,
+ * the loss kernels, the adjoint trace kernel (float mode) and the Adam kernels
+ * are launched so that they may begin while the previous kernel on the stream
+ * is still running (their blocks start, then wait on the device for that
+ * kernel to complete before reading anything). This hides launch latency
+ * between the kernels of an optimisation step, most of all inside a CUDA
+ * graph. The waits are in the kernels: a call that follows a kernel of another
+ * library behaves the same.
+ *   mode 0: off (default); 1: on; 2: on, and the adjoint also builds its lens
+ *   tables (reads ctrl_z) before it waits: only when the kernel right before
+ *   the adjoint does not write the control heights (true for forward -> loss
+ *   -> adjoint -> Adam steps). FR_ERR_INVALID_ARG for other modes. */
+fr_status fr_set_programmatic_launch(fr_handle* h, int32_t mode);
+
+/* Zeroes `bytes` bytes of device memory at `ptr` on `stream` (a memset node
+ * when captured): for clearing outputs that later calls accumulate into. */
+fr_status fr_zero(fr_handle* h, void* ptr, uint64_t bytes, void* stream);
+
 /* Wait for `stream` on the host by polling, at most timeout_ms milliseconds.
  * Returns FR_ERR_TIMEOUT if the work has not finished by then. */
 fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms);

@@ -115,6 +115,8 @@ _SIGNATURES = {
     "fr_trace_batch_adjoint": (C.c_int, [C.c_void_p, C.POINTER(BatchItem), C.c_int32, C.POINTER(Options),
                                          C.c_void_p]),
     "fr_stream_wait": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "fr_set_programmatic_launch": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fr_zero": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "fr_trace_forward_static": (C.c_int, [C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
                                           C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -272,6 +274,16 @@ def fr_trace_batch_forward(h, items, options=None, stream=None):
 def fr_trace_batch_adjoint(h, items, options=None, stream=None):
     arr = (BatchItem * len(items))(*items)
     h.check(lib().fr_trace_batch_adjoint(h.ptr, arr, len(items), _opts(options), _stream(stream)))
+
+
+def fr_set_programmatic_launch(h, mode):
+    """0 off, 1 on, 2 on with the adjoint reading the lens before its wait."""
+    h.check(lib().fr_set_programmatic_launch(h.ptr, int(mode)))
+
+
+def fr_zero(h, t, stream=None):
+    """Zero a device tensor with a memset on the stream."""
+    h.check(lib().fr_zero(h.ptr, _ptr(t), t.numel() * t.element_size(), _stream(stream)))
 
 
 def fr_stream_wait(h, timeout_ms, stream=None):

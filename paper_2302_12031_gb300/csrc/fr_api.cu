@@ -25,6 +25,8 @@ struct fr_handle {
   std::string err;
   // CTAs per SM of a trace kernel, by (adjoint, det, batch, nu, kinds, threads, smem).
   std::map<std::tuple<int, int, int, int, int, int, size_t>, int> occupancy;
+  bool pdl = false;             // programmatic dependent launch for loss, adjoint and Adam
+  bool pdl_early = false;       // ... with the adjoint reading the lens before its wait
 };
 
 namespace {
@@ -384,6 +386,7 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     std::memset(&L, 0, sizeof L);
     L.n_items = (int)items.size();
     L.warps = warps;
+    L.early_lens = adjoint && h->pdl && h->pdl_early && !det ? 1 : 0;
     for (size_t i = 0; i < items.size(); ++i) {
       L.items[i] = items[i];
       grid = std::max(grid, items[i].cta_end);
@@ -395,7 +398,9 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     const unsigned int rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (o.event_begin)
       FR_CUDA(h, cudaEventRecordWithFlags((cudaEvent_t)o.event_begin, st, rec_flags), "cudaEventRecord");
-    cudaError_t e = adjoint ? fr::launch_adjoint<CAP>(L, grid, smem, det, st)
+    // Programmatic overlap only where the adjoint directly follows a kernel
+    // (in deterministic mode it follows the max-|dL/dE| kernel: no overlap).
+    cudaError_t e = adjoint ? fr::launch_adjoint<CAP>(L, grid, smem, det, st, h->pdl && !det)
                             : fr::launch_forward<CAP>(L, grid, smem, det, st);
     if (e != cudaSuccess) return cuda_error(h, e, adjoint ? "adjoint kernel" : "forward kernel");
     if (o.event_end)
@@ -549,7 +554,7 @@ fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t n
   if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
   if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || nu_x < 1 || nu_y < 1 || nu_x % 2 == 0 || nu_y % 2 == 0)
     return set_error(h, FR_ERR_INVALID_ARG, "bad grid sizes");
-  cudaError_t e = fr::launch_loss_l2(E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, as_stream(stream));
+  cudaError_t e = fr::launch_loss_l2(E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, as_stream(stream), h->pdl);
   if (e != cudaSuccess) return cuda_error(h, e, "loss kernel");
   return FR_OK;
 }
@@ -562,7 +567,7 @@ fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* 
   if (n < 0) return set_error(h, FR_ERR_INVALID_ARG, "n < 0");
   if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) || !finite(lr))
     return set_error(h, FR_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
-  cudaError_t e = fr::launch_adam(P, m, v, g, n, lr, beta1, beta2, eps, step, as_stream(stream));
+  cudaError_t e = fr::launch_adam(P, m, v, g, n, lr, beta1, beta2, eps, step, as_stream(stream), h->pdl);
   if (e != cudaSuccess) return cuda_error(h, e, "adam kernel");
   return FR_OK;
 }
@@ -574,7 +579,8 @@ fr_status fr_loss_frobenius(fr_handle* h, const float* E, const float* E_ref, in
   if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
   if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || nu_x < 1 || nu_y < 1 || nu_x % 2 == 0 || nu_y % 2 == 0)
     return set_error(h, FR_ERR_INVALID_ARG, "bad grid sizes");
-  cudaError_t e = fr::launch_loss_frobenius(E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, as_stream(stream));
+  cudaError_t e =
+      fr::launch_loss_frobenius(E, E_ref, nx, ny, nu_x, nu_y, loss_out, dLdE_out, as_stream(stream), h->pdl);
   if (e != cudaSuccess) return cuda_error(h, e, "Frobenius loss kernel");
   return FR_OK;
 }
@@ -641,7 +647,7 @@ fr_status fr_adam_step_tanh(fr_handle* h, float* theta, float* m, float* v, cons
   if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) || !finite(lr))
     return set_error(h, FR_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
   cudaError_t e = fr::launch_adam_tanh(theta, m, v, dLdP, offset, n, lr, beta1, beta2, eps, z_min, z_max, step, P_out,
-                                       as_stream(stream));
+                                       as_stream(stream), h->pdl);
   if (e != cudaSuccess) return cuda_error(h, e, "tanh Adam kernel");
   return FR_OK;
 }
@@ -679,6 +685,23 @@ fr_status fr_trace_batch_forward(fr_handle* h, const fr_batch_item* items, int32
 fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32_t n_items,
                                  const fr_options* options, void* stream) {
   return batch(h, items, n_items, options, stream, true);
+}
+
+fr_status fr_set_programmatic_launch(fr_handle* h, int32_t enable) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (enable < 0 || enable > 2) return set_error(h, FR_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+  h->pdl = enable != 0;
+  h->pdl_early = enable == 2;
+  return FR_OK;
+}
+
+fr_status fr_zero(fr_handle* h, void* ptr, uint64_t bytes, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (!ptr && bytes) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
+  if (bytes) FR_CUDA(h, cudaMemsetAsync(ptr, 0, bytes, as_stream(stream)), "cudaMemsetAsync");
+  return FR_OK;
 }
 
 fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms) {

@@ -34,6 +34,13 @@ __device__ __forceinline__ uint2 philox_ray_words(uint64_t seed, uint64_t id) {
   return make_uint2(c0, c1);
 }
 
+// Programmatic dependent launch: pdl_wait() returns once the kernel this one
+// was launched to follow has completed and its writes are visible (at once
+// when the launch did not ask for overlap); pdl_trigger() lets the next kernel
+// on the stream begin launching before this one ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Top 23 bits of a word plus one half, times 2^-23: exact in FP32, in (0,1).
 __device__ __forceinline__ float unit23(uint32_t w) {
   return fmaf((float)(w >> 9), 1.0f / 8388608.0f, 0.5f / 8388608.0f);

@@ -78,8 +78,29 @@ template <int CAP>
 struct Launch {
   int n_items;
   int warps;                    // warps per CTA
+  int early_lens;               // adjoint under programmatic launch: build the lens tables before
+                                // waiting for the previous kernel (which must not write the lens)
   Item items[CAP];
 };
+
+// Launch with or without programmatic dependent launch: with `pdl` the kernel
+// may begin while the previous kernel on the stream is still running; it calls
+// pdl_wait() (griddepcontrol.wait) before it reads anything that kernel wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // Shared-memory bytes a CTA of the forward / adjoint kernel needs for `it`.
 size_t fwd_smem_bytes(const Item& it, bool det);
@@ -89,25 +110,25 @@ size_t adj_smem_bytes(const Item& it, bool det);
 template <int CAP>
 cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
 template <int CAP>
-cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
+cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl);
 cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st);
 cudaError_t launch_fix_to_float(const unsigned long long* q, float* out, size_t n, float inv_scale,
                                 int accumulate, cudaStream_t st);
 cudaError_t launch_absmax(const float* x, size_t n, float* out, cudaStream_t st);
 cudaError_t launch_loss_l2(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y, double* loss,
-                           float* dLdE, cudaStream_t st);
+                           float* dLdE, cudaStream_t st, bool pdl);
 cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1,
-                        float b2, float eps, int32_t* step, cudaStream_t st);
+                        float b2, float eps, int32_t* step, cudaStream_t st, bool pdl);
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st);
 cudaError_t launch_loss_frobenius(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y,
-                                  double* loss, float* dLdE, cudaStream_t st);
+                                  double* loss, float* dLdE, cudaStream_t st, bool pdl);
 cudaError_t launch_reparam_tanh(const float* theta, const float* offset, int64_t n, float z_min, float z_max,
                                 float* P, cudaStream_t st);
 cudaError_t launch_reparam_tanh_adjoint(const float* theta, const float* dLdP, int64_t n, float z_min,
                                         float z_max, float* out, cudaStream_t st);
 cudaError_t launch_adam_tanh(float* theta, float* m, float* v, const float* dLdP, const float* offset, int64_t n,
                              float lr, float b1, float b2, float eps, float z_min, float z_max, int32_t* step,
-                             float* P, cudaStream_t st);
+                             float* P, cudaStream_t st, bool pdl);
 cudaError_t launch_offset_spherical(int n1, int n2, int p, int q, double rx, double ry, double c, double R,
                                     float* out, cudaStream_t st);
 size_t tan_smem_bytes(const Item& it);

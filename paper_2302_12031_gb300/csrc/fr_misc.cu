@@ -2,7 +2,7 @@
 // point -> float, and Adam (row a10).
 #include <algorithm>
 
-#include "fr_internal.h"
+#include "fr_device.cuh"
 
 namespace fr {
 namespace {
@@ -29,6 +29,7 @@ __global__ void k_fix_to_float(const unsigned long long* __restrict__ q, float* 
 __global__ void __launch_bounds__(1024) k_adam(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
                                                const float* __restrict__ g, int64_t n, float lr, float b1, float b2,
                                                float eps, int32_t* step) {
+  pdl_wait();      // the gradient is the previous kernel's output
   __shared__ int s_t;
   if (threadIdx.x == 0) s_t = *step + 1;
   __syncthreads();
@@ -64,9 +65,8 @@ cudaError_t launch_fix_to_float(const unsigned long long* q, float* out, size_t 
 }
 
 cudaError_t launch_adam(float* P, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2,
-                        float eps, int32_t* step, cudaStream_t st) {
-  k_adam<<<1, 1024, 0, st>>>(P, m, v, g, n, lr, b1, b2, eps, step);
-  return cudaGetLastError();
+                        float eps, int32_t* step, cudaStream_t st, bool pdl) {
+  return launch_k(k_adam, dim3(1), dim3(1024), 0, st, pdl, P, m, v, g, n, lr, b1, b2, eps, step);
 }
 
 }  // namespace fr

@@ -11,7 +11,7 @@
 //    variables fused with both maps.
 #include <cooperative_groups.h>
 
-#include "fr_internal.h"
+#include "fr_device.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -113,6 +113,8 @@ __global__ void __cluster_dims__(kObjCluster, 1, 1) __launch_bounds__(kObjThread
   const int nthr = kObjCluster * kObjThreads;
   const int tid = (int)cl.block_rank() * kObjThreads + threadIdx.x;
   const int n = nx * ny;
+  pdl_trigger();
+  pdl_wait();      // E is the previous kernel's output
 
   float p[2] = {0.0f, 0.0f};
   for (int k0 = tid; k0 < n; k0 += kObjUnroll * nthr) {
@@ -207,6 +209,8 @@ __global__ void __cluster_dims__(kObjCluster, 1, 1) __launch_bounds__(kObjThread
   const int nthr = kObjCluster * kObjThreads;
   const int tid = (int)cl.block_rank() * kObjThreads + threadIdx.x;
   const int ncell = ncol * nrow;
+  pdl_trigger();
+  pdl_wait();      // E is the previous kernel's output
   float part[1] = {0.0f};
   for (int q0 = tid; q0 < ncell; q0 += kObjUnroll * nthr) {
     float e[kObjUnroll], r[kObjUnroll];
@@ -258,6 +262,7 @@ __global__ void __launch_bounds__(1024) k_adam_tanh(float* __restrict__ theta, f
                                                     const float* __restrict__ offset, int64_t n, float lr, float b1,
                                                     float b2, float eps, float z_min, float half_range,
                                                     int32_t* step, float* __restrict__ P) {
+  pdl_wait();
   __shared__ int s_t;
   if (threadIdx.x == 0) s_t = *step + 1;
   __syncthreads();
@@ -306,19 +311,17 @@ __global__ void k_offset_spherical(int n1, int n2, int p, int q, double rx, doub
 }  // namespace
 
 cudaError_t launch_loss_l2(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y, double* loss,
-                           float* dLdE, cudaStream_t st) {
+                           float* dLdE, cudaStream_t st, bool pdl) {
   const int ncol = nx + nu_x - 1, nrow = ny + nu_y - 1;
-  k_loss_l2<<<kObjCluster, kObjThreads, 0, st>>>(E, Eref, nx, ny, (nu_x - 1) / 2, (nu_y - 1) / 2, ncol, nrow, loss,
-                                                 dLdE);
-  return cudaGetLastError();
+  return launch_k(k_loss_l2, dim3(kObjCluster), dim3(kObjThreads), 0, st, pdl, E, Eref, nx, ny, (nu_x - 1) / 2,
+                  (nu_y - 1) / 2, ncol, nrow, loss, dLdE);
 }
 
 cudaError_t launch_loss_frobenius(const float* E, const float* Eref, int nx, int ny, int nu_x, int nu_y,
-                                  double* loss, float* dLdE, cudaStream_t st) {
+                                  double* loss, float* dLdE, cudaStream_t st, bool pdl) {
   const int ncol = nx + nu_x - 1, nrow = ny + nu_y - 1;
-  k_loss_frobenius<<<kObjCluster, kObjThreads, 0, st>>>(E, Eref, nx, ny, (nu_x - 1) / 2, (nu_y - 1) / 2, ncol,
-                                                        nrow, loss, dLdE);
-  return cudaGetLastError();
+  return launch_k(k_loss_frobenius, dim3(kObjCluster), dim3(kObjThreads), 0, st, pdl, E, Eref, nx, ny,
+                  (nu_x - 1) / 2, (nu_y - 1) / 2, ncol, nrow, loss, dLdE);
 }
 
 cudaError_t launch_reparam_tanh(const float* theta, const float* offset, int64_t n, float z_min, float z_max,
@@ -337,10 +340,9 @@ cudaError_t launch_reparam_tanh_adjoint(const float* theta, const float* dLdP, i
 
 cudaError_t launch_adam_tanh(float* theta, float* m, float* v, const float* dLdP, const float* offset, int64_t n,
                              float lr, float b1, float b2, float eps, float z_min, float z_max, int32_t* step,
-                             float* P, cudaStream_t st) {
-  k_adam_tanh<<<1, 1024, 0, st>>>(theta, m, v, dLdP, offset, n, lr, b1, b2, eps, z_min, 0.5f * (z_max - z_min),
-                                  step, P);
-  return cudaGetLastError();
+                             float* P, cudaStream_t st, bool pdl) {
+  return launch_k(k_adam_tanh, dim3(1), dim3(1024), 0, st, pdl, theta, m, v, dLdP, offset, n, lr, b1, b2, eps, z_min,
+                  0.5f * (z_max - z_min), step, P);
 }
 
 cudaError_t launch_offset_spherical(int n1, int n2, int p, int q, double rx, double ry, double c, double R,

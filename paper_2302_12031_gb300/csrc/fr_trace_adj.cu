@@ -381,8 +381,13 @@ __global__ void __launch_bounds__(256, 2) k_adjoint(const __grid_constant__ Laun
   }
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  pdl_trigger();
+  // Launched to overlap the previous kernel: dL/dE only after it ends; the
+  // lens too unless the caller has said that kernel does not write it.
+  if (!L.early_lens) pdl_wait();
   if ((KINDS & 4) && it.two_face) build_two_face_tables(it, ls, li);   // ends with __syncthreads
   else build_lens_tables(it, ls);
+  if (L.early_lens) pdl_wait();
   go.fixP = 0.0f;
   if constexpr (DET) {
     // Fixed-point scale 2^40 / (max|dL/dE| * flux / pixel area), a power of two.
@@ -454,14 +459,13 @@ AdjKernel<kMaxItems> pick_adjoint<kMaxItems>(bool det, int nu, int) {
 }
 
 template <int CAP>
-cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
+cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl) {
   const int threads = 32 * L.warps;
   const int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
-  pick_adjoint<CAP>(det, L.items[0].nu, kinds)<<<grid, threads, smem, st>>>(L);
-  return cudaGetLastError();
+  return launch_k(pick_adjoint<CAP>(det, L.items[0].nu, kinds), dim3(grid), dim3(threads), smem, st, pdl, L);
 }
-template cudaError_t launch_adjoint<1>(const Launch<1>&, int, size_t, bool, cudaStream_t);
-template cudaError_t launch_adjoint<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t);
+template cudaError_t launch_adjoint<1>(const Launch<1>&, int, size_t, bool, cudaStream_t, bool);
+template cudaError_t launch_adjoint<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t, bool);
 
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st) {
   const int n = it.nparam;

@@ -170,6 +170,7 @@ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t
 
 template <int CAP, bool DET, int NU, int KINDS>
 __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __grid_constant__ Launch<CAP> L) {
+  pdl_trigger();   // the loss kernel may start launching; it waits for this one to end
   int ii = 0;
   while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
   const Item& it = L.items[ii];

@@ -21,7 +21,7 @@ from . import api
 
 class OptimStep:
     def __init__(self, workloads, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, options=None, graph=True,
-                 device="cuda", adj_options=None, loss="l2", reparam=None):
+                 device="cuda", adj_options=None, loss="l2", reparam=None, pdl=True):
         """`options` apply to both traces unless `adj_options` is given for the adjoint
         (e.g. to record timing events around each trace kernel separately)."""
         if isinstance(workloads, dict):
@@ -30,10 +30,17 @@ class OptimStep:
             raise ValueError("loss must be 'l2' or 'frobenius'")
         self.loss_kind = loss
         self.reparam = reparam
+        self.pdl = pdl   # programmatic dependent launch between the step's kernels
         self.h = api.default_handle()
         self.lr, self.betas, self.eps = lr, betas, eps
         self.options = options
         self.adj_options = adj_options if adj_options is not None else options
+        # The step clears E and dL/dP itself (memsets first), so that the
+        # trace calls accumulate and the four kernels follow one another
+        # directly: with programmatic launch each may start while the previous
+        # one drains.
+        self._fwd_opts = self._accumulating(self.options)
+        self._adj_opts = self._accumulating(self.adj_options)
         # per lens: the exit heights, then (two-face lenses) the entry heights
         n_out = [(w["lens"]["n1"] + 1) * (w["lens"]["n2"] + 1) for w in workloads]
         n_in = [(w["lens"]["n1_in"] + 1) * (w["lens"]["n2_in"] + 1) if w["lens"].get("P_in") is not None else 0
@@ -100,14 +107,25 @@ class OptimStep:
             self.theta.copy_(torch.as_tensor(self.reparam["theta0"], dtype=torch.float32).reshape(-1))
         api.fr_reparam_tanh(self.h, self.theta, self.offset, self.n_params, zmin, zmax, self.P)
 
+    @staticmethod
+    def _accumulating(options):
+        o = api.make_options() if options is None else api.Options.from_buffer_copy(options)
+        o.accumulate = 1
+        return o
+
+    def _clear(self):
+        for E in self.E:
+            api.fr_zero(self.h, E)
+        api.fr_zero(self.h, self.g)
+
     def _forward(self):
         if self.batched:
             items = [pb.batch_item(E=E) for pb, E in zip(self.problems, self.E)]
-            api.fr_trace_batch_forward(self.h, items, self.options)
+            api.fr_trace_batch_forward(self.h, items, self._fwd_opts)
         else:
             pb = self.problems[0]
             api.fr_trace_forward(self.h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS,
-                                 self.options, self.E[0])
+                                 self._fwd_opts, self.E[0])
 
     def _loss(self):
         fn = api.fr_loss_l2 if self.loss_kind == "l2" else api.fr_loss_frobenius
@@ -117,11 +135,11 @@ class OptimStep:
     def _adjoint(self):
         if self.batched:
             items = [pb.batch_item(dLdE=d, dLdP=g) for pb, d, g in zip(self.problems, self.dLdE, self.grads)]
-            api.fr_trace_batch_adjoint(self.h, items, self.adj_options)
+            api.fr_trace_batch_adjoint(self.h, items, self._adj_opts)
         else:
             pb = self.problems[0]
             api.fr_trace_adjoint(self.h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS,
-                                 self.adj_options, self.dLdE[0], self.grads[0])
+                                 self._adj_opts, self.dLdE[0], self.grads[0])
 
     def _adam(self):
         if self.theta is None:
@@ -133,10 +151,16 @@ class OptimStep:
                                   float(self.reparam["z_max"]), self.step_count, self.P)
 
     def eager_step(self):
-        self._forward()
-        self._loss()
-        self._adjoint()
-        self._adam()
+        self._clear()
+        # mode 2: the adjoint follows the loss kernel, which does not write the lens
+        api.fr_set_programmatic_launch(self.h, 2 if self.pdl else 0)
+        try:
+            self._forward()
+            self._loss()
+            self._adjoint()
+            self._adam()
+        finally:
+            api.fr_set_programmatic_launch(self.h, 0)
 
     def _capture(self):
         state = self._state()
@@ -172,6 +196,6 @@ class OptimStep:
     def launches_per_step(self):
         n_items = len(self.problems)
         det = bool(self.options is not None and self.options.deterministic)
-        fwd = 2 + (n_items if det else 0)                 # prep + trace (+ fixed->float)
-        adj = 2 + (2 * n_items if det else 0)             # prep + trace (+ absmax, fixed->float)
-        return fwd + n_items + adj + 1                    # + one loss per lens + Adam
+        fwd = 1 + (n_items if det else 0)                 # trace (+ fixed->float)
+        adj = 1 + (2 * n_items if det else 0)             # trace (+ absmax, fixed->float)
+        return fwd + n_items + adj + 1                    # + one loss per lens + Adam (memsets are not kernels)

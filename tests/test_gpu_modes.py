@@ -226,3 +226,18 @@ def test_stream_wait_times_out_and_completes():
     h = api.default_handle()
     api.fr_stream_wait(h, 1000)
     torch.cuda.synchronize()
+
+
+def test_programmatic_launch_gives_the_same_step():
+    wl = W.config(1)
+    det = api.make_options(deterministic=True)
+    a = step.OptimStep(wl, lr=1e-3, graph=True, options=det, pdl=True)
+    b = step.OptimStep(wl, lr=1e-3, graph=True, options=det, pdl=False)
+    for _ in range(4):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert torch.equal(a.P, b.P) and torch.equal(a.losses(), b.losses())
+    h = api.default_handle()
+    assert api.lib().fr_set_programmatic_launch(h.ptr, 3) == api.FR_ERR_INVALID_ARG
+    api.fr_set_programmatic_launch(h, 0)
