@@ -132,8 +132,8 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
     return set_error(h, FR_ERR_INVALID_ARG, "screen half-widths must be positive and finite");
   if (T->nx < 1 || T->ny < 1 || T->nx > 4096 || T->ny > 4096)
     return set_error(h, FR_ERR_INVALID_ARG, "screen pixels must be 1..4096 per axis");
-  if (T->nu_x != T->nu_y || (T->nu_x != 1 && T->nu_x != 3 && T->nu_x != 5))
-    return set_error(h, FR_ERR_UNSUPPORTED, "filter sizes must be equal and one of 1, 3, 5");
+  if (T->nu_x != T->nu_y || T->nu_x < 1 || T->nu_x > 11 || T->nu_x % 2 == 0)
+    return set_error(h, FR_ERR_UNSUPPORTED, "filter sizes must be equal and odd, 1 to 11");
   if (!(T->alpha > 0.0f) || !finite(T->alpha)) return set_error(h, FR_ERR_INVALID_ARG, "alpha must be positive");
   if (!finite(S->flux)) return set_error(h, FR_ERR_INVALID_ARG, "flux must be finite");
   // Lens.
@@ -302,6 +302,10 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 template <int CAP>
 fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o, bool adjoint,
                     cudaStream_t st) {
+  for (auto& it : items)
+    if (it.nu > 5)
+      return set_error(h, FR_ERR_UNSUPPORTED, "the forward and adjoint traces take filter sizes 1, 3, 5 "
+                                              "(derivative maps up to 11)");
   bool det = o.deterministic != 0;
   // A forward whose histograms cannot live in shared memory deposits with
   // global atomics; 64-bit integer reductions there are faster than float ones,
@@ -778,6 +782,7 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
   Item it;
   fr_status s = make_item(nullptr, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
   if (s != FR_OK) return s;
+  if (it.nu > 5) return set_error(nullptr, FR_ERR_UNSUPPORTED, "filter sizes 1, 3, 5");
   StaticDevice* dev = nullptr;
   s = static_setup(&dev);
   if (s != FR_OK) return s;

@@ -106,11 +106,12 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
   } else {
     lane_range(it, warps, &a0, &a1);
   }
-  float acc[NU][NU];
+  constexpr int NA = NU <= 5 ? NU : 1;   // register footprint (unused for larger filters)
+  float acc[NA][NA];
 #pragma unroll
-  for (int b = 0; b < NU; ++b)
+  for (int b = 0; b < NA; ++b)
 #pragma unroll
-    for (int a = 0; a < NU; ++a) acc[b][a] = 0.0f;
+    for (int a = 0; a < NA; ++a) acc[b][a] = 0.0f;
   int acc_ie = -1, acc_je = -1;
   for (uint64_t j = a0; j < a1; ++j) {
     RayFwd r;
@@ -210,19 +211,20 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
                                 fmaf(slope_t, dt, dZt));
       }
       const float cw = tg.dw * it.inv_area, cx = K * tg.dX, cy = K * tg.dY;
-      if (n_dirs == 1) {
+      if (NU <= 5 && n_dirs == 1) {
         // One direction: consecutive rays of a lane mostly share a footprint;
-        // sum them in registers and flush when the footprint moves.
+        // sum them in registers and flush when the footprint moves (small
+        // footprints only: nu^2 registers).
         if (f.ie != acc_ie || f.je != acc_je) {
-          flush_acc<NU>(acc, acc_ie, acc_je, dE, it.ncol);
+          flush_acc<NA>(acc, acc_ie, acc_je, dE, it.ncol);
           acc_ie = f.ie;
           acc_je = f.je;
         }
 #pragma unroll
-        for (int b = 0; b < NU; ++b) {
+        for (int b = 0; b < NA; ++b) {
           const float rb = cw * Fy[b], sb = cx * Fy[b], tb = cy * gy[b];
 #pragma unroll
-          for (int a = 0; a < NU; ++a) acc[b][a] += fmaf(rb, Fx[a], fmaf(sb, gx[a], tb * Fx[a]));
+          for (int a = 0; a < NA; ++a) acc[b][a] += fmaf(rb, Fx[a], fmaf(sb, gx[a], tb * Fx[a]));
         }
         continue;
       }
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       }
     }
   }
-  flush_acc<NU>(acc, acc_ie, acc_je, dE, it.ncol);
+  flush_acc<NA>(acc, acc_ie, acc_je, dE, it.ncol);
   cnt.reduce_into(cnt_dst);
   __syncthreads();
   RayCount::publish(s_cnt, it.stats);
@@ -247,7 +249,14 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
 using TanKernel = void (*)(Item, int, const float*, int, float*);
 
 TanKernel pick_tangent(int nu) {
-  return nu == 1 ? k_tangent<1> : (nu == 3 ? k_tangent<3> : k_tangent<5>);
+  switch (nu) {
+    case 1: return k_tangent<1>;
+    case 3: return k_tangent<3>;
+    case 5: return k_tangent<5>;
+    case 7: return k_tangent<7>;
+    case 9: return k_tangent<9>;
+    default: return k_tangent<11>;
+  }
 }
 
 }  // namespace
@@ -269,7 +278,7 @@ int tangent_occupancy(int threads, size_t smem, int nu) {
 }
 
 cudaError_t configure_tangent(int optin) {
-  for (int nu = 1; nu <= 5; nu += 2) {
+  for (int nu = 1; nu <= 11; nu += 2) {
     cudaFuncAttributes a;
     cudaError_t e = cudaFuncGetAttributes(&a, pick_tangent(nu));
     if (e != cudaSuccess) return e;

@@ -124,3 +124,35 @@ def test_tangent_argument_errors():
                                  dE)
     # a direction that moves nothing gives a zero map
     assert float(pb.tangent(dP[0]).abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("nu", [7, 11])
+def test_wide_filter_maps_match_oracle(nu):
+    # Sec. 3.1 shows maps with filter sizes 3 and 11: wide filters for the maps
+    wl = W.collimated("c", 192, 9, 24, 1, 2, with_target=False, jitter=1)
+    wl["target"]["nu_x"] = wl["target"]["nu_y"] = nu
+    dP = np.stack([np.random.default_rng(nu).normal(size=wl["lens"]["P"].shape), _unit(wl, 4, 4)])
+    g, o = tangent_both(wl, dP)
+    for q in range(2):
+        assert rel_l2(g[q], o[q]) < TOL_GRAD, (q, rel_l2(g[q], o[q]))
+
+
+def test_flat_lens_maps_sum_to_zero_for_both_filter_sizes():
+    for nu in (3, 11):
+        wl = W.collimated("c", 512, 8, 48, 1, 2, with_target=False)
+        wl["lens"]["P"][:] = 0.0
+        wl["target"]["nu_x"] = wl["target"]["nu_y"] = nu
+        t = api.Problem(wl).tangent(_unit(wl, 3, 4)).double()
+        # zero up to FP32 rounding of the float-atomic sums: the map's terms
+        # cancel to ~1e-5 of their absolute sum
+        assert abs(float(t.sum())) < 5e-5 * float(t.abs().sum())
+
+
+def test_traces_refuse_wide_filters():
+    wl = W.collimated("c", 64, 8, 16, 1, 2, with_target=False)
+    wl["target"]["nu_x"] = wl["target"]["nu_y"] = 7
+    pb = api.Problem(wl)
+    with pytest.raises(api.FreerayError):
+        pb.forward()
+    with pytest.raises(api.FreerayError):
+        pb.adjoint(torch.zeros(pb.ext_shape, device="cuda"))
