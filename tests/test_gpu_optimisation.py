@@ -1,0 +1,51 @@
+"""Whole optimisation runs: the graph-captured step on the GPU against the same
+run of the FP64 oracle (forward, loss, gradient, Adam), on small instances of
+the collimated workload and of the grid-of-point-sources workload. The loss
+curves must agree step by step to the irradiance tolerance and the heights to
+FP32 rounding of a few dozen Adam updates."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2302_12031_gb300 import step
+from paper_2302_12031_gb300 import workloads as W
+from tests.gpu_helpers import TOL_E
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_run(wl, n_steps, lr, loss="l2"):
+    P = wl["lens"]["P"].astype(np.float64).copy()
+    m = np.zeros_like(P).ravel()
+    v = np.zeros_like(P).ravel()
+    theta = P.ravel().copy()
+    losses = []
+    for k in range(1, n_steps + 1):
+        E, _ = O.trace_forward(wl, P=theta.reshape(P.shape))
+        L, d = O.loss_l2(wl, E) if loss == "l2" else O.loss_frobenius(wl, E)
+        losses.append(L)
+        g = O.trace_gradient(wl, d, P=theta.reshape(P.shape))
+        O.adam_step(theta, m, v, g.ravel(), lr=lr, step=k)
+    return np.array(losses), theta
+
+
+@pytest.mark.parametrize("kind,loss", [("collimated", "l2"), ("collimated", "frobenius"), ("grid", "l2")])
+def test_loss_curve_matches_the_oracle(kind, loss):
+    if kind == "collimated":
+        wl = W.collimated("c", 128, 8, 16, 1, 2)
+        n_steps, lr = 30, 2e-3
+    else:
+        wl = W.point("g", 4 * 4 * 2048, 8, 16, 5, 5, 5, grid=(4, 4), grid_size=(0.2, 0.2))
+        n_steps, lr = 20, 1e-3
+    st = step.OptimStep(wl, lr=lr, graph=True, loss=loss)
+    losses = []
+    for _ in range(n_steps):
+        st.step()
+        losses.append(float(st.losses()[0]))
+    losses = np.array(losses)
+    o_losses, o_theta = _oracle_run(wl, n_steps, lr, loss)
+    assert losses[-1] < losses[0] and o_losses[-1] < o_losses[0]
+    rel = np.abs(losses - o_losses) / o_losses
+    assert rel.max() < 10 * TOL_E, rel
+    assert np.abs(st.P.double().cpu().numpy() - o_theta).max() < 1e-4
