@@ -271,6 +271,11 @@ def run_ours(args, rank, world, local):
 
     f_ms = time_steps(graphed(fwd), args.steps, args.warmup, flush)
     fwd_value, _ = D.replica_throughput(n_rays, statistics.mean(f_ms) * 1e-3, dev)
+    # rays by fate, outside the timed region
+    stats = api.new_stats(dev)
+    pb.forward(stats=stats)
+    causes = ("on_screen", "aperture_miss", "out_of_domain", "tir", "off_screen", "invalid", "newton_fail", "other")
+    by_cause = dict(zip(causes, (int(c) for c in stats.cpu().tolist())))
 
     # --- end to end through the public API: pinned host heights in, loss out
     P_host = torch.as_tensor(wl["lens"]["P"], dtype=torch.float32).reshape(-1).pin_memory()
@@ -316,6 +321,7 @@ def run_ours(args, rank, world, local):
                        "step": "graph: prep+forward, loss, prep+adjoint, Adam",
                        "schedule": {"forward": sched_f or "default", "adjoint": sched_a or "default"}},
             "forward_rays_per_s": fwd_value,
+            "rays_by_cause": by_cause,
             "forward_ms": statistics.mean(f_ms),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "rays/s", "h2d_bytes_per_step": P_host.numel() * 4,

@@ -14,6 +14,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fr_internal.h"
 
 struct fr_handle {
@@ -32,6 +34,13 @@ struct fr_handle {
 namespace {
 
 using fr::Item;
+
+// An NVTX range around each entry point (visible to Nsight tools; without a
+// tool attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr size_t kAlign = 256;
 constexpr size_t kHeaderBytes = kAlign;   // reserved at the start of the workspace
@@ -467,6 +476,7 @@ fr_status fr_trace_forward(fr_handle* h, const fr_lens_desc* lens, const fr_sour
                            const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
                            uint64_t ray_count, const fr_options* options, float* E_out, fr_stats* stats_out,
                            void* stream) {
+  NvtxRange nvtx_range("fr_trace_forward");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   const fr_options o = defaults(options);
@@ -483,6 +493,7 @@ fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_sour
                            const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
                            uint64_t ray_count, const fr_options* options, const float* dLdE, float* dLdP_out,
                            fr_stats* stats_out, void* stream) {
+  NvtxRange nvtx_range("fr_trace_adjoint");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   const fr_options o = defaults(options);
@@ -500,6 +511,7 @@ fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_sour
                            const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
                            uint64_t ray_count, const fr_options* options, const float* dP, int32_t n_dirs,
                            float* dE_out, fr_stats* stats_out, void* stream) {
+  NvtxRange nvtx_range("fr_trace_tangent");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   const fr_options o = defaults(options);
@@ -539,6 +551,7 @@ fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_sour
 fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
                          const fr_target_desc* target, uint64_t n_rays, uint64_t seed, uint64_t ray_begin,
                          uint64_t ray_count, const fr_options* options, fr_ray_record* out, void* stream) {
+  NvtxRange nvtx_range("fr_trace_debug");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   const fr_options o = defaults(options);
@@ -553,6 +566,7 @@ fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source
 
 fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny, int32_t nu_x,
                      int32_t nu_y, double* loss_out, float* dLdE_out, void* stream) {
+  NvtxRange nvtx_range("fr_loss_l2");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -565,6 +579,7 @@ fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t n
 
 fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* g, int64_t n, float lr, float beta1,
                        float beta2, float eps, int32_t* step, void* stream) {
+  NvtxRange nvtx_range("fr_adam_step");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!P || !m || !v || !g || !step) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -578,6 +593,7 @@ fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* 
 
 fr_status fr_loss_frobenius(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny, int32_t nu_x,
                             int32_t nu_y, double* loss_out, float* dLdE_out, void* stream) {
+  NvtxRange nvtx_range("fr_loss_frobenius");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!E || !E_ref || !loss_out || !dLdE_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -598,6 +614,7 @@ static fr_status check_range(fr_handle* h, int64_t n, float z_min, float z_max) 
 
 fr_status fr_reparam_tanh(fr_handle* h, const float* theta, const float* offset, int64_t n, float z_min,
                           float z_max, float* P_out, void* stream) {
+  NvtxRange nvtx_range("fr_reparam_tanh");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!theta || !P_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -610,6 +627,7 @@ fr_status fr_reparam_tanh(fr_handle* h, const float* theta, const float* offset,
 
 fr_status fr_reparam_tanh_adjoint(fr_handle* h, const float* theta, const float* dLdP, int64_t n, float z_min,
                                   float z_max, float* dLdtheta_out, void* stream) {
+  NvtxRange nvtx_range("fr_reparam_tanh_adjoint");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!theta || !dLdP || !dLdtheta_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -622,6 +640,7 @@ fr_status fr_reparam_tanh_adjoint(fr_handle* h, const float* theta, const float*
 
 fr_status fr_offset_spherical(fr_handle* h, const fr_lens_desc* lens, float c, float R, float* offset_out,
                               void* stream) {
+  NvtxRange nvtx_range("fr_offset_spherical");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!lens || !offset_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -643,6 +662,7 @@ fr_status fr_offset_spherical(fr_handle* h, const fr_lens_desc* lens, float c, f
 fr_status fr_adam_step_tanh(fr_handle* h, float* theta, float* m, float* v, const float* dLdP, const float* offset,
                             int64_t n, float lr, float beta1, float beta2, float eps, float z_min, float z_max,
                             int32_t* step, float* P_out, void* stream) {
+  NvtxRange nvtx_range("fr_adam_step_tanh");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!theta || !m || !v || !dLdP || !step || !P_out) return set_error(h, FR_ERR_INVALID_ARG, "null pointer");
@@ -658,6 +678,7 @@ fr_status fr_adam_step_tanh(fr_handle* h, float* theta, float* m, float* v, cons
 
 static fr_status batch(fr_handle* h, const fr_batch_item* in, int32_t n_items, const fr_options* options,
                        void* stream, bool adjoint) {
+  NvtxRange nvtx_range(adjoint ? "fr_trace_batch_adjoint" : "fr_trace_batch_forward");
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
   if (!in || n_items < 1 || n_items > fr::kMaxItems)

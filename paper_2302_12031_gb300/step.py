@@ -192,6 +192,39 @@ class OptimStep:
     def losses(self):
         return torch.stack(self.loss).cpu()
 
+    # Checkpoint and resume: the optimiser's whole state. Rays are functions of
+    # (seed, id), so a resumed run continues exactly (bit for bit in
+    # deterministic mode).
+    def state_dict(self):
+        st = {"P": self.P.clone(), "m": self.m.clone(), "v": self.v.clone(), "step": self.step_count.clone(),
+              "lr": self.lr, "betas": self.betas, "eps": self.eps, "loss": self.loss_kind,
+              "seeds": [pb.seed for pb in self.problems], "n_rays": [pb.n_rays for pb in self.problems]}
+        if self.theta is not None:
+            st["theta"] = self.theta.clone()
+            st["offset"] = self.offset.clone()
+            st["reparam"] = {k: v for k, v in self.reparam.items() if k in ("z_min", "z_max")}
+        return st
+
+    def load_state_dict(self, st):
+        if st["seeds"] != [pb.seed for pb in self.problems] or st["n_rays"] != [pb.n_rays for pb in self.problems]:
+            raise ValueError("the checkpoint is of other rays")
+        if (st.get("theta") is None) != (self.theta is None) or st["P"].numel() != self.P.numel():
+            raise ValueError("the checkpoint is of another parametrisation")
+        torch.cuda.synchronize()
+        for name in ("P", "m", "v"):
+            getattr(self, name).copy_(st[name])
+        self.step_count.copy_(st["step"])
+        if self.theta is not None:
+            self.theta.copy_(st["theta"])
+            self.offset.copy_(st["offset"])
+        torch.cuda.synchronize()
+
+    def save(self, path):
+        torch.save(self.state_dict(), path)
+
+    def load(self, path):
+        self.load_state_dict(torch.load(path, map_location=self.P.device, weights_only=False))
+
     # Kernel launches per step (for the launch count of a timed region).
     def launches_per_step(self):
         n_items = len(self.problems)

@@ -241,3 +241,51 @@ def test_programmatic_launch_gives_the_same_step():
     h = api.default_handle()
     assert api.lib().fr_set_programmatic_launch(h.ptr, 3) == api.FR_ERR_INVALID_ARG
     api.fr_set_programmatic_launch(h, 0)
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    wl = W.config(1)
+    det = api.make_options(deterministic=True)
+    a = step.OptimStep(wl, lr=1e-3, graph=True, options=det)
+    for _ in range(3):
+        a.step()
+    a.save(str(tmp_path / "ckpt.pt"))
+    for _ in range(3):
+        a.step()
+    b = step.OptimStep(wl, lr=1e-3, graph=True, options=det)
+    b.load(str(tmp_path / "ckpt.pt"))
+    for _ in range(3):
+        b.step()
+    torch.cuda.synchronize()
+    assert torch.equal(a.P, b.P) and torch.equal(a.m, b.m) and torch.equal(a.v, b.v)
+    assert int(a.step_count) == int(b.step_count) == 6
+    other = W.config(1)
+    other["seed"] = 99
+    c = step.OptimStep(other, lr=1e-3, graph=False, options=det)
+    with pytest.raises(ValueError):
+        c.load(str(tmp_path / "ckpt.pt"))
+
+
+def test_non_finite_control_heights_lose_rays_not_the_image():
+    # a NaN height: the rays over its patches are culled (and counted), E stays finite
+    for wl in (W.config(1, with_target=False), W.point("p", 1 << 15, 8, 16, 3, 4, 5, with_target=False)):
+        wl["lens"]["P"][3, 4] = float("nan")
+        pb = api.Problem(wl)
+        stats = api.new_stats()
+        E = pb.forward(stats=stats)
+        counts = stats.cpu().numpy()
+        assert torch.isfinite(E).all()
+        assert counts.sum() == wl["n_rays"] and counts[0] < wl["n_rays"]
+        g = pb.adjoint(torch.ones(pb.ext_shape, device="cuda"))
+        assert torch.isfinite(g).all()
+
+
+def test_lens_below_its_entry_face_is_counted_invalid():
+    wl = W.point("p", 1 << 14, 8, 16, 3, 4, 5, with_target=False)
+    wl["lens"]["P"][:] = wl["lens"]["z_in"] - 0.05          # the freeform below the flat entry face
+    pb = api.Problem(wl)
+    stats = api.new_stats()
+    E = pb.forward(stats=stats)
+    counts = stats.cpu().numpy()
+    assert float(E.abs().sum()) == 0.0
+    assert counts[5] > 0 and counts[0] == 0                # FR_RAY_INVALID
