@@ -128,7 +128,11 @@ typedef struct fr_options {
   int32_t warps_per_cta;    /* 0 -> tuned; 1..32 */
   int32_t rays_per_lane;    /* 0 -> tuned; 1..64 */
   int32_t ctas_per_sm;      /* 0 -> tuned; 1..8 */
-  int32_t hist_mode;        /* 0 auto, 1 global atomics, 2 shared-memory privatised */
+  int32_t hist_mode;        /* 0 auto, 1 global atomics, 2 shared-memory privatised,
+                               3 shared-memory window (point sources, float mode): the central
+                               part of the extended grid that fits in shared memory is
+                               privatised, deposits outside it go to global memory; auto picks
+                               it for a point source whose extended grid does not fit */
   void* event_begin;        /* optional cudaEvent_t, recorded on the stream right before the
                                trace kernel (not the prep or conversion kernels) */
   void* event_end;          /* optional cudaEvent_t, recorded right after the trace kernel */
@@ -136,7 +140,9 @@ typedef struct fr_options {
                                the triangle mesh of Sec. 2.2.2 with mesh_nu x mesh_nv rectangles
                                (two triangles each) per knot span product; 1..64 */
   int32_t mesh_nv;          /* 0 with mesh_nu = 0, else 1..64 */
-  int32_t reserved[6];
+  int32_t window_cells;     /* hist_mode 3: at most this many cells in the window; 0 -> as
+                               many as shared memory holds */
+  int32_t reserved[5];
 } fr_options;
 
 /* Per-cause ray counts (device, uint64). Kernels add to it; zero it first. */

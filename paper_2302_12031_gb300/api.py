@@ -52,8 +52,8 @@ class Options(C.Structure):
                 ("warps_per_cta", C.c_int32), ("rays_per_lane", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("hist_mode", C.c_int32),
                 ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
-                ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32), ("window_cells", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class Stats(C.Structure):
@@ -302,7 +302,7 @@ def fr_trace_forward_static(lens, source, target, n_rays, seed, ray_begin, ray_c
 # --- descriptors from a workload dict ----------------------------------------
 
 def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newton_tol=0.0, warps_per_cta=0,
-                 rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0)):
+                 rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0), window_cells=0):
     """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel."""
     o = Options()
     o.deterministic = int(deterministic)
@@ -314,6 +314,7 @@ def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newto
     o.ctas_per_sm = ctas_per_sm
     o.hist_mode = hist_mode
     o.mesh_nu, o.mesh_nv = mesh
+    o.window_cells = window_cells
     if events is not None:
         o.event_begin = events[0].cuda_event
         o.event_end = events[1].cuda_event

@@ -247,6 +247,8 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   it->newton_tol = o.newton_tol;
   if (o.mesh_nu < 0 || o.mesh_nu > 64 || o.mesh_nv < 0 || o.mesh_nv > 64 || (o.mesh_nu > 0) != (o.mesh_nv > 0))
     return set_error(h, FR_ERR_INVALID_ARG, "mesh_nu, mesh_nv must both be 0 or both 1..64");
+  if (o.hist_mode < 0 || o.hist_mode > 3 || o.window_cells < 0)
+    return set_error(h, FR_ERR_INVALID_ARG, "hist_mode must be 0..3 and window_cells >= 0");
   if (it->kind == FR_SOURCE_POINT && o.mesh_nu > 0) {
     it->mesh_nu = o.mesh_nu;
     it->mesh_nv = o.mesh_nv;
@@ -285,6 +287,32 @@ bool want_smem_hist(const Item& it, const fr_options& o, bool det) {
   return hist <= 100 * 1024;
 }
 
+// Float-mode forward of one point-source lens whose extended grid does not fit
+// in shared memory (or hist_mode 3): a window of the grid does. Point-source
+// rays come in random order, so no CTA owns a part of the screen; every CTA
+// privatises the same central window, as large as shared memory allows next
+// to the lens tables (or window_cells), and as square as the grid allows.
+// One CTA per SM holds it.
+bool plan_window(Item* it, const fr_options& o, int smem_optin) {
+  if (o.deterministic || it->kind != FR_SOURCE_POINT || it->two_face) return false;
+  if (o.hist_mode == 1 || o.hist_mode == 2) return false;
+  if (o.hist_mode == 0 && want_smem_hist(*it, o, false)) return false;
+  const size_t tables = fr::lens_tables_bytes(*it);
+  const size_t room = (size_t)smem_optin > tables + 4096 ? (size_t)smem_optin - tables - 4096 : 0;
+  long cells = (long)(room / 4);
+  if (o.window_cells > 0) cells = std::min<long>(cells, o.window_cells);
+  if (cells < 1) return false;
+  const int side = (int)std::sqrt((double)cells);
+  const int w = (int)std::min<long>(it->ncol, std::max<long>(side, cells / it->nrow));
+  const int hgt = (int)std::min<long>(it->nrow, cells / w);
+  if (w < 1 || hgt < 1) return false;
+  it->win_c0 = (it->ncol - w) / 2;
+  it->win_c1 = it->win_c0 + w;
+  it->win_r0 = (it->nrow - hgt) / 2;
+  it->win_r1 = it->win_r0 + hgt;
+  return true;
+}
+
 // Splits `total_ctas` over the items in proportion to their estimated cost.
 void assign_ctas(std::vector<Item>& items, int total_ctas) {
   double cost_sum = 0.0;
@@ -316,15 +344,20 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
       return set_error(h, FR_ERR_UNSUPPORTED, "the forward and adjoint traces take filter sizes 1, 3, 5 "
                                               "(derivative maps up to 11)");
   bool det = o.deterministic != 0;
-  // A forward whose histograms cannot live in shared memory deposits with
+  // A point-source forward privatises a window of its grid (plan_window).
+  const bool window = !adjoint && items.size() == 1 && plan_window(&items[0], o, h->smem_optin);
+  // Another forward whose histograms cannot live in shared memory deposits with
   // global atomics; 64-bit integer reductions there are faster than float ones,
   // so it runs the fixed-point (deterministic) kernel and converts at the end.
-  if (!adjoint && !det) {
+  if (!adjoint && !det && !window) {
     bool any_smem = false;
     for (auto& it : items) any_smem |= want_smem_hist(it, o, false);
     det = !any_smem;
   }
-  const int warps = pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind : FR_SOURCE_POINT);
+  // 16 warps in the one CTA per SM of the window form, else pick_warps.
+  const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 16) : 16)
+                           : pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind
+                                                                                           : FR_SOURCE_POINT);
   // Workspace.
   size_t at = kHeaderBytes;
   std::vector<ItemWs> ws(items.size());
@@ -341,7 +374,7 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     it.Pfix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].pfix);
     it.gmax = reinterpret_cast<float*>(h->ws + ws[i].gmax);
     schedule_item(&it, warps, o);
-    if (!adjoint) it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
+    if (!adjoint) it.smem_hist = window ? 2 : (want_smem_hist(it, o, det) ? 1 : 0);
     smem = std::max(smem, adjoint ? fr::adj_smem_bytes(it, det) : fr::fwd_smem_bytes(it, det));
   }
   // Outputs.

@@ -70,7 +70,10 @@ struct Item {
   // Schedule: the item's rays are split evenly over the lanes of CTAs
   // [cta_begin, cta_end) of the launch (lane_range in fr_device.cuh).
   int max_ctas;                 // CTAs worth launching (every lane gets a minimum run)
-  int smem_hist;                // forward: 1 = privatised histogram in shared memory
+  int smem_hist;                // forward: 1 = privatised histogram in shared memory,
+                                // 2 = a window of it (rows win_r0..win_r1-1, columns
+                                // win_c0..win_c1-1 of the extended grid) in shared memory
+  int win_r0, win_r1, win_c0, win_c1;
   int cta_begin, cta_end;
 };
 
@@ -104,6 +107,7 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
 
 // Shared-memory bytes a CTA of the forward / adjoint kernel needs for `it`.
 size_t fwd_smem_bytes(const Item& it, bool det);
+size_t lens_tables_bytes(const Item& it);   // the lens tables part of it
 size_t adj_smem_bytes(const Item& it, bool det);
 
 // Launchers (return the CUDA error of the launch).

@@ -11,7 +11,9 @@
 // registers (with atomics) when it does: consecutive collimated rays usually
 // share a pixel, so most rays cost no atomic. The flush goes to a privatised
 // histogram in shared memory when the extended grid fits, else straight to
-// global memory.
+// global memory. A point-source lens whose grid does not fit privatises a
+// central window of it; flushes outside the window go to global memory as
+// 16-byte vector reductions (one per aligned group of four cells).
 #include "fr_device.cuh"
 
 namespace fr {
@@ -41,7 +43,55 @@ struct Target {
   unsigned long long* sh_q;
   float* gl_f;
   unsigned long long* gl_q;
+  // Window form (float mode): sh_u holds rows wr0..wr1-1, columns wc0..wc1-1
+  // (wcol = wc1 - wc0 per row); vec: gl_f is 16-byte aligned.
+  bool win, vec;
+  int wr0, wr1, wc0, wc1, wcol, ncell;
 };
+
+// Adds NU consecutive values v to global cells idx..idx+NU-1, where
+// OFF = idx mod 4: one float4 reduction per aligned group of four cells
+// (zeros in the lanes outside the run); groups that would pass the end of the
+// grid are added cell by cell.
+template <int NU, int OFF>
+__device__ __forceinline__ void red_run_vec(float* g, int idx, int ncell, const float (&v)[NU]) {
+  constexpr int NCH = (OFF + NU + 3) / 4;
+  const int c0 = idx - OFF;
+#pragma unroll
+  for (int m = 0; m < NCH; ++m) {
+    const int c = c0 + 4 * m;
+    float l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * m + j - OFF;
+      l[j] = (k >= 0 && k < NU) ? v[k] : 0.0f;
+    }
+    if (c + 4 <= ncell) {
+      atomicAdd(reinterpret_cast<float4*>(g + c), make_float4(l[0], l[1], l[2], l[3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = 4 * m + j - OFF;
+        if (k >= 0 && k < NU) atomicAdd(g + c + j, l[j]);
+      }
+    }
+  }
+}
+
+template <int NU>
+__device__ __forceinline__ void red_run(const Target& tg, int idx, const float (&v)[NU]) {
+  if (!tg.vec) {
+#pragma unroll
+    for (int a = 0; a < NU; ++a) atomicAdd(tg.gl_f + idx + a, v[a]);
+    return;
+  }
+  switch (idx & 3) {
+    case 0: red_run_vec<NU, 0>(tg.gl_f, idx, tg.ncell, v); break;
+    case 1: red_run_vec<NU, 1>(tg.gl_f, idx, tg.ncell, v); break;
+    case 2: red_run_vec<NU, 2>(tg.gl_f, idx, tg.ncell, v); break;
+    default: red_run_vec<NU, 3>(tg.gl_f, idx, tg.ncell, v); break;
+  }
+}
 
 template <int NU, bool DET>
 struct FootAcc {
@@ -49,7 +99,8 @@ struct FootAcc {
   typename AccT<DET>::type v[NU][NU];
 };
 
-template <int NU, bool DET>
+// WIN: the kernel may run in the window form (single point-source lens, float mode).
+template <int NU, bool DET, bool WIN = false>
 __device__ __forceinline__ void acc_flush(FootAcc<NU, DET>& acc, const Target& tg, Bbox& bb) {
   if (acc.ie < 0) return;
   bb.imin = min(bb.imin, acc.ie);
@@ -57,6 +108,24 @@ __device__ __forceinline__ void acc_flush(FootAcc<NU, DET>& acc, const Target& t
   bb.jmin = min(bb.jmin, acc.je);
   bb.jmax = max(bb.jmax, acc.je);
   const int base = acc.je * tg.ncol + acc.ie;
+  if constexpr (WIN && !DET) {
+    if (tg.win) {
+      const bool cols_in = acc.ie >= tg.wc0 && acc.ie + NU <= tg.wc1;
+#pragma unroll
+      for (int b = 0; b < NU; ++b) {
+        const int row = acc.je + b;
+        if (cols_in && row >= tg.wr0 && row < tg.wr1) {
+          unsigned int* sh = tg.sh_u + (row - tg.wr0) * tg.wcol + (acc.ie - tg.wc0);
+#pragma unroll
+          for (int a = 0; a < NU; ++a) atomicAdd(sh + a, __float2uint_rn(acc.v[b][a] * tg.sh_scale));
+        } else {
+          red_run<NU>(tg, base + b * tg.ncol, acc.v[b]);
+        }
+      }
+      acc.ie = -1;
+      return;
+    }
+  }
 #pragma unroll
   for (int b = 0; b < NU; ++b) {
 #pragma unroll
@@ -76,13 +145,13 @@ __device__ __forceinline__ void acc_flush(FootAcc<NU, DET>& acc, const Target& t
 }
 
 // E_ij += w F_ij / (w_x w_y), F_ij = (f_i / S_x) (f_j / S_y).
-template <int NU, bool DET>
+template <int NU, bool DET, bool WIN = false>
 __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const Target& tg, FootAcc<NU, DET>& acc,
                                         Bbox& bb) {
   Foot<NU> f;
   if (!footprint<NU>(it, r.X, r.Y, f)) return;
   if (f.ie != acc.ie || f.je != acc.je) {
-    acc_flush<NU, DET>(acc, tg, bb);
+    acc_flush<NU, DET, WIN>(acc, tg, bb);
     acc.ie = f.ie;
     acc.je = f.je;
 #pragma unroll
@@ -159,17 +228,20 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
         RayFwd r;
         trace_point(it, ls, id, zmin, zmax, r);
         cnt.add(r.status, s_cnt);
-        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, KINDS == 2>(it, r, tg, acc, bb);
       }
     }
   }
-  acc_flush<NU, DET>(acc, tg, bb);
+  acc_flush<NU, DET, KINDS == 2>(acc, tg, bb);
 }
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Launch bounds: two CTAs per SM of up to 384 (collimated) or 256 threads; the
+// single point-source kernel also runs one CTA of 512 threads (window form).
 template <int CAP, bool DET, int NU, int KINDS>
-__global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __grid_constant__ Launch<CAP> L) {
+__global__ void __launch_bounds__(KINDS == 1 ? 384 : (KINDS == 2 ? 512 : 256), KINDS == 2 ? 1 : 2)
+    k_forward(const __grid_constant__ Launch<CAP> L) {
   pdl_trigger();   // the loss kernel may start launching; it waits for this one to end
   int ii = 0;
   while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
@@ -182,12 +254,20 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
   uint64_t a, b;
   lane_range(it, L.warps, &a, &b);
   Target tg;
-  tg.smem = it.smem_hist != 0;
+  tg.smem = it.smem_hist == 1;
   tg.ncol = it.ncol;
   tg.sh_u = reinterpret_cast<unsigned int*>(hist_raw);
   tg.sh_q = reinterpret_cast<unsigned long long*>(hist_raw);
   tg.gl_f = it.E;
   tg.gl_q = it.Efix;
+  tg.win = !DET && it.smem_hist == 2;
+  tg.vec = (reinterpret_cast<uintptr_t>(it.E) & 15) == 0;
+  tg.wr0 = it.win_r0;
+  tg.wr1 = it.win_r1;
+  tg.wc0 = it.win_c0;
+  tg.wc1 = it.win_c1;
+  tg.wcol = it.win_c1 - it.win_c0;
+  tg.ncell = ncell;
   {
     // 2^31 / (rays of this CTA x largest contribution of one ray), a power of two.
     const uint64_t n = it.ray_end - it.ray_begin;
@@ -204,6 +284,9 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
     } else {
       for (int q = threadIdx.x; q < ncell; q += blockDim.x) tg.sh_u[q] = 0u;
     }
+  } else if (tg.win) {
+    const int nwin = (tg.wr1 - tg.wr0) * tg.wcol;
+    for (int q = threadIdx.x; q < nwin; q += blockDim.x) tg.sh_u[q] = 0u;
   }
   __shared__ int s_bb[4];
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
@@ -219,7 +302,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
   Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
   run_lane<NU, DET, KINDS>(it, ls, li, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
   cnt.reduce_into(cnt_dst);
-  if (tg.smem) {
+  if (tg.smem || tg.win) {
     // Touched window: warp reductions, then one shared atomic per warp.
     const int i0 = __reduce_min_sync(0xffffffffu, bb.imin), i1 = __reduce_max_sync(0xffffffffu, bb.imax);
     const int j0 = __reduce_min_sync(0xffffffffu, bb.jmin), j1 = __reduce_max_sync(0xffffffffu, bb.jmax);
@@ -244,6 +327,38 @@ __global__ void __launch_bounds__(KINDS == 1 ? 384 : 256, 2) k_forward(const __g
       } else {
         const unsigned int v = tg.sh_u[idx];
         if (v) atomicAdd(tg.gl_f + idx, (float)v / tg.sh_scale);
+      }
+    }
+  }
+  if constexpr (KINDS == 2 && !DET) {
+    if (tg.win && s_bb[1] >= 0) {
+      // Flush the touched part of the window: per row, one float4 reduction
+      // per aligned group of four global cells.
+      const int r0 = max(tg.wr0, s_bb[2]), r1 = min(tg.wr1 - 1, s_bb[3] + NU - 1);
+      const int c0 = max(tg.wc0, s_bb[0]), c1 = min(tg.wc1 - 1, s_bb[1] + NU - 1);
+      const float inv_scale = 1.0f / tg.sh_scale;
+      const int maxch = (c1 - c0 + 3) / 4 + 1;          // groups a run of c1 - c0 + 1 cells can touch
+      const int n = r0 <= r1 && c0 <= c1 ? (r1 - r0 + 1) * maxch : 0;
+      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int rr = r0 + q / maxch, m = q % maxch;
+        const int gA = rr * tg.ncol + c0, gB = rr * tg.ncol + c1;
+        const int c = (gA & ~3) + 4 * m;
+        if (c > gB) continue;
+        const unsigned int* srow = tg.sh_u + (rr - tg.wr0) * tg.wcol;
+        float l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int g = c + j;
+          l[j] = (g >= gA && g <= gB) ? (float)srow[g - rr * tg.ncol - tg.wc0] * inv_scale : 0.0f;
+        }
+        if (tg.vec && c + 4 <= ncell) {
+          if (l[0] != 0.0f || l[1] != 0.0f || l[2] != 0.0f || l[3] != 0.0f)
+            atomicAdd(reinterpret_cast<float4*>(tg.gl_f + c), make_float4(l[0], l[1], l[2], l[3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (l[j] != 0.0f) atomicAdd(tg.gl_f + c + j, l[j]);
+        }
       }
     }
   }
@@ -306,9 +421,12 @@ __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, 
 
 size_t fwd_smem_bytes(const Item& it, bool det) {
   size_t b = tables_bytes(it);
-  if (it.smem_hist) b += (size_t)it.ncol * it.nrow * (det ? 8 : 4);
+  if (it.smem_hist == 2) b += (size_t)(it.win_r1 - it.win_r0) * (it.win_c1 - it.win_c0) * 4;
+  else if (it.smem_hist) b += (size_t)it.ncol * it.nrow * (det ? 8 : 4);
   return b;
 }
+
+size_t lens_tables_bytes(const Item& it) { return tables_bytes(it); }
 
 // The kernel variant for (deterministic, nu, kinds); KINDS as in run_lane.
 template <int CAP>
