@@ -354,8 +354,10 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     for (auto& it : items) any_smem |= want_smem_hist(it, o, false);
     det = !any_smem;
   }
-  // 16 warps in the one CTA per SM of the window form, else pick_warps.
-  const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 16) : 16)
+  // The one CTA per SM of the window form: 20 warps with filter sizes 1 and 3
+  // (the kernel's launch bounds allow 640 threads there), 16 with 5; else pick_warps.
+  const int win_cap = items[0].nu <= 3 ? 20 : 16;
+  const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, win_cap) : win_cap)
                            : pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind
                                                                                            : FR_SOURCE_POINT);
   // Workspace.
