@@ -271,10 +271,16 @@ void schedule_item(Item* it, int warps, const fr_options& o) {
   it->max_ctas = (int)std::min<uint64_t>((count + per_cta - 1) / per_cta, 1 << 20);
 }
 
-// Warps per CTA: 12 for the collimated forward kernel (whose launch bounds
-// allow 384 threads: two such CTAs share an SM with their histograms), 8 else.
-int pick_warps(const fr_options& o, bool adjoint, int kind) {
-  const int cap = (!adjoint && kind == FR_SOURCE_COLLIMATED) ? 12 : 8;
+// Warps per CTA: the most the trace kernels' launch bounds allow with two
+// CTAs per SM. The collimated forward takes 14 in float mode (12
+// deterministic), the single-lens collimated float adjoint with filter sizes 1
+// and 3 takes 10, every other variant 8. (Collimated 2048^2 rays on GB300:
+// forward 61.1 us with 12 warps, 59.1 us with 14; adjoint 79.9 us with 8,
+// 76.6 us with 10.)
+int pick_warps(const fr_options& o, bool adjoint, int kind, bool det, int nu) {
+  int cap = 8;
+  if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = det ? 12 : 14;
+  else if (adjoint && kind == FR_SOURCE_COLLIMATED && !det && nu <= 3) cap = 10;
   return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, cap) : cap;
 }
 
@@ -358,8 +364,9 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   // (the kernel's launch bounds allow 640 threads there), 16 with 5; else pick_warps.
   const int win_cap = items[0].nu <= 3 ? 20 : 16;
   const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, win_cap) : win_cap)
-                           : pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind
-                                                                                           : FR_SOURCE_POINT);
+                           : pick_warps(o, adjoint,
+                                        items.size() == 1 && !items[0].two_face ? items[0].kind : FR_SOURCE_POINT,
+                                        det, items[0].nu);
   // Workspace.
   size_t at = kHeaderBytes;
   std::vector<ItemWs> ws(items.size());
@@ -858,7 +865,7 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
   it.Efix = reinterpret_cast<unsigned long long*>(base + w.efix);
   it.E = E_out;
   it.stats = stats_out;
-  const int warps = pick_warps(o, false, it.kind);
+  const int warps = pick_warps(o, false, it.kind, det, it.nu);
   schedule_item(&it, warps, o);
   it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
   const size_t smem = fr::fwd_smem_bytes(it, det);

@@ -237,11 +237,14 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Launch bounds: two CTAs per SM of up to 384 (collimated) or 256 threads; the
-// single point-source kernel also runs one CTA per SM of 640 threads (filter
-// sizes 1, 3) or 512 (size 5) in the window form.
+// Launch bounds: two CTAs per SM of up to 448 (collimated, float), 384
+// (collimated, deterministic) or 256 threads; the single point-source kernel
+// also runs one CTA per SM of 640 threads (filter sizes 1, 3) or 512 (size 5)
+// in the window form.
 template <int CAP, bool DET, int NU, int KINDS>
-__global__ void __launch_bounds__(KINDS == 1 ? 384 : (KINDS == 2 ? (!DET && NU <= 3 ? 640 : 512) : 256), KINDS == 2 ? 1 : 2)
+__global__ void __launch_bounds__(KINDS == 1 ? (DET ? 384 : 448)
+                                             : (KINDS == 2 ? (!DET && NU <= 3 ? 640 : 512) : 256),
+                                  KINDS == 2 ? 1 : 2)
     k_forward(const __grid_constant__ Launch<CAP> L) {
   pdl_trigger();   // the loss kernel may start launching; it waits for this one to end
   int ii = 0;
