@@ -41,7 +41,7 @@ FLOPS_ADJ_COLLIMATED = 290
 # DRAM bytes (read + write) per launch of each trace kernel on this workload,
 # from the ncu capture summarised in profiles/trace_kernels_collimated_2048x2048.md.
 # Set to None whenever the kernel changes after that capture.
-PROFILED_DRAM_BYTES = {"forward": 106496, "adjoint": 135168}
+PROFILED_DRAM_BYTES = {"forward": 108288, "adjoint": 135680}
 
 
 def parse():
@@ -278,19 +278,22 @@ def run_ours(args, rank, world, local):
     by_cause = dict(zip(causes, (int(c) for c in stats.cpu().tolist())))
 
     # --- end to end through the public API: pinned host heights in, loss out
+    # (the step's graph copies the heights in and the loss out: one launch and
+    # one synchronisation per step)
     P_host = torch.as_tensor(wl["lens"]["P"], dtype=torch.float32).reshape(-1).pin_memory()
-    loss_host = torch.zeros((), dtype=torch.float64).pin_memory()
-    e2e_ms = []
+    loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    st.attach_host_io(P_host, loss_host)
+    e2e_ms, e2e_losses = [], []
     for k in range(args.warmup + args.steps):
         flush()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st.P.copy_(P_host, non_blocking=True)
         st.step()
-        loss_host.copy_(st.loss[0], non_blocking=True)
         torch.cuda.current_stream().synchronize()
+        e2e_losses.append(float(loss_host[0]))
         if k >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    st.attach_host_io(None, None)
     e2e_value, _ = D.replica_throughput(n_rays, statistics.mean(e2e_ms) * 1e-3, dev)
 
     # --- roofline of the dominant kernel (the adjoint trace), timed live

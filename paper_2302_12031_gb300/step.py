@@ -81,8 +81,32 @@ class OptimStep:
             self._init_reparam(workloads, sizes, device)
         self.n_rays = sum(pb.n_rays for pb in self.problems)
         self.batched = len(self.problems) > 1
+        self.P_host = self.loss_host = None
         self.graph = None
         if graph:
+            self._capture()
+
+    def attach_host_io(self, P_host=None, loss_host=None):
+        """Make every step read its control heights from host memory and write
+        its losses to host memory: P_host (n_params float32, pinned) is copied
+        into the device heights before the forward trace, the device losses into
+        loss_host (one float64 per lens, pinned) after the Adam update. Both
+        copies are part of the step (captured into its graph), so a caller that
+        feeds heights from the host and reads the loss back pays one graph launch
+        and one synchronisation per step. None detaches."""
+        if P_host is not None:
+            if self.theta is not None:
+                raise ValueError("with a reparametrisation the heights follow theta; attach no P_host")
+            if (P_host.device.type != "cpu" or not P_host.is_pinned() or P_host.dtype != torch.float32
+                    or P_host.numel() != self.n_params or not P_host.is_contiguous()):
+                raise ValueError("P_host must be a contiguous pinned float32 CPU tensor of n_params values")
+        if loss_host is not None:
+            if (loss_host.device.type != "cpu" or not loss_host.is_pinned() or loss_host.dtype != torch.float64
+                    or loss_host.numel() != len(self.problems) or not loss_host.is_contiguous()):
+                raise ValueError("loss_host must be a contiguous pinned float64 CPU tensor, one value per lens")
+        self.P_host = P_host
+        self.loss_host = loss_host
+        if self.graph is not None:
             self._capture()
 
     def _init_reparam(self, workloads, sizes, device):
@@ -151,6 +175,8 @@ class OptimStep:
                                   float(self.reparam["z_max"]), self.step_count, self.P)
 
     def eager_step(self):
+        if self.P_host is not None:
+            self.P.copy_(self.P_host, non_blocking=True)
         self._clear()
         # mode 2: the adjoint follows the loss kernel, which does not write the lens
         api.fr_set_programmatic_launch(self.h, 2 if self.pdl else 0)
@@ -161,6 +187,10 @@ class OptimStep:
             self._adam()
         finally:
             api.fr_set_programmatic_launch(self.h, 0)
+        if self.loss_host is not None:
+            flat = self.loss_host.view(-1)
+            for k, L in enumerate(self.loss):
+                flat[k:k + 1].copy_(L.view(1), non_blocking=True)
 
     def _capture(self):
         state = self._state()

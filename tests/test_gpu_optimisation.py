@@ -49,3 +49,33 @@ def test_loss_curve_matches_the_oracle(kind, loss):
     rel = np.abs(losses - o_losses) / o_losses
     assert rel.max() < 10 * TOL_E, rel
     assert np.abs(st.P.double().cpu().numpy() - o_theta).max() < 1e-4
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_step_with_host_io(graph):
+    # Heights copied in from pinned host memory and the loss copied out, inside
+    # the step: in deterministic mode bit-identical to a step on device heights.
+    from paper_2302_12031_gb300 import api
+    wl = W.config(1)
+    kw = dict(lr=1e-2, graph=graph, options=api.make_options(deterministic=True))
+    a, b = step.OptimStep(wl, **kw), step.OptimStep(wl, **kw)
+    P_host = torch.as_tensor(wl["lens"]["P"], dtype=torch.float32).reshape(-1).pin_memory()
+    L_host = torch.full((1,), -1.0, dtype=torch.float64).pin_memory()
+    a.attach_host_io(P_host, L_host)
+    for k in range(3):
+        a.P.fill_(7.0)                      # overwritten by the copy from P_host
+        a.step()
+        b.step()
+        torch.cuda.synchronize()
+        assert float(L_host[0]) == float(b.loss[0])
+        assert torch.equal(a.P, b.P)
+        P_host.copy_(b.P.cpu())             # the next step starts from b's heights
+    a.attach_host_io(None, None)
+    a.step()
+    b.step()
+    torch.cuda.synchronize()
+    assert torch.equal(a.P, b.P) and float(L_host[0]) != float(b.loss[0])
+    with pytest.raises(ValueError):
+        a.attach_host_io(torch.zeros(a.n_params), None)          # not pinned
+    with pytest.raises(ValueError):
+        a.attach_host_io(None, torch.zeros(2, dtype=torch.float64).pin_memory())
