@@ -360,13 +360,28 @@ def extra_workloads(args, flush, world):
     k = max(3, args.steps // 4)
     for name, wls in (("point_16M", W.config(3)), ("grid_8x8_64M_batched_graph", W.config(4)),
                       ("sweep_32_lenses_batched_graph", W.config(5))):
-        st = step.OptimStep(wls, lr=1e-3, graph=True)
+        st = step.OptimStep(wls, lr=1e-3, graph=True)      # point sources: traced in the coherent ray order
+        order_ms = None
+        if st.order is not None:
+            # the order depends on the source and aperture only: built once per problem (time of the build
+            # alone, outside the step)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st.problems[0].ray_order()
+            torch.cuda.synchronize()
+            order_ms = 1e3 * (time.perf_counter() - t1)
         ms = time_steps(st.step, k, 2, flush)
         rays = st.n_rays
         rays_per_s, t = D.replica_throughput(rays, statistics.mean(ms) * 1e-3)
         out[name] = {"rays_per_step": rays, "ms_per_step": 1e3 * t, "rays_per_s": rays_per_s,
                      "steps_per_s": 1.0 / t, "lenses": len(st.problems)}
         del st
+        if order_ms is not None:
+            st = step.OptimStep(wls, lr=1e-3, graph=True, ray_order=False)
+            ms = time_steps(st.step, k, 2, flush)
+            out[name]["ray_order_build_ms"] = order_ms
+            out[name]["ms_per_step_in_id_order"] = statistics.mean(ms)
+            del st
         torch.cuda.empty_cache()
     # triangle mesh (Sec. 2.2.2) against Newton on the 16M-ray point source:
     # step time, and the freeform hits' distance to Newton's on 2^16 rays

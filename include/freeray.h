@@ -140,9 +140,14 @@ typedef struct fr_options {
                                the triangle mesh of Sec. 2.2.2 with mesh_nu x mesh_nv rectangles
                                (two triangles each) per knot span product; 1..64 */
   int32_t mesh_nv;          /* 0 with mesh_nu = 0, else 1..64 */
+  const uint32_t* ray_order; /* point sources, optional (device): the n_rays + 1 words written
+                               by fr_ray_order, in whose order the forward, adjoint and
+                               derivative-map traces take the rays; the sums are over the
+                               same rays. Only for calls over all rays of one lens with a
+                               flat entry face (FR_ERR_INVALID_ARG else); NULL: id order */
   int32_t window_cells;     /* hist_mode 3: at most this many cells in the window; 0 -> as
                                many as shared memory holds */
-  int32_t reserved[5];
+  int32_t reserved[3];
 } fr_options;
 
 /* Per-cause ray counts (device, uint64). Kernels add to it; zero it first. */
@@ -318,6 +323,28 @@ fr_status fr_set_programmatic_launch(fr_handle* h, int32_t mode);
 /* Zeroes `bytes` bytes of device memory at `ptr` on `stream` (a memset node
  * when captured): for clearing outputs that later calls accumulate into. */
 fr_status fr_zero(fr_handle* h, void* ptr, uint64_t bytes, void* stream);
+
+/* A coherent order of the rays of a point source or grid of point sources
+ * (the rays of Sec. 2.2.1). order_out (device, n_rays + 1 uint32) receives a
+ * permutation of the ray ids 0..n_rays-1 followed by a count H: positions
+ * 0..H-1 hold the rays that meet the aperture, grouped by source and, within a
+ * source, sorted by the cell of a G x G grid over the aperture where the ray
+ * meets the entry plane z = z_in (cells in Z order; G a power of two up to 128,
+ * about 128 rays per cell); positions H..n_rays-1 hold rays that miss it (the
+ * test has a 1e-5 relative margin toward "meets", so a ray placed among the
+ * misses misses in the trace too). With this order (fr_options.ray_order) the
+ * traces split only the H rays over their lanes and count the others as
+ * aperture misses: no warp idles on misses, rays next to each other meet the
+ * same knot spans and land on the same pixels, and their Newton iterations
+ * agree. The order is a function of the source, the aperture (rx, ry, z_in),
+ * n_rays and seed only, not of the control heights, so one order serves every
+ * optimisation step. Within a cell the order is the order of arrival (it may
+ * differ from call to call); deterministic-mode results do not depend on it.
+ * Needs n_rays < 2^32 and a flat entry face; uses the handle's workspace (4
+ * bytes per cell); asynchronous on `stream`. FR_ERR_UNSUPPORTED for
+ * collimated sources. */
+fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source, uint64_t n_rays,
+                       uint64_t seed, uint32_t* order_out, void* stream);
 
 /* Wait for `stream` on the host by polling, at most timeout_ms milliseconds.
  * Returns FR_ERR_TIMEOUT if the work has not finished by then. */

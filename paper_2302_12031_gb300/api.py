@@ -52,8 +52,8 @@ class Options(C.Structure):
                 ("warps_per_cta", C.c_int32), ("rays_per_lane", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("hist_mode", C.c_int32),
                 ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
-                ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32), ("window_cells", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32), ("ray_order", C.c_void_p),
+                ("window_cells", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class Stats(C.Structure):
@@ -117,6 +117,8 @@ _SIGNATURES = {
     "fr_stream_wait": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "fr_set_programmatic_launch": (C.c_int, [C.c_void_p, C.c_int32]),
     "fr_zero": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
+    "fr_ray_order": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
+                               C.c_void_p]),
     "fr_trace_forward_static": (C.c_int, [C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
                                           C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -286,6 +288,15 @@ def fr_zero(h, t, stream=None):
     h.check(lib().fr_zero(h.ptr, _ptr(t), t.numel() * t.element_size(), _stream(stream)))
 
 
+def fr_ray_order(h, lens, source, n_rays, seed, order_out, stream=None):
+    """Coherent ray order of a point source into order_out (int32 CUDA tensor of n_rays + 1:
+    the permuted ray ids, then the number of them that meet the aperture)."""
+    if order_out.dtype != torch.int32 or order_out.numel() != n_rays + 1 or not order_out.is_contiguous():
+        raise ValueError("order_out must be a contiguous int32 tensor of n_rays + 1 elements")
+    h.check(lib().fr_ray_order(h.ptr, C.byref(lens), C.byref(source), n_rays, seed, _ptr(order_out),
+                               _stream(stream)))
+
+
 def fr_stream_wait(h, timeout_ms, stream=None):
     h.check(lib().fr_stream_wait(h.ptr, _stream(stream), timeout_ms))
 
@@ -302,7 +313,8 @@ def fr_trace_forward_static(lens, source, target, n_rays, seed, ray_begin, ray_c
 # --- descriptors from a workload dict ----------------------------------------
 
 def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newton_tol=0.0, warps_per_cta=0,
-                 rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0), window_cells=0):
+                 rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0), window_cells=0,
+                 ray_order=None):
     """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel."""
     o = Options()
     o.deterministic = int(deterministic)
@@ -315,6 +327,10 @@ def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newto
     o.hist_mode = hist_mode
     o.mesh_nu, o.mesh_nv = mesh
     o.window_cells = window_cells
+    if ray_order is not None:
+        if ray_order.dtype != torch.int32 or not ray_order.is_cuda or not ray_order.is_contiguous():
+            raise ValueError("ray_order must be a contiguous int32 CUDA tensor (uint32 ids)")
+        o.ray_order = ray_order.data_ptr()
     if events is not None:
         o.event_begin = events[0].cuda_event
         o.event_end = events[1].cuda_event
@@ -392,6 +408,13 @@ class Problem:
         fr_trace_forward(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                          options, E, stats)
         return E
+
+    def ray_order(self, h=None):
+        """fr_ray_order for this problem's point source (int32 tensor: n_rays ray ids, then
+        the number H of them, first in the order, that meet the aperture)."""
+        out = torch.empty(self.n_rays + 1, dtype=torch.int32, device=self.device)
+        fr_ray_order(h or default_handle(), self.lens, self.source, self.n_rays, self.seed, out)
+        return out
 
     def n_params(self):
         n = self.ctrl_shape[0] * self.ctrl_shape[1]

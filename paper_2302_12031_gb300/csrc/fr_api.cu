@@ -249,6 +249,13 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
     return set_error(h, FR_ERR_INVALID_ARG, "mesh_nu, mesh_nv must both be 0 or both 1..64");
   if (o.hist_mode < 0 || o.hist_mode > 3 || o.window_cells < 0)
     return set_error(h, FR_ERR_INVALID_ARG, "hist_mode must be 0..3 and window_cells >= 0");
+  if (o.ray_order) {
+    if (it->kind != FR_SOURCE_POINT || it->two_face)
+      return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to point sources and a flat entry face");
+    if (begin != 0 || it->ray_end != n_rays || n_rays > 0xffffffffull)
+      return set_error(h, FR_ERR_INVALID_ARG, "ray_order needs a call over all rays (and n_rays < 2^32)");
+    it->order = o.ray_order;
+  }
   if (it->kind == FR_SOURCE_POINT && o.mesh_nu > 0) {
     it->mesh_nu = o.mesh_nu;
     it->mesh_nv = o.mesh_nv;
@@ -345,6 +352,8 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 template <int CAP>
 fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o, bool adjoint,
                     cudaStream_t st) {
+  if (o.ray_order && items.size() > 1)
+    return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to one lens, not to a batch");
   for (auto& it : items)
     if (it.nu > 5)
       return set_error(h, FR_ERR_UNSUPPORTED, "the forward and adjoint traces take filter sizes 1, 3, 5 "
@@ -760,6 +769,38 @@ fr_status fr_set_programmatic_launch(fr_handle* h, int32_t enable) {
   if (enable < 0 || enable > 2) return set_error(h, FR_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
   h->pdl = enable != 0;
   h->pdl_early = enable == 2;
+  return FR_OK;
+}
+
+fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source, uint64_t n_rays,
+                       uint64_t seed, uint32_t* order_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  NvtxRange nvtx_range("fr_ray_order");
+  if (!order_out) return set_error(h, FR_ERR_INVALID_ARG, "order_out is null");
+  if (!source) return set_error(h, FR_ERR_INVALID_ARG, "null descriptor");
+  if (source->kind != FR_SOURCE_POINT) return set_error(h, FR_ERR_UNSUPPORTED, "ray orders are for point sources");
+  if (n_rays > 0xffffffffull) return set_error(h, FR_ERR_UNSUPPORTED, "ray orders need n_rays < 2^32");
+  // The order does not depend on the screen: any valid target completes the item.
+  fr_target_desc t;
+  std::memset(&t, 0, sizeof t);
+  t.z_screen = lens ? lens->z_in + 1.0f : 1.0f;
+  t.Rx = t.Ry = 1.0f;
+  t.nx = t.ny = 1;
+  t.nu_x = t.nu_y = 1;
+  t.alpha = 1.0f;
+  const fr_options o = defaults(nullptr);
+  Item it;
+  fr_status s = make_item(h, lens, source, &t, n_rays, seed, 0, UINT64_MAX, o, &it);
+  if (s != FR_OK) return s;
+  if (it.two_face) return set_error(h, FR_ERR_UNSUPPORTED, "ray orders need a flat entry face");
+  const int G = fr::ray_order_grid(it);
+  const uint64_t nk = fr::ray_order_keys(it, G);
+  cudaStream_t st = as_stream(stream);
+  s = ensure_workspace(h, kHeaderBytes + nk * sizeof(uint32_t), st);
+  if (s != FR_OK) return s;
+  cudaError_t e = fr::launch_ray_order(it, G, reinterpret_cast<uint32_t*>(h->ws + kHeaderBytes), order_out, st);
+  if (e != cudaSuccess) return cuda_error(h, e, "ray order kernels");
   return FR_OK;
 }
 

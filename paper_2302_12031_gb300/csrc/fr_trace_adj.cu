@@ -286,7 +286,26 @@ __device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, const LensS
   acc.k = -1;
   GCache<NU> gc;
   gc.ie = gc.je = -1;
-  if (a < b) {
+  if ((KINDS & 2) && it.order) {
+    // Ray order: chunks dealt over the lanes (OrderCursor), next id loaded one
+    // ray ahead.
+    float Nv[4], dNv[4];
+    OrderCursor oc;
+    oc.init(it, true);
+    uint32_t next = oc.valid() ? __ldg(it.order + oc.p) : 0u;
+    while (oc.valid()) {
+      const uint64_t id = next;
+      oc.advance();
+      if (oc.valid()) next = __ldg(it.order + oc.p);
+      RayFwd r;
+      trace_point(it, ls, id, zmin, zmax, r);
+      cnt.add(r.status, s_cnt);
+      if (r.status == FR_RAY_ON_SCREEN) {
+        basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+        adjoint_ray<NU, DET, false>(it, ls, r, gc, Nv, dNv, acc, go);
+      }
+    }
+  } else if (a < b) {
     if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
       const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
       uint32_t row = (uint32_t)(a / (uint64_t)it.cols);
@@ -408,6 +427,7 @@ __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 32
   unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
   run_adjoint_lane<NU, DET, KINDS>(it, ls, li, a, b, zmin, zmax, go, cnt, cnt_dst);
   cnt.reduce_into(cnt_dst);
+  ordered_misses_into(it, cnt_dst);
   __syncthreads();
   for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
     if constexpr (DET) {

@@ -198,7 +198,22 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
       return;
     }
   }
-  if (a < b) {
+  if ((KINDS & 2) && it.order) {
+    // Ray order: chunks dealt over the lanes (OrderCursor); the next id is
+    // loaded one ray ahead, its latency hidden behind the current ray's trace.
+    OrderCursor oc;
+    oc.init(it, false);
+    uint32_t next = oc.valid() ? __ldg(it.order + oc.p) : 0u;
+    while (oc.valid()) {
+      const uint64_t id = next;
+      oc.advance();
+      if (oc.valid()) next = __ldg(it.order + oc.p);
+      RayFwd r;
+      trace_point(it, ls, id, zmin, zmax, r);
+      cnt.add(r.status, s_cnt);
+      if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, KINDS == 2>(it, r, tg, acc, bb);
+    }
+  } else if (a < b) {
     if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
       const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
       uint32_t row = (uint32_t)(a / (uint64_t)it.cols);
@@ -277,7 +292,8 @@ __global__ void __launch_bounds__(KINDS == 1 ? (DET ? 384 : 448)
     const uint64_t n = it.ray_end - it.ray_begin;
     const uint64_t G = (uint64_t)(it.cta_end - it.cta_begin);
     const uint64_t ci = (uint64_t)((int)blockIdx.x - it.cta_begin);
-    const float rays = (float)(n * (ci + 1) / G - n * ci / G) + 1.0f;
+    const float rays = (float)((KINDS & 2) && it.order ? OrderCursor::max_per_cta(it, L.warps)
+                                                        : n * (ci + 1) / G - n * ci / G) + 1.0f;
     int e = 0;
     frexpf(rays * it.omega0 * it.inv_area, &e);
     tg.sh_scale = ldexpf(1.0f, 31 - e);
@@ -306,6 +322,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? (DET ? 384 : 448)
   Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
   run_lane<NU, DET, KINDS>(it, ls, li, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
   cnt.reduce_into(cnt_dst);
+  ordered_misses_into(it, cnt_dst);
   if (tg.smem || tg.win) {
     // Touched window: warp reductions, then one shared atomic per warp.
     const int i0 = __reduce_min_sync(0xffffffffu, bb.imin), i1 = __reduce_max_sync(0xffffffffu, bb.imax);

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
     } else {
       float zmin, zmax;
       zbounds(ls, &zmin, &zmax);
+      if (it.order) id = __ldg(it.order + j);
       trace_point(it, ls, id, zmin, zmax, r);
       m = 0u;
       if (r.status == FR_RAY_ON_SCREEN) {
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
   }
   flush_acc<NA>(acc, acc_ie, acc_je, dE, it.ncol);
   cnt.reduce_into(cnt_dst);
+  ordered_misses_into(it, cnt_dst);
   __syncthreads();
   RayCount::publish(s_cnt, it.stats);
 }

@@ -21,9 +21,12 @@ from . import api
 
 class OptimStep:
     def __init__(self, workloads, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, options=None, graph=True,
-                 device="cuda", adj_options=None, loss="l2", reparam=None, pdl=True):
+                 device="cuda", adj_options=None, loss="l2", reparam=None, pdl=True, ray_order=True):
         """`options` apply to both traces unless `adj_options` is given for the adjoint
-        (e.g. to record timing events around each trace kernel separately)."""
+        (e.g. to record timing events around each trace kernel separately).
+        ray_order: a single point-source lens with a flat entry face traces its
+        rays in the coherent order of fr_ray_order (built once here: it does not
+        depend on the heights)."""
         if isinstance(workloads, dict):
             workloads = [workloads]
         if loss not in ("l2", "frobenius"):
@@ -81,6 +84,13 @@ class OptimStep:
             self._init_reparam(workloads, sizes, device)
         self.n_rays = sum(pb.n_rays for pb in self.problems)
         self.batched = len(self.problems) > 1
+        self.order = None
+        pb0 = self.problems[0]
+        if (ray_order and not self.batched and pb0.source.kind == api.FR_SOURCE_POINT
+                and pb0.entry_shape is None):
+            self.order = pb0.ray_order(self.h)
+            for o in (self._fwd_opts, self._adj_opts):
+                o.ray_order = self.order.data_ptr()
         self.P_host = self.loss_host = None
         self.graph = None
         if graph:
