@@ -362,12 +362,14 @@ def extra_workloads(args, flush, world):
                       ("sweep_32_lenses_batched_graph", W.config(5))):
         st = step.OptimStep(wls, lr=1e-3, graph=True)      # point sources: traced in the coherent ray order
         order_ms = None
-        if st.order is not None:
-            # the order depends on the source and aperture only: built once per problem (time of the build
-            # alone, outside the step)
+        if any(o is not None for o in st.orders):
+            # the orders depend on the sources and apertures only: built once per problem (time of the
+            # builds alone, outside the step)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            st.problems[0].ray_order()
+            for pb, o in zip(st.problems, st.orders):
+                if o is not None:
+                    pb.ray_order()
             torch.cuda.synchronize()
             order_ms = 1e3 * (time.perf_counter() - t1)
         ms = time_steps(st.step, k, 2, flush)

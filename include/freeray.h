@@ -180,6 +180,9 @@ typedef struct fr_batch_item {
   const float* dLdE;     /* device: adjoint input, extended grid */
   float* dLdP;           /* device: adjoint output, (n1+1)*(n2+1) */
   fr_stats* stats;       /* device or NULL */
+  const uint32_t* ray_order; /* point source with a flat entry face, optional (device): this
+                               item's fr_ray_order output (as fr_options.ray_order for one
+                               lens); NULL: id order */
 } fr_batch_item;
 
 typedef struct fr_handle fr_handle;

@@ -72,7 +72,8 @@ class RayRecord(C.Structure):
 class BatchItem(C.Structure):
     _fields_ = [("lens", LensDesc), ("source", SourceDesc), ("target", TargetDesc),
                 ("n_rays", C.c_uint64), ("seed", C.c_uint64),
-                ("E", C.c_void_p), ("dLdE", C.c_void_p), ("dLdP", C.c_void_p), ("stats", C.c_void_p)]
+                ("E", C.c_void_p), ("dLdE", C.c_void_p), ("dLdP", C.c_void_p), ("stats", C.c_void_p),
+                ("ray_order", C.c_void_p)]
 
 
 RECORD_FIELDS = [name for name, _ in RayRecord._fields_]
@@ -390,7 +391,7 @@ class Problem:
         self.ctrl_z = ctrl_z.contiguous()
         self.lens.ctrl_z = self.ctrl_z.data_ptr()
 
-    def batch_item(self, E=None, dLdE=None, dLdP=None, stats=None):
+    def batch_item(self, E=None, dLdE=None, dLdP=None, stats=None, ray_order=None):
         it = BatchItem()
         it.lens, it.source, it.target = self.lens, self.source, self.target
         it.n_rays, it.seed = self.n_rays, self.seed
@@ -398,6 +399,10 @@ class Problem:
         it.dLdE = None if dLdE is None else dLdE.data_ptr()
         it.dLdP = None if dLdP is None else dLdP.data_ptr()
         it.stats = None if stats is None else stats.data_ptr()
+        if ray_order is not None:
+            if ray_order.dtype != torch.int32 or not ray_order.is_cuda or ray_order.numel() != self.n_rays + 1:
+                raise ValueError("ray_order must be the int32 CUDA tensor of Problem.ray_order()")
+            it.ray_order = ray_order.data_ptr()
         return it
 
     # Convenience wrappers (allocate outputs with torch, then call the ABI).

@@ -279,14 +279,14 @@ void schedule_item(Item* it, int warps, const fr_options& o) {
 }
 
 // Warps per CTA: the most the trace kernels' launch bounds allow with two
-// CTAs per SM. The collimated forward takes 14 in float mode (12
-// deterministic), the single-lens collimated float adjoint with filter sizes 1
-// and 3 takes 10, every other variant 8. (Collimated 2048^2 rays on GB300:
-// forward 61.1 us with 12 warps, 59.1 us with 14; adjoint 79.9 us with 8,
-// 76.6 us with 10.)
+// CTAs per SM. The collimated forward takes 14 in float mode with filter sizes
+// 1 and 3 (12 with 5), 12 deterministic (8 with 5), the single-lens collimated
+// float adjoint with filter sizes 1 and 3 takes 10, every other variant 8.
+// (Collimated 2048^2 rays on GB300: forward 61.1 us with 12 warps, 59.1 us
+// with 14; adjoint 79.9 us with 8, 76.6 us with 10.)
 int pick_warps(const fr_options& o, bool adjoint, int kind, bool det, int nu) {
   int cap = 8;
-  if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = det ? 12 : 14;
+  if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = nu <= 3 ? (det ? 12 : 14) : (det ? 8 : 12);
   else if (adjoint && kind == FR_SOURCE_COLLIMATED && !det && nu <= 3) cap = 10;
   return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, cap) : cap;
 }
@@ -306,12 +306,17 @@ bool want_smem_hist(const Item& it, const fr_options& o, bool det) {
 // privatises the same central window, as large as shared memory allows next
 // to the lens tables (or window_cells), and as square as the grid allows.
 // One CTA per SM holds it.
-bool plan_window(Item* it, const fr_options& o, int smem_optin) {
-  if (o.deterministic || it->kind != FR_SOURCE_POINT || it->two_face) return false;
+// In a batch (budget > 0) every item whose grid does not fit takes a window
+// (collimated items too), sized so that a CTA needs at most `budget` bytes:
+// two CTAs of the batch kernel share an SM.
+bool plan_window(Item* it, const fr_options& o, int smem_optin, size_t budget = 0) {
+  if (o.deterministic || it->two_face) return false;
+  if (budget == 0 && it->kind != FR_SOURCE_POINT) return false;
   if (o.hist_mode == 1 || o.hist_mode == 2) return false;
   if (o.hist_mode == 0 && want_smem_hist(*it, o, false)) return false;
   const size_t tables = fr::lens_tables_bytes(*it);
-  const size_t room = (size_t)smem_optin > tables + 4096 ? (size_t)smem_optin - tables - 4096 : 0;
+  const size_t cap = budget > 0 ? std::min(budget, (size_t)smem_optin) : (size_t)smem_optin;
+  const size_t room = cap > tables + 4096 ? cap - tables - 4096 : 0;
   long cells = (long)(room / 4);
   if (o.window_cells > 0) cells = std::min<long>(cells, o.window_cells);
   if (cells < 1) return false;
@@ -325,6 +330,8 @@ bool plan_window(Item* it, const fr_options& o, int smem_optin) {
   it->win_r1 = it->win_r0 + hgt;
   return true;
 }
+
+constexpr int kBatchWaves = 4;
 
 // Splits `total_ctas` over the items in proportion to their estimated cost.
 void assign_ctas(std::vector<Item>& items, int total_ctas) {
@@ -359,12 +366,25 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
       return set_error(h, FR_ERR_UNSUPPORTED, "the forward and adjoint traces take filter sizes 1, 3, 5 "
                                               "(derivative maps up to 11)");
   bool det = o.deterministic != 0;
-  // A point-source forward privatises a window of its grid (plan_window).
+  // A point-source forward privatises a window of its grid (plan_window); in a
+  // batch every item whose grid does not fit does (two CTAs per SM).
   const bool window = !adjoint && items.size() == 1 && plan_window(&items[0], o, h->smem_optin);
+  std::vector<char> batch_window(items.size(), 0);
+  bool any_batch_window = false;
+  if (!adjoint && items.size() > 1 && !det)
+    for (size_t i = 0; i < items.size(); ++i) {
+      // the whole grid when it fits the two-CTA budget beside the tables, else a window
+      const size_t budget = (size_t)h->smem_optin / 2 - 1024;
+      const size_t full = fr::lens_tables_bytes(items[i]) + (size_t)items[i].ncol * items[i].nrow * 4;
+      fr_options ob = o;
+      if (ob.hist_mode == 0 && full > budget) ob.hist_mode = 3;
+      batch_window[i] = plan_window(&items[i], ob, h->smem_optin, budget) ? 1 : 0;
+      any_batch_window |= batch_window[i] != 0;
+    }
   // Another forward whose histograms cannot live in shared memory deposits with
   // global atomics; 64-bit integer reductions there are faster than float ones,
   // so it runs the fixed-point (deterministic) kernel and converts at the end.
-  if (!adjoint && !det && !window) {
+  if (!adjoint && !det && !window && !any_batch_window) {
     bool any_smem = false;
     for (auto& it : items) any_smem |= want_smem_hist(it, o, false);
     det = !any_smem;
@@ -392,7 +412,7 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     it.Pfix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].pfix);
     it.gmax = reinterpret_cast<float*>(h->ws + ws[i].gmax);
     schedule_item(&it, warps, o);
-    if (!adjoint) it.smem_hist = window ? 2 : (want_smem_hist(it, o, det) ? 1 : 0);
+    if (!adjoint) it.smem_hist = (window || batch_window[i]) ? 2 : (want_smem_hist(it, o, det) ? 1 : 0);
     smem = std::max(smem, adjoint ? fr::adj_smem_bytes(it, det) : fr::fwd_smem_bytes(it, det));
   }
   // Outputs.
@@ -438,7 +458,10 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   int total_ctas = 0;
   for (auto& it : items) total_ctas += it.max_ctas;
   if (total_ctas > 0) {
-    const int want = std::max<int>(1, h->sm_count * per_sm);
+    // A batch launches four waves: its items' CTAs take unequal times (sizes,
+    // sources and nets differ), and with one wave the SMs that finish first
+    // idle until the longest CTA ends.
+    const int want = std::max<int>(1, h->sm_count * per_sm * (items.size() > 1 ? kBatchWaves : 1));
     if (items.size() == 1) {
       items[0].cta_begin = 0;
       items[0].cta_end = std::min(want, items[0].max_ctas);
@@ -749,6 +772,12 @@ static fr_status batch(fr_handle* h, const fr_batch_item* in, int32_t n_items, c
     items[i].dLdE = in[i].dLdE;
     items[i].dLdP = in[i].dLdP;
     items[i].stats = in[i].stats;
+    if (in[i].ray_order) {
+      if (items[i].kind != FR_SOURCE_POINT || items[i].two_face || in[i].n_rays > 0xffffffffull)
+        return set_error(h, FR_ERR_INVALID_ARG,
+                         "item %d: ray_order applies to point sources (n_rays < 2^32) with a flat entry face", i);
+      items[i].order = in[i].ray_order;
+    }
   }
   return run_trace<fr::kMaxItems>(h, items, o, adjoint, as_stream(stream));
 }

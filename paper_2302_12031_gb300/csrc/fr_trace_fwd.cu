@@ -181,6 +181,8 @@ __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const T
 template <int NU, bool DET, int KINDS>
 __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li, const Target& tg, uint64_t a,
                          uint64_t b, float zmin, float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb) {
+  // Kernels that take point-source items may run the window form (float mode).
+  constexpr bool WINK = (KINDS & 2) != 0;
   FootAcc<NU, DET> acc;
   acc.ie = -1;
   if constexpr ((KINDS & 4) != 0) {
@@ -192,9 +194,9 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
         const uint32_t col = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id % (uint64_t)it.cols) : 0u;
         trace_two_face(it, ls, li, id, row, col, r, e);
         cnt.add(r.status, s_cnt);
-        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
       }
-      acc_flush<NU, DET>(acc, tg, bb);
+      acc_flush<NU, DET, WINK>(acc, tg, bb);
       return;
     }
   }
@@ -211,7 +213,7 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
       RayFwd r;
       trace_point(it, ls, id, zmin, zmax, r);
       cnt.add(r.status, s_cnt);
-      if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, KINDS == 2>(it, r, tg, acc, bb);
+      if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
     }
   } else if (a < b) {
     if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
@@ -226,7 +228,7 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
           RayFwd r;
           trace_collimated_row(it, ls, row, col, inv_cols, inv_rows, rp, r);
           cnt.add(r.status, s_cnt);
-          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
           if (++col == (uint32_t)it.cols) { col = 0; ++row; }
         }
       } else {
@@ -234,7 +236,7 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
           RayFwd r;
           trace_collimated(it, ls, row, col, a + j, inv_cols, inv_rows, r);
           cnt.add(r.status, s_cnt);
-          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET>(it, r, tg, acc, bb);
+          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
           if (++col == (uint32_t)it.cols) { col = 0; ++row; }
         }
       }
@@ -243,21 +245,23 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
         RayFwd r;
         trace_point(it, ls, id, zmin, zmax, r);
         cnt.add(r.status, s_cnt);
-        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, KINDS == 2>(it, r, tg, acc, bb);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
       }
     }
   }
-  acc_flush<NU, DET, KINDS == 2>(acc, tg, bb);
+  acc_flush<NU, DET, WINK>(acc, tg, bb);
 }
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Launch bounds: two CTAs per SM of up to 448 (collimated, float), 384
-// (collimated, deterministic) or 256 threads; the single point-source kernel
-// also runs one CTA per SM of 640 threads (filter sizes 1, 3) or 512 (size 5)
-// in the window form.
+// Launch bounds: two CTAs per SM of up to 448 (collimated, float, filter
+// sizes 1 and 3), 384 (collimated: float with size 5, deterministic with 1 and
+// 3), 256 (collimated deterministic with 5; batches); the single point-source
+// kernel also runs one CTA per SM of 640 threads (filter sizes 1, 3) or 512
+// (size 5) in the window form. The variants of filter sizes 1 and 3 do not
+// spill; those of size 5 spill 150-200 bytes at any two-CTA bound.
 template <int CAP, bool DET, int NU, int KINDS>
-__global__ void __launch_bounds__(KINDS == 1 ? (DET ? 384 : 448)
+__global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? (DET ? 384 : 448) : (DET ? 256 : 384))
                                              : (KINDS == 2 ? (!DET && NU <= 3 ? 640 : 512) : 256),
                                   KINDS == 2 ? 1 : 2)
     k_forward(const __grid_constant__ Launch<CAP> L) {
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? (DET ? 384 : 448)
       }
     }
   }
-  if constexpr (KINDS == 2 && !DET) {
+  if constexpr ((KINDS & 2) != 0 && !DET) {
     if (tg.win && s_bb[1] >= 0) {
       // Flush the touched part of the window: per row, one float4 reduction
       // per aligned group of four global cells.

@@ -24,8 +24,8 @@ class OptimStep:
                  device="cuda", adj_options=None, loss="l2", reparam=None, pdl=True, ray_order=True):
         """`options` apply to both traces unless `adj_options` is given for the adjoint
         (e.g. to record timing events around each trace kernel separately).
-        ray_order: a single point-source lens with a flat entry face traces its
-        rays in the coherent order of fr_ray_order (built once here: it does not
+        ray_order: point-source lenses with a flat entry face trace their rays
+        in the coherent order of fr_ray_order (built once here: it does not
         depend on the heights)."""
         if isinstance(workloads, dict):
             workloads = [workloads]
@@ -84,11 +84,11 @@ class OptimStep:
             self._init_reparam(workloads, sizes, device)
         self.n_rays = sum(pb.n_rays for pb in self.problems)
         self.batched = len(self.problems) > 1
-        self.order = None
-        pb0 = self.problems[0]
-        if (ray_order and not self.batched and pb0.source.kind == api.FR_SOURCE_POINT
-                and pb0.entry_shape is None):
-            self.order = pb0.ray_order(self.h)
+        # per lens: its ray order (point sources with a flat entry face) or None
+        self.orders = [pb.ray_order(self.h) if ray_order and pb.source.kind == api.FR_SOURCE_POINT
+                       and pb.entry_shape is None else None for pb in self.problems]
+        self.order = None if self.batched else self.orders[0]
+        if self.order is not None:
             for o in (self._fwd_opts, self._adj_opts):
                 o.ray_order = self.order.data_ptr()
         self.P_host = self.loss_host = None
@@ -154,7 +154,7 @@ class OptimStep:
 
     def _forward(self):
         if self.batched:
-            items = [pb.batch_item(E=E) for pb, E in zip(self.problems, self.E)]
+            items = [pb.batch_item(E=E, ray_order=r) for pb, E, r in zip(self.problems, self.E, self.orders)]
             api.fr_trace_batch_forward(self.h, items, self._fwd_opts)
         else:
             pb = self.problems[0]
@@ -168,7 +168,8 @@ class OptimStep:
 
     def _adjoint(self):
         if self.batched:
-            items = [pb.batch_item(dLdE=d, dLdP=g) for pb, d, g in zip(self.problems, self.dLdE, self.grads)]
+            items = [pb.batch_item(dLdE=d, dLdP=g, ray_order=r)
+                     for pb, d, g, r in zip(self.problems, self.dLdE, self.grads, self.orders)]
             api.fr_trace_batch_adjoint(self.h, items, self._adj_opts)
         else:
             pb = self.problems[0]
