@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--tune", action="store_true", help="autotune the trace kernels' schedule first")
+    p.add_argument("--point-kernels", action="store_true",
+                   help="time only the point-source trace kernels (16M rays), in id order and in the ray order")
     return p.parse_args()
 
 
@@ -451,11 +453,57 @@ def extra_workloads(args, flush, world):
     return out
 
 
+def run_point_kernels(args):
+    """The point-source forward and adjoint trace kernels alone (16M rays, 24x24 net, 256^2 bins), each
+    step launching the forward and the adjoint in ray-id order and then in the coherent ray order, every
+    launch timed by CUDA events with an L2 flush before it. One JSON line of mean kernel times (us). Under
+    ncu, the launches of step k are the (4 k)-th to (4 k + 3)-th trace kernels."""
+    import torch
+    from paper_2302_12031_gb300 import api
+    from paper_2302_12031_gb300 import workloads as W
+    wl = W.config(3, with_target=False)
+    pb = api.Problem(wl)
+    h = api.default_handle()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    order = pb.ray_order()
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    E = torch.empty(pb.ext_shape, device="cuda")
+    d = torch.randn(pb.ext_shape, generator=torch.Generator(device="cpu").manual_seed(1)).cuda()
+    G = torch.empty(pb.ctrl_shape, device="cuda")
+    scratch = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    opts = {"id": api.make_options(), "ray_order": api.make_options(ray_order=order)}
+    calls = []
+    for name in ("id", "ray_order"):
+        calls.append(("forward", name, lambda o=opts[name]: api.fr_trace_forward(
+            h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS, o, E)))
+    for name in ("id", "ray_order"):
+        calls.append(("adjoint", name, lambda o=opts[name]: api.fr_trace_adjoint(
+            h, pb.lens, pb.source, pb.target, pb.n_rays, pb.seed, 0, api.ALL_RAYS, o, d, G)))
+    times = {}
+    for step_no in range(args.warmup + args.steps):
+        for kind, name, fn in calls:
+            scratch.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            if step_no >= args.warmup:
+                times.setdefault(kind, {}).setdefault(name, []).append(1e3 * a.elapsed_time(b))
+    out = {"workload": wl["name"], "rays": pb.n_rays, "ray_order_build_ms": build_ms,
+           "kernel_us": {k: {n: statistics.mean(v) for n, v in d_.items()} for k, d_ in times.items()}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     from paper_2302_12031_gb300 import dist as D
     rank, world, local = D.env()
-    if args.impl == "reference":
+    if args.point_kernels:
+        run_point_kernels(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local)
