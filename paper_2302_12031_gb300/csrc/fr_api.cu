@@ -282,8 +282,11 @@ void schedule_item(Item* it, int warps, const fr_options& o) {
 // CTAs per SM. The collimated forward takes 14 in float mode with filter sizes
 // 1 and 3 (12 with 5), 12 deterministic (8 with 5), the single-lens collimated
 // float adjoint with filter sizes 1 and 3 takes 10, every other variant 8.
-// (Collimated 2048^2 rays on GB300: forward 61.1 us with 12 warps, 59.1 us
-// with 14; adjoint 79.9 us with 8, 76.6 us with 10.)
+// kind: the source of a single lens with a flat entry face, -1 for a batch or
+// a two-face lens. (Collimated 2048^2 rays on GB300: forward 61.1 us with 12
+// warps, 59.1 us with 14; adjoint 79.9 us with 8, 76.6 us with 10. The
+// point-source adjoint at 10 warps spills and took 1040 us in the ray order
+// against 1005 us at 8.)
 int pick_warps(const fr_options& o, bool adjoint, int kind, bool det, int nu) {
   int cap = 8;
   if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = nu <= 3 ? (det ? 12 : 14) : (det ? 8 : 12);
@@ -393,8 +396,7 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   // (the kernel's launch bounds allow 640 threads there), 16 with 5; else pick_warps.
   const int win_cap = items[0].nu <= 3 ? 20 : 16;
   const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, win_cap) : win_cap)
-                           : pick_warps(o, adjoint,
-                                        items.size() == 1 && !items[0].two_face ? items[0].kind : FR_SOURCE_POINT,
+                           : pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind : -1,
                                         det, items[0].nu);
   // Workspace.
   size_t at = kHeaderBytes;

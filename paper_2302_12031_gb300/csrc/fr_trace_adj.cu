@@ -382,7 +382,7 @@ __device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, const LensS
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Launch bounds: two CTAs per SM of 320 threads for the single-lens collimated
-// float kernel with filter sizes 1 and 3 (95 registers, no spills), 256 else.
+// float kernel with filter sizes 1 and 3 (96 registers, no spills), 256 else.
 template <int CAP, bool DET, int NU, int KINDS>
 __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 320 : 256, 2)
     k_adjoint(const __grid_constant__ Launch<CAP> L) {
