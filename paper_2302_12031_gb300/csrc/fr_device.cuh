@@ -1229,7 +1229,8 @@ __device__ __forceinline__ void lane_range(const Item& it, int warps, uint64_t* 
 // additions per flush then go to different addresses, not to the same ones
 // from every lane). On the 16M-ray point source: forward 573 -> 451 us with
 // `near` (567 with `spread`), adjoint 1307 -> 1008 us with `spread` (1533 with
-// `near`).
+// `near`; 1445 with `near`, lockstep chunks and the 16 terms summed across
+// the warp by shuffles before one addition: the flushes were not the cost).
 constexpr uint64_t kOrderChunk = 16;
 
 struct OrderCursor {
