@@ -320,12 +320,24 @@ fr_status fr_trace_batch_adjoint(fr_handle* h, const fr_batch_item* items, int32
  *   mode 0: off (default); 1: on; 2: on, and the adjoint also builds its lens
  *   tables (reads ctrl_z) before it waits: only when the kernel right before
  *   the adjoint does not write the control heights (true for forward -> loss
- *   -> adjoint -> Adam steps). FR_ERR_INVALID_ARG for other modes. */
+ *   -> adjoint -> Adam steps); in mode 2 a float-mode forward with
+ *   accumulate = 1 also starts early: it builds its tables and, with a
+ *   shared-memory histogram, traces all its rays before it waits, so the
+ *   kernel right before it must write neither the control heights nor read or
+ *   write E except to clear it (true after fr_zero_list of E and dL/dP in a
+ *   step). FR_ERR_INVALID_ARG for other modes. */
 fr_status fr_set_programmatic_launch(fr_handle* h, int32_t mode);
 
 /* Zeroes `bytes` bytes of device memory at `ptr` on `stream` (a memset node
  * when captured): for clearing outputs that later calls accumulate into. */
 fr_status fr_zero(fr_handle* h, void* ptr, uint64_t bytes, void* stream);
+
+/* Zeroes n (0..80) device buffers, ptrs[k] of bytes[k] bytes (host arrays), in
+ * one kernel on `stream`: for clearing a step's outputs (E, dL/dP) before its
+ * traces accumulate into them. The kernel lets the next kernel begin launching
+ * at once (programmatic launch); a forward in mode 2 waits for it before its
+ * first write. */
+fr_status fr_zero_list(fr_handle* h, void* const* ptrs, const uint64_t* bytes, int32_t n, void* stream);
 
 /* A coherent order of the rays of a point source or grid of point sources
  * (the rays of Sec. 2.2.1). order_out (device, n_rays + 1 uint32) receives a

@@ -120,6 +120,7 @@ _SIGNATURES = {
     "fr_zero": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "fr_ray_order": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
                                C.c_void_p]),
+    "fr_zero_list": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint64), C.c_int32, C.c_void_p]),
     "fr_trace_forward_static": (C.c_int, [C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
                                           C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -287,6 +288,14 @@ def fr_set_programmatic_launch(h, mode):
 def fr_zero(h, t, stream=None):
     """Zero a device tensor with a memset on the stream."""
     h.check(lib().fr_zero(h.ptr, _ptr(t), t.numel() * t.element_size(), _stream(stream)))
+
+
+def fr_zero_list(h, tensors, stream=None):
+    """Zero several device tensors in one kernel."""
+    n = len(tensors)
+    ptrs = (C.c_void_p * max(n, 1))(*[t.data_ptr() for t in tensors])
+    sizes = (C.c_uint64 * max(n, 1))(*[t.numel() * t.element_size() for t in tensors])
+    h.check(lib().fr_zero_list(h.ptr, ptrs, sizes, n, _stream(stream)))
 
 
 def fr_ray_order(h, lens, source, n_rays, seed, order_out, stream=None):

@@ -490,7 +490,8 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     // Programmatic overlap only where the adjoint directly follows a kernel
     // (in deterministic mode it follows the max-|dL/dE| kernel: no overlap).
     cudaError_t e = adjoint ? fr::launch_adjoint<CAP>(L, grid, smem, det, st, h->pdl && !det)
-                            : fr::launch_forward<CAP>(L, grid, smem, det, st);
+                            : fr::launch_forward<CAP>(L, grid, smem, det, st,
+                                                      h->pdl && h->pdl_early && !det && o.accumulate);
     if (e != cudaSuccess) return cuda_error(h, e, adjoint ? "adjoint kernel" : "forward kernel");
     if (o.event_end)
       FR_CUDA(h, cudaEventRecordWithFlags((cudaEvent_t)o.event_end, st, rec_flags), "cudaEventRecord");
@@ -803,6 +804,24 @@ fr_status fr_set_programmatic_launch(fr_handle* h, int32_t enable) {
   return FR_OK;
 }
 
+fr_status fr_zero_list(fr_handle* h, void* const* ptrs, const uint64_t* bytes, int32_t n, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (n < 0 || n > fr::kMaxZero) return set_error(h, FR_ERR_INVALID_ARG, "n must be 0..%d", fr::kMaxZero);
+  if (n > 0 && (!ptrs || !bytes)) return set_error(h, FR_ERR_INVALID_ARG, "null list");
+  fr::ZeroList z;
+  std::memset(&z, 0, sizeof z);
+  for (int k = 0; k < n; ++k) {
+    if (!ptrs[k] && bytes[k]) return set_error(h, FR_ERR_INVALID_ARG, "buffer %d is null", k);
+    z.ptr[z.n] = ptrs[k];
+    z.bytes[z.n] = bytes[k];
+    ++z.n;
+  }
+  cudaError_t e = fr::launch_zero_list(z, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "zero kernel");
+  return FR_OK;
+}
+
 fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source, uint64_t n_rays,
                        uint64_t seed, uint32_t* order_out, void* stream) {
   if (!h) return FR_ERR_INVALID_ARG;
@@ -958,7 +977,7 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
     L.n_items = 1;
     L.warps = warps;
     L.items[0] = it;
-    e = fr::launch_forward<1>(L, it.cta_end, smem, det, st);
+    e = fr::launch_forward<1>(L, it.cta_end, smem, det, st, false);
     if (e != cudaSuccess) return cuda_error(nullptr, e, "forward kernel");
   }
   if (det) {

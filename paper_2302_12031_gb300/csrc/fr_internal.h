@@ -113,7 +113,15 @@ size_t adj_smem_bytes(const Item& it, bool det);
 
 // Launchers (return the CUDA error of the launch).
 template <int CAP>
-cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
+cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl);
+// Zeroes up to kMaxZero buffers (sizes in bytes) in one launch.
+constexpr int kMaxZero = 80;   // a batch's 64 grids and its dL/dP, with room
+struct ZeroList {
+  int n;
+  void* ptr[kMaxZero];
+  uint64_t bytes[kMaxZero];
+};
+cudaError_t launch_zero_list(const ZeroList& z, cudaStream_t st);
 template <int CAP>
 cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl);
 cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st);

@@ -47,7 +47,37 @@ __global__ void __launch_bounds__(1024) k_adam(float* __restrict__ P, float* __r
   if (threadIdx.x == 0) *step = t;
 }
 
+// Zeroes the buffers of a ZeroList: 16-byte stores where a buffer is aligned,
+// bytes at its unaligned ends. Lets the next kernel (a forward launched early)
+// begin at once; it waits for this one before it writes.
+__global__ void __launch_bounds__(256) k_zero_list(const __grid_constant__ ZeroList z) {
+  pdl_trigger();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int k = 0; k < z.n; ++k) {
+    unsigned char* p = static_cast<unsigned char*>(z.ptr[k]);
+    const uint64_t n = z.bytes[k];
+    const uint64_t lead = (uint64_t)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15);
+    const uint64_t head = lead < n ? lead : n;
+    const uint64_t nv = (n - head) / 16;
+    uint4* pv = reinterpret_cast<uint4*>(p + head);
+    for (uint64_t i = t0; i < nv; i += stride) pv[i] = make_uint4(0u, 0u, 0u, 0u);
+    const uint64_t tail0 = head + nv * 16;
+    for (uint64_t i = t0; i < head; i += stride) p[i] = 0;
+    for (uint64_t i = tail0 + t0; i < n; i += stride) p[i] = 0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_zero_list(const ZeroList& z, cudaStream_t st) {
+  uint64_t most = 0;
+  for (int k = 0; k < z.n; ++k) most = std::max<uint64_t>(most, z.bytes[k]);
+  if (most == 0) return cudaSuccess;
+  const uint64_t blocks = std::min<uint64_t>(152, (most / 16 + 255) / 256 + 1);
+  k_zero_list<<<(unsigned int)blocks, 256, 0, st>>>(z);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_absmax(const float* x, size_t n, float* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), st);

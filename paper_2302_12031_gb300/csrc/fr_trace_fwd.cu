@@ -324,9 +324,14 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? (DET ? 384 : 448) : (D
   cnt.on_screen = 0u;
   unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
   Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
+  // Launched early (programmatic launch, the previous kernel clears E): wait
+  // for it before the first write to global memory, which with a shared
+  // histogram is the final flush, else the first deposit.
+  if (!tg.smem) pdl_wait();
   run_lane<NU, DET, KINDS>(it, ls, li, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
   cnt.reduce_into(cnt_dst);
   ordered_misses_into(it, cnt_dst);
+  if (tg.smem) pdl_wait();
   if (tg.smem || tg.win) {
     // Touched window: warp reductions, then one shared atomic per warp.
     const int i0 = __reduce_min_sync(0xffffffffu, bb.imin), i1 = __reduce_max_sync(0xffffffffu, bb.imax);
@@ -476,14 +481,13 @@ FwdKernel<kMaxItems> pick_forward<kMaxItems>(bool det, int nu, int) {
 }
 
 template <int CAP>
-cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
+cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl) {
   const int threads = 32 * L.warps;
   const int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
-  pick_forward<CAP>(det, L.items[0].nu, kinds)<<<grid, threads, smem, st>>>(L);
-  return cudaGetLastError();
+  return launch_k(pick_forward<CAP>(det, L.items[0].nu, kinds), dim3(grid), dim3(threads), smem, st, pdl, L);
 }
-template cudaError_t launch_forward<1>(const Launch<1>&, int, size_t, bool, cudaStream_t);
-template cudaError_t launch_forward<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t);
+template cudaError_t launch_forward<1>(const Launch<1>&, int, size_t, bool, cudaStream_t, bool);
+template cudaError_t launch_forward<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t, bool);
 
 cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st) {
   const uint64_t n = it.ray_end - it.ray_begin;

@@ -148,9 +148,9 @@ class OptimStep:
         return o
 
     def _clear(self):
-        for E in self.E:
-            api.fr_zero(self.h, E)
-        api.fr_zero(self.h, self.g)
+        # one kernel for all of them; in programmatic-launch mode 2 the forward
+        # starts while it runs and waits for it before its first write
+        api.fr_zero_list(self.h, list(self.E) + [self.g])
 
     def _forward(self):
         if self.batched:
@@ -189,7 +189,8 @@ class OptimStep:
         if self.P_host is not None:
             self.P.copy_(self.P_host, non_blocking=True)
         self._clear()
-        # mode 2: the adjoint follows the loss kernel, which does not write the lens
+        # mode 2: the forward follows the clearing kernel and the adjoint the
+        # loss kernel, neither of which writes the lens
         api.fr_set_programmatic_launch(self.h, 2 if self.pdl else 0)
         try:
             self._forward()

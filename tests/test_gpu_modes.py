@@ -289,3 +289,18 @@ def test_lens_below_its_entry_face_is_counted_invalid():
     counts = stats.cpu().numpy()
     assert float(E.abs().sum()) == 0.0
     assert counts[5] > 0 and counts[0] == 0                # FR_RAY_INVALID
+
+
+def test_zero_list_clears_exactly_its_buffers():
+    h = api.default_handle()
+    big = torch.full((4096,), 7.0, device="cuda")
+    views = [big[1:2], big[3:70], big[101:1100], big[2000:2003], big[3000:3000]]   # 4-byte offsets, odd lengths, empty
+    api.fr_zero_list(h, views)
+    torch.cuda.synchronize()
+    want = torch.full((4096,), 7.0)
+    for a, b in ((1, 2), (3, 70), (101, 1100), (2000, 2003)):
+        want[a:b] = 0.0
+    assert torch.equal(big.cpu(), want)
+    api.fr_zero_list(h, [])
+    with pytest.raises(api.FreerayError):
+        api.fr_zero_list(h, [big] * 81)
