@@ -273,4 +273,4 @@ class OptimStep:
         det = bool(self.options is not None and self.options.deterministic)
         fwd = 1 + (n_items if det else 0)                 # trace (+ fixed->float)
         adj = 1 + (2 * n_items if det else 0)             # trace (+ absmax, fixed->float)
-        return fwd + n_items + adj + 1                    # + one loss per lens + Adam (memsets are not kernels)
+        return 1 + fwd + n_items + adj + 1                # clearing kernel + ... + one loss per lens + Adam
