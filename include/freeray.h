@@ -143,8 +143,8 @@ typedef struct fr_options {
   const uint32_t* ray_order; /* point sources, optional (device): the n_rays + 1 words written
                                by fr_ray_order, in whose order the forward, adjoint and
                                derivative-map traces take the rays; the sums are over the
-                               same rays. Only for calls over all rays of one lens with a
-                               flat entry face (FR_ERR_INVALID_ARG else); NULL: id order */
+                               same rays. Only for calls over all rays of one lens
+                               (FR_ERR_INVALID_ARG else); NULL: id order */
   int32_t window_cells;     /* hist_mode 3: at most this many cells in the window; 0 -> as
                                many as shared memory holds */
   int32_t reserved[3];
@@ -180,9 +180,8 @@ typedef struct fr_batch_item {
   const float* dLdE;     /* device: adjoint input, extended grid */
   float* dLdP;           /* device: adjoint output, (n1+1)*(n2+1) */
   fr_stats* stats;       /* device or NULL */
-  const uint32_t* ray_order; /* point source with a flat entry face, optional (device): this
-                               item's fr_ray_order output (as fr_options.ray_order for one
-                               lens); NULL: id order */
+  const uint32_t* ray_order; /* point source, optional (device): this item's fr_ray_order
+                               output (as fr_options.ray_order for one lens); NULL: id order */
 } fr_batch_item;
 
 typedef struct fr_handle fr_handle;
@@ -355,9 +354,10 @@ fr_status fr_zero_list(fr_handle* h, void* const* ptrs, const uint64_t* bytes, i
  * n_rays and seed only, not of the control heights, so one order serves every
  * optimisation step. Within a cell the order is the order of arrival (it may
  * differ from call to call); deterministic-mode results do not depend on it.
- * Needs n_rays < 2^32 and a flat entry face; uses the handle's workspace (4
- * bytes per cell); asynchronous on `stream`. FR_ERR_UNSUPPORTED for
- * collimated sources. */
+ * With a freeform entry face (entry_ctrl_z) the same key orders the rays but
+ * H = n_rays: the entry face decides the aperture in the trace. Needs n_rays
+ * < 2^32; uses the handle's workspace (4 bytes per cell); asynchronous on
+ * `stream`. FR_ERR_UNSUPPORTED for collimated sources. */
 fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source, uint64_t n_rays,
                        uint64_t seed, uint32_t* order_out, void* stream);
 

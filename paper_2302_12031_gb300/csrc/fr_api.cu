@@ -250,8 +250,8 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   if (o.hist_mode < 0 || o.hist_mode > 3 || o.window_cells < 0)
     return set_error(h, FR_ERR_INVALID_ARG, "hist_mode must be 0..3 and window_cells >= 0");
   if (o.ray_order) {
-    if (it->kind != FR_SOURCE_POINT || it->two_face)
-      return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to point sources and a flat entry face");
+    if (it->kind != FR_SOURCE_POINT)
+      return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to point sources");
     if (begin != 0 || it->ray_end != n_rays || n_rays > 0xffffffffull)
       return set_error(h, FR_ERR_INVALID_ARG, "ray_order needs a call over all rays (and n_rays < 2^32)");
     it->order = o.ray_order;
@@ -776,9 +776,8 @@ static fr_status batch(fr_handle* h, const fr_batch_item* in, int32_t n_items, c
     items[i].dLdP = in[i].dLdP;
     items[i].stats = in[i].stats;
     if (in[i].ray_order) {
-      if (items[i].kind != FR_SOURCE_POINT || items[i].two_face || in[i].n_rays > 0xffffffffull)
-        return set_error(h, FR_ERR_INVALID_ARG,
-                         "item %d: ray_order applies to point sources (n_rays < 2^32) with a flat entry face", i);
+      if (items[i].kind != FR_SOURCE_POINT || in[i].n_rays > 0xffffffffull)
+        return set_error(h, FR_ERR_INVALID_ARG, "item %d: ray_order applies to point sources (n_rays < 2^32)", i);
       items[i].order = in[i].ray_order;
     }
   }
@@ -843,7 +842,6 @@ fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_d
   Item it;
   fr_status s = make_item(h, lens, source, &t, n_rays, seed, 0, UINT64_MAX, o, &it);
   if (s != FR_OK) return s;
-  if (it.two_face) return set_error(h, FR_ERR_UNSUPPORTED, "ray orders need a flat entry face");
   const int G = fr::ray_order_grid(it);
   const uint64_t nk = fr::ray_order_keys(it, G);
   cudaStream_t st = as_stream(stream);

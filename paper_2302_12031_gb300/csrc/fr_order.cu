@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_order_count(const __grid_constant__ Ite
 // thread sums a contiguous chunk, the CTA scans the chunk sums, each thread
 // writes its chunk's prefixes. The prefix of the last key (the misses) is the
 // number of rays that meet the aperture: it goes to *hits.
-__global__ void __launch_bounds__(1024) k_order_scan(uint32_t* counts, uint64_t n, uint32_t* hits) {
+__global__ void __launch_bounds__(1024) k_order_scan(uint32_t* counts, uint64_t n, uint32_t* hits, uint32_t all) {
   __shared__ uint32_t s_warp[32];
   const uint64_t chunk = (n + blockDim.x - 1) / blockDim.x;
   const uint64_t lo = min(n, chunk * threadIdx.x), hi = min(n, lo + chunk);
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(1024) k_order_scan(uint32_t* counts, uint64_t 
   for (uint64_t i = lo; i < hi; ++i) {
     const uint32_t c = counts[i];
     counts[i] = run;
-    if (i == n - 1) *hits = run;
+    if (i == n - 1) *hits = all ? all : run;
     run += c;
   }
 }
@@ -120,7 +120,8 @@ cudaError_t launch_ray_order(const Item& it, int G, uint32_t* counts, uint32_t* 
   const unsigned int blocks = (unsigned int)(want < 4096 ? want : 4096);
   k_order_count<<<blocks, 256, 0, st>>>(it, G, counts);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_order_scan<<<1, 1024, 0, st>>>(counts, nk, order + it.n_rays);
+  // a freeform entry face decides the aperture in the trace: every position is traced
+  k_order_scan<<<1, 1024, 0, st>>>(counts, nk, order + it.n_rays, it.two_face ? (uint32_t)it.n_rays : 0u);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_order_scatter<<<blocks, 256, 0, st>>>(it, G, counts, order);
   return cudaGetLastError();

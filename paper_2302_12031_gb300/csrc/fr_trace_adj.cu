@@ -244,7 +244,20 @@ __device__ void run_adjoint_lane_two(const Item& it, const LensSmem& ls, const L
   const int nout = it.ncu * it.ncv;
   float* sgi_f = go.sg_f + nout;
   unsigned long long* sgi_q = go.sg_q + nout;
-  for (uint64_t id = a; id < b; ++id) {
+  // ray ids [a, b), or with a ray order chunks dealt far apart (OrderCursor)
+  OrderCursor oc;
+  if (it.order) oc.init(it, true);
+  uint64_t next_id = a;
+  for (;;) {
+    uint64_t id;
+    if (it.order) {
+      if (!oc.valid()) break;
+      id = __ldg(it.order + oc.p);
+      oc.advance();
+    } else {
+      if (next_id >= b) break;
+      id = next_id++;
+    }
     RayFwd r;
     RayIn e;
     const uint32_t row = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id / (uint64_t)it.cols) : 0u;

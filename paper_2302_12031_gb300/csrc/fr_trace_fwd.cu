@@ -187,7 +187,20 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
   acc.ie = -1;
   if constexpr ((KINDS & 4) != 0) {
     if (it.two_face) {
-      for (uint64_t id = a; id < b; ++id) {
+      // ray ids [a, b), or with a ray order chunks dealt to neighbouring lanes
+      OrderCursor oc;
+      if (it.order) oc.init(it, false);
+      uint64_t next_id = a;
+      for (;;) {
+        uint64_t id;
+        if (it.order) {
+          if (!oc.valid()) break;
+          id = __ldg(it.order + oc.p);
+          oc.advance();
+        } else {
+          if (next_id >= b) break;
+          id = next_id++;
+        }
         RayFwd r;
         RayIn e;
         const uint32_t row = it.kind == FR_SOURCE_COLLIMATED ? (uint32_t)(id / (uint64_t)it.cols) : 0u;

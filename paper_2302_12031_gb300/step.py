@@ -24,7 +24,7 @@ class OptimStep:
                  device="cuda", adj_options=None, loss="l2", reparam=None, pdl=True, ray_order=True):
         """`options` apply to both traces unless `adj_options` is given for the adjoint
         (e.g. to record timing events around each trace kernel separately).
-        ray_order: point-source lenses with a flat entry face trace their rays
+        ray_order: point-source lenses trace their rays
         in the coherent order of fr_ray_order (built once here: it does not
         depend on the heights)."""
         if isinstance(workloads, dict):
@@ -84,9 +84,9 @@ class OptimStep:
             self._init_reparam(workloads, sizes, device)
         self.n_rays = sum(pb.n_rays for pb in self.problems)
         self.batched = len(self.problems) > 1
-        # per lens: its ray order (point sources with a flat entry face) or None
-        self.orders = [pb.ray_order(self.h) if ray_order and pb.source.kind == api.FR_SOURCE_POINT
-                       and pb.entry_shape is None else None for pb in self.problems]
+        # per lens: its ray order (point sources) or None
+        self.orders = [pb.ray_order(self.h) if ray_order and pb.source.kind == api.FR_SOURCE_POINT else None
+                       for pb in self.problems]
         self.order = None if self.batched else self.orders[0]
         if self.order is not None:
             for o in (self._fwd_opts, self._adj_opts):

@@ -164,3 +164,25 @@ def test_batch_with_orders_and_windows():
         assert np.array_equal(a, b)
     for a, b in zip(gs["float"], gs["det"]):
         assert rel_l2(a, b) < 1e-5
+
+
+def test_two_face_point_lens_in_order():
+    # a freeform entry face: every position is traced (H = n_rays), the entry
+    # face decides the aperture; deterministic results equal the id order's
+    wl = W.with_entry_face(_wl(9 * 8000, (3, 3)), 8, 0.01, 5)
+    pb = api.Problem(wl)
+    full = pb.ray_order()
+    assert int(full[-1]) == wl["n_rays"]
+    assert np.array_equal(np.sort(full[:-1].cpu().numpy()), np.arange(wl["n_rays"]))
+    order = full
+    s0, s1 = api.new_stats(), api.new_stats()
+    E0 = pb.forward(_opts(wl, deterministic=True), stats=s0)
+    E1 = pb.forward(_opts(wl, order, deterministic=True), stats=s1)
+    assert torch.equal(E0, E1) and torch.equal(s0, s1)
+    d = torch.as_tensor(random_dLdE(wl, 7), dtype=torch.float32, device="cuda")
+    g0 = pb.adjoint(d, _opts(wl, deterministic=True))
+    g1 = pb.adjoint(d, _opts(wl, order, deterministic=True))
+    for a, b in zip(g0, g1):
+        assert torch.equal(a, b)
+    E2 = pb.forward(_opts(wl, order)).double().cpu().numpy()
+    assert rel_l2(E2, E0.double().cpu().numpy()) < 1e-5
