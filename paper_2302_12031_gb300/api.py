@@ -325,7 +325,9 @@ def fr_trace_forward_static(lens, source, target, n_rays, seed, ray_begin, ray_c
 def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newton_tol=0.0, warps_per_cta=0,
                  rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0), window_cells=0,
                  ray_order=None):
-    """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel."""
+    """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel;
+    `ray_order` = the tensor of Problem.ray_order() (the options keep its address: keep the
+    tensor alive while they are used); `window_cells` bounds the window of hist_mode 3."""
     o = Options()
     o.deterministic = int(deterministic)
     o.accumulate = int(accumulate)
