@@ -240,8 +240,10 @@ fr_status fr_trace_debug(fr_handle* h, const fr_lens_desc* lens, const fr_source
                          fr_ray_record* out, void* stream);
 
 /* Squared L2 loss over the interior pixels, L = sum (E - E_ref)^2, into
- * *loss_out (device double), and dL/dE = 2 (E - E_ref) on the interior and 0 on
- * ghost pixels into dLdE_out (device, extended grid). E is on the extended
+ * *loss_out (a double in device memory, or in pinned host memory, which the
+ * kernel writes through unified addressing: no copy needed to read it on the
+ * host after the stream completes), and dL/dE = 2 (E - E_ref) on the interior
+ * and 0 on ghost pixels into dLdE_out (device, extended grid). E is on the extended
  * grid, E_ref on the interior ny x nx grid. The sum is reduced in a fixed order
  * (bit-identical run to run). */
 fr_status fr_loss_l2(fr_handle* h, const float* E, const float* E_ref, int32_t nx, int32_t ny,
@@ -256,8 +258,9 @@ fr_status fr_adam_step(fr_handle* h, float* P, float* m, float* v, const float* 
 
 /* The paper's loss (Sec. 2.5, Eq. pipelineLoss): with the interior images
  * normalised to unit sum, I^ = E / sum(E) and I^_ref = E_ref / sum(E_ref),
- * L = ||I^ - I^_ref||_F / sqrt(nx ny) into *loss_out (device double), and dL/dE
- * through both normalisations into dLdE_out (device, extended grid; 0 on ghost
+ * L = ||I^ - I^_ref||_F / sqrt(nx ny) into *loss_out (device double or
+ * pinned host memory, as for fr_loss_l2), and dL/dE through both
+ * normalisations into dLdE_out (device, extended grid; 0 on ghost
  * pixels). E is on the extended grid, E_ref on the interior ny x nx grid.
  * Where ||I^ - I^_ref|| = 0 the gradient is 0. Where sum(E) <= 0 or
  * sum(E_ref) <= 0 the normalisation is undefined: *loss_out is NaN and the

@@ -99,11 +99,13 @@ class OptimStep:
     def attach_host_io(self, P_host=None, loss_host=None):
         """Make every step read its control heights from host memory and write
         its losses to host memory: P_host (n_params float32, pinned) is copied
-        into the device heights before the forward trace, the device losses into
-        loss_host (one float64 per lens, pinned) after the Adam update. Both
-        copies are part of the step (captured into its graph), so a caller that
-        feeds heights from the host and reads the loss back pays one graph launch
-        and one synchronisation per step. None detaches."""
+        into the device heights before the forward trace, and the loss kernels
+        write loss_host (one float64 per lens, pinned; pinned host memory is
+        addressable from the device) directly, in place of the device losses
+        (losses() then reads loss_host). Both transfers are part of the step
+        (captured into its graph), so a caller that feeds heights from the host
+        and reads the loss back pays one graph launch and one synchronisation
+        per step. None detaches."""
         if P_host is not None:
             if self.theta is not None:
                 raise ValueError("with a reparametrisation the heights follow theta; attach no P_host")
@@ -163,7 +165,9 @@ class OptimStep:
 
     def _loss(self):
         fn = api.fr_loss_l2 if self.loss_kind == "l2" else api.fr_loss_frobenius
-        for pb, E, Er, d, L in zip(self.problems, self.E, self.E_ref, self.dLdE, self.loss):
+        for k, (pb, E, Er, d) in enumerate(zip(self.problems, self.E, self.E_ref, self.dLdE)):
+            # with host I/O the loss kernel writes the pinned host buffer itself
+            L = self.loss[k] if self.loss_host is None else self.loss_host.view(-1)[k:k + 1]
             fn(self.h, E, Er, pb.nx, pb.ny, pb.nu_x, pb.nu_y, L, d)
 
     def _adjoint(self):
@@ -199,10 +203,6 @@ class OptimStep:
             self._adam()
         finally:
             api.fr_set_programmatic_launch(self.h, 0)
-        if self.loss_host is not None:
-            flat = self.loss_host.view(-1)
-            for k, L in enumerate(self.loss):
-                flat[k:k + 1].copy_(L.view(1), non_blocking=True)
 
     def _capture(self):
         state = self._state()
@@ -232,6 +232,9 @@ class OptimStep:
             self.eager_step()
 
     def losses(self):
+        if self.loss_host is not None:
+            torch.cuda.synchronize()
+            return self.loss_host.view(-1).clone()
         return torch.stack(self.loss).cpu()
 
     # Checkpoint and resume: the optimiser's whole state. Rays are functions of
