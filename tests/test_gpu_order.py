@@ -186,3 +186,18 @@ def test_two_face_point_lens_in_order():
         assert torch.equal(a, b)
     E2 = pb.forward(_opts(wl, order)).double().cpu().numpy()
     assert rel_l2(E2, E0.double().cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("nu", [1, 5])
+def test_order_with_other_filter_sizes(nu):
+    wl = _wl(9 * 10000, (3, 3))
+    wl["target"]["nu_x"] = wl["target"]["nu_y"] = nu
+    pb = api.Problem(wl)
+    order = pb.ray_order()
+    E0 = pb.forward(_opts(wl, deterministic=True))
+    E1 = pb.forward(_opts(wl, order, deterministic=True))
+    assert torch.equal(E0, E1)
+    d = torch.as_tensor(random_dLdE(wl, 3), dtype=torch.float32, device="cuda")
+    assert torch.equal(pb.adjoint(d, _opts(wl, deterministic=True)), pb.adjoint(d, _opts(wl, order, deterministic=True)))
+    E2 = pb.forward(_opts(wl, order)).double().cpu().numpy()
+    assert rel_l2(E2, E0.double().cpu().numpy()) < 1e-5

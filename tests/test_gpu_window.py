@@ -91,3 +91,16 @@ def test_invalid_histogram_options():
     for kw in (dict(hist_mode=4), dict(hist_mode=-1), dict(hist_mode=3, window_cells=-5)):
         with pytest.raises(api.FreerayError):
             pb.forward(api.make_options(**kw))
+
+
+def test_window_with_triangle_mesh_and_order():
+    wl = _wl(nx=37, ny=23, n_rays=30000)
+    wl["mesh"] = (2, 2)
+    pb = api.Problem(wl)
+    order = pb.ray_order()
+    kw = dict(mesh=(2, 2))
+    E_win = pb.forward(api.make_options(hist_mode=3, window_cells=300, ray_order=order, **kw)).double().cpu().numpy()
+    E_det = pb.forward(api.make_options(deterministic=True, **kw)).double().cpu().numpy()
+    assert rel_l2(E_win, E_det) < TOL_FORMS
+    E, E_or, _, _ = forward_both(wl, options=api.make_options(hist_mode=3, window_cells=300, ray_order=order, **kw))
+    assert rel_l2(E, E_or) < TOL_E
