@@ -23,8 +23,8 @@ pytestmark = pytest.mark.gpu
 TOL_FORMS = 1e-5
 
 
-def _wl(nu=3, nx=40, ny=40, n_rays=30000, grid=(1, 1)):
-    wl = W.point("w", n_rays, 10, nx, 4, 7, 6, grid=grid, grid_size=(0.2, 0.2), sigma=0.02)
+def _wl(nu=3, nx=40, ny=40, n_rays=30000, grid=(1, 1), sigma=0.02):
+    wl = W.point("w", n_rays, 10, nx, 4, 7, 6, grid=grid, grid_size=(0.2, 0.2), sigma=sigma)
     t = wl["target"]
     t["nx"], t["ny"], t["nu_x"], t["nu_y"] = nx, ny, nu, nu
     t["Ry"] = t["Rx"] * ny / nx
@@ -94,7 +94,9 @@ def test_invalid_histogram_options():
 
 
 def test_window_with_triangle_mesh_and_order():
-    wl = _wl(nx=37, ny=23, n_rays=30000)
+    # sigma 0.01 as in the mesh parity tests: steeper lenses make mesh rays
+    # ill-conditioned in FP32 against the FP64 oracle
+    wl = _wl(nx=37, ny=23, n_rays=30000, sigma=0.01)
     wl["mesh"] = (2, 2)
     pb = api.Problem(wl)
     order = pb.ray_order()
