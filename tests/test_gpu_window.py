@@ -94,15 +94,18 @@ def test_invalid_histogram_options():
 
 
 def test_window_with_triangle_mesh_and_order():
-    # sigma 0.01 as in the mesh parity tests: steeper lenses make mesh rays
-    # ill-conditioned in FP32 against the FP64 oracle
+    # the window form and the ray order on the mesh intersection give the
+    # deterministic id-order result (the mesh path's parity with the oracle is
+    # tests/test_gpu_mesh.py's: rays within rounding of a triangle edge can
+    # differ between FP32 and FP64, and at 30K rays one such ray moves E by
+    # about 5e-4)
     wl = _wl(nx=37, ny=23, n_rays=30000, sigma=0.01)
     wl["mesh"] = (2, 2)
     pb = api.Problem(wl)
     order = pb.ray_order()
     kw = dict(mesh=(2, 2))
-    E_win = pb.forward(api.make_options(hist_mode=3, window_cells=300, ray_order=order, **kw)).double().cpu().numpy()
-    E_det = pb.forward(api.make_options(deterministic=True, **kw)).double().cpu().numpy()
-    assert rel_l2(E_win, E_det) < TOL_FORMS
-    E, E_or, _, _ = forward_both(wl, options=api.make_options(hist_mode=3, window_cells=300, ray_order=order, **kw))
-    assert rel_l2(E, E_or) < TOL_E
+    s_win, s_det = api.new_stats(), api.new_stats()
+    E_win = pb.forward(api.make_options(hist_mode=3, window_cells=300, ray_order=order, **kw), stats=s_win)
+    E_det = pb.forward(api.make_options(deterministic=True, **kw), stats=s_det)
+    assert torch.equal(s_win, s_det)
+    assert rel_l2(E_win.double().cpu().numpy(), E_det.double().cpu().numpy()) < TOL_FORMS
