@@ -47,7 +47,8 @@
 extern "C" {
 #endif
 
-#define FR_ABI_VERSION 1
+/* Version 2: fr_options.ray_order and window_cells, fr_batch_item.ray_order. */
+#define FR_ABI_VERSION 2
 
 typedef enum fr_status {
   FR_OK = 0,

@@ -127,6 +127,7 @@ _SIGNATURES = {
 }
 
 _lib = None
+ABI_VERSION = 2   # FR_ABI_VERSION of include/freeray.h: the structures' layout
 
 
 def lib():
@@ -140,6 +141,9 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        if L.fr_abi_version() != ABI_VERSION:
+            raise ImportError("%s has ABI version %d, this binding expects %d: rebuild it"
+                              % (LIB_PATH, L.fr_abi_version(), ABI_VERSION))
         _lib = L
     return _lib
 
