@@ -72,3 +72,14 @@ def test_struct_layouts_match_the_c_compiler(tmp_path, freeray):
         assert int(out[cname]) == C.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert int(out["%s.%s" % (cname, field)]) == getattr(cls, field).offset, (cname, field)
+
+
+def test_options_marshalling_without_gpu(freeray):
+    import torch
+    o = freeray.make_options(hist_mode=3, window_cells=1234, mesh=(2, 3))
+    assert (o.hist_mode, o.window_cells, o.mesh_nu, o.mesh_nv) == (3, 1234, 2, 3)
+    assert not o.ray_order and not freeray.BatchItem().ray_order        # NULL: ray-id order
+    with pytest.raises(ValueError):
+        freeray.make_options(ray_order=torch.zeros(9, dtype=torch.int32))        # host memory
+    with pytest.raises(ValueError):
+        freeray.make_options(ray_order=torch.zeros(9, dtype=torch.int64))        # not 32-bit ids
