@@ -201,3 +201,20 @@ def test_order_with_other_filter_sizes(nu):
     assert torch.equal(pb.adjoint(d, _opts(wl, deterministic=True)), pb.adjoint(d, _opts(wl, order, deterministic=True)))
     E2 = pb.forward(_opts(wl, order)).double().cpu().numpy()
     assert rel_l2(E2, E0.double().cpu().numpy()) < 1e-5
+
+
+def test_full_size_point_workload_in_order():
+    # the 16M-ray point source as the optimisation step traces it (window form,
+    # ray order) against the deterministic id-order traces
+    wl = W.config(3)
+    pb = api.Problem(wl)
+    order = pb.ray_order()
+    s0, s1 = api.new_stats(), api.new_stats()
+    E_det = pb.forward(api.make_options(deterministic=True), stats=s0).double().cpu().numpy()
+    E_ord = pb.forward(api.make_options(ray_order=order), stats=s1).double().cpu().numpy()
+    assert torch.equal(s0, s1)
+    assert rel_l2(E_ord, E_det) < 1e-5
+    d = torch.as_tensor(random_dLdE(wl, 9), dtype=torch.float32, device="cuda")
+    g_det = pb.adjoint(d, api.make_options(deterministic=True)).double().cpu().numpy()
+    g_ord = pb.adjoint(d, api.make_options(ray_order=order)).double().cpu().numpy()
+    assert rel_l2(g_ord, g_det) < 1e-5
