@@ -313,6 +313,13 @@ def run_ours(args, rank, world, local):
                 "peak_note": "FP32 FMA peak %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock of %s peaks file)"
                              % (sm_count, pk.get("sm_max_mhz", 2070.0), pk_kind),
                 "kernel_ms": {"forward": fwd_k, "adjoint": adj_k},
+                # both trace kernels against the same peak (the forward-only and forward+adjoint
+                # paths each as a fraction of its binding roofline)
+                "per_kernel": {name: {"achieved": n_rays * fl / (ms * 1e-3) / 1e12,
+                                      "frac": n_rays * fl / (ms * 1e-3) / 1e12 / peak,
+                                      "flops_per_ray": fl, "traffic": PROFILED_DRAM_BYTES.get(name)}
+                               for name, fl, ms in (("forward", FLOPS_FWD_COLLIMATED, fwd_k),
+                                                    ("adjoint", FLOPS_ADJ_COLLIMATED, adj_k))},
                 "kernel_timing": "library events around each trace kernel in a second graph of the same step "
                                  "(%.1f us per step with those event nodes, %.1f us without), same timed loop"
                                  % (1e3 * statistics.mean(inst_step_ms), 1e3 * statistics.mean(step_ms))}
@@ -323,7 +330,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": wl["name"], "rays": n_rays, "control_net": "16x16", "bins": "128x128",
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (256 MiB write)",
-                       "step": "graph: prep+forward, loss, prep+adjoint, Adam",
+                       "step": "graph: clear, forward, loss, adjoint, Adam",
                        "schedule": {"forward": sched_f or "default", "adjoint": sched_a or "default"}},
             "forward_rays_per_s": fwd_value,
             "rays_by_cause": by_cause,
