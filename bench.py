@@ -44,6 +44,15 @@ FLOPS_ADJ_COLLIMATED = 290
 PROFILED_DRAM_BYTES = {"forward": 108544, "adjoint": 136192}
 
 
+# Per-ray work of each trace kernel on the cases of counting_cases(), from one
+# `ncu --metrics` capture of `python bench.py --counts` (profiles/trace_kernel_counts.md):
+#   warp: warp instructions issued; fp32: FP32 flops executed (FFMA 2, FADD and FMUL 1,
+#   their packed pairs twice that); xu: thread operations on the XU pipe (MUFU and
+#   conversions); satom: shared-memory atomic warp instructions. None where the kernels
+#   changed after that capture.
+COUNTS_PER_RAY = None
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -55,6 +64,9 @@ def parse():
     p.add_argument("--tune", action="store_true", help="autotune the trace kernels' schedule first")
     p.add_argument("--point-kernels", action="store_true",
                    help="time only the point-source trace kernels (16M rays), in id order and in the ray order")
+    p.add_argument("--counts", action="store_true",
+                   help="launch each trace kernel of the roofline table once on its counting case (run under "
+                        "ncu --metrics to take the per-ray instruction counts of COUNTS_PER_RAY)")
     return p.parse_args()
 
 
@@ -118,6 +130,53 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+PROBES = (  # fr_probe kinds: name, kind, iterations per thread
+    ("fp32_fma", 0, 4096), ("fp32_fma2", 1, 4096), ("xu_ex2", 2, 1024), ("xu_rsqrt", 3, 1024),
+    ("xu_cvt", 4, 1024), ("shared_atom_u32", 5, 256), ("shared_atom_f32", 6, 256), ("global_red_v4", 7, 64))
+
+
+def measure_ceilings(sm_count, repeats=5):
+    """Throughput of each fr_probe kernel (operations per second, best of `repeats` launches timed
+    by CUDA events on the launching stream): the measured ceilings of the trace kernels' roofline."""
+    import torch
+    from paper_2302_12031_gb300 import api
+    h = api.default_handle()
+    buf = torch.zeros(4 << 20, dtype=torch.float32, device="cuda")
+    blocks, threads = sm_count * 8, 256
+    out = {}
+    for name, kind, iters in PROBES:
+        best = 0.0
+        for _ in range(repeats + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ops = api.fr_probe(h, kind, blocks, threads, iters, buf)
+            b.record()
+            b.synchronize()
+            best = max(best, ops / (a.elapsed_time(b) * 1e-3))
+        out[name] = best
+    return out
+
+
+def kernel_roofline(counts, n_rays, ms, sm_count, mhz, ceil):
+    """Fractions of each ceiling one trace kernel reaches: per-ray counts x rays / kernel time
+    against the issue rate (4 warp instructions per SM per clock), the FP32 FMA rate (128 lanes x 2
+    flops per SM per clock), and the measured XU (MUFU ex2) and shared-atomic probe rates. The
+    binding ceiling is the one with the largest fraction: no schedule can run the kernel faster
+    than that resource allows."""
+    if counts is None:
+        return None
+    t = ms * 1e-3
+    issue_peak = sm_count * 4 * mhz * 1e6
+    fp32_peak = sm_count * 128 * 2 * mhz * 1e6
+    rows = {"issue": (counts["warp"] * n_rays / t, issue_peak, "warp inst/s"),
+            "fp32": (counts["fp32"] * n_rays / t, fp32_peak, "flop/s"),
+            "xu": (counts["xu"] * n_rays / t, ceil["xu_ex2"], "ops/s"),
+            "shared_atomics": (counts["satom"] * n_rays / t, ceil["shared_atom_u32"] / 32.0, "warp inst/s")}
+    out = {k: {"achieved": a, "peak": p, "unit": u, "frac": a / p} for k, (a, p, u) in rows.items()}
+    binding = max(out, key=lambda k: out[k]["frac"])
+    return {"binding": binding, "frac": out[binding]["frac"], "kernel_ms": ms, "ceilings": out}
 
 
 def time_steps(fn, steps, warmup, flush):
@@ -298,31 +357,46 @@ def run_ours(args, rank, world, local):
     st.attach_host_io(None, None)
     e2e_value, _ = D.replica_throughput(n_rays, statistics.mean(e2e_ms) * 1e-3, dev)
 
-    # --- roofline of the dominant kernel (the adjoint trace), timed live
+    # --- roofline of the trace kernels, timed live: every ceiling they share
+    # (issue slots, FP32, the XU pipe, shared-memory atomics) as a fraction of
+    # its peak (the FP32 and issue peaks from the clock, the XU and atomic peaks
+    # measured by the fr_probe kernels); the binding one is the largest
     pk, pk_kind = peaks()
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    ceil = measure_ceilings(sm_count)
     fwd_k = statistics.mean(fwd_kernel_ms)
     adj_k = statistics.mean(adj_kernel_ms)
     dominant = "adjoint" if adj_k >= fwd_k else "forward"
-    k_ms = max(adj_k, fwd_k)
-    flops = n_rays * (FLOPS_ADJ_COLLIMATED if dominant == "adjoint" else FLOPS_FWD_COLLIMATED)
-    achieved = flops / (k_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops(sm_count, pk.get("sm_max_mhz", 2070.0))
-    roofline = {"bound": "alu", "kernel": "k_%s (trace)" % dominant, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": PROFILED_DRAM_BYTES.get(dominant),
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
-                "peak_note": "FP32 FMA peak %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock of %s peaks file)"
-                             % (sm_count, pk.get("sm_max_mhz", 2070.0), pk_kind),
-                "kernel_ms": {"forward": fwd_k, "adjoint": adj_k},
-                # both trace kernels against the same peak (the forward-only and forward+adjoint
-                # paths each as a fraction of its binding roofline)
-                "per_kernel": {name: {"achieved": n_rays * fl / (ms * 1e-3) / 1e12,
-                                      "frac": n_rays * fl / (ms * 1e-3) / 1e12 / peak,
-                                      "flops_per_ray": fl, "traffic": PROFILED_DRAM_BYTES.get(name)}
-                               for name, fl, ms in (("forward", FLOPS_FWD_COLLIMATED, fwd_k),
-                                                    ("adjoint", FLOPS_ADJ_COLLIMATED, adj_k))},
-                "kernel_timing": "library events around each trace kernel in a second graph of the same step "
-                                 "(%.1f us per step with those event nodes, %.1f us without), same timed loop"
-                                 % (1e3 * statistics.mean(inst_step_ms), 1e3 * statistics.mean(step_ms))}
+    counts = COUNTS_PER_RAY.get("collimated_2048x2048") if COUNTS_PER_RAY else None
+    per_kernel = {}
+    for name, ms, fl in (("forward", fwd_k, FLOPS_FWD_COLLIMATED), ("adjoint", adj_k, FLOPS_ADJ_COLLIMATED)):
+        rl = kernel_roofline(counts[name] if counts else None, n_rays, ms, sm_count, mhz, ceil) or {"kernel_ms": ms}
+        alg = n_rays * fl / (ms * 1e-3) / 1e12
+        rl["fp32_algorithmic"] = {"flops_per_ray": fl, "achieved": alg,
+                                  "frac": alg / fp32_peak_tflops(sm_count, mhz), "unit": "TFLOP/s"}
+        rl["traffic"] = PROFILED_DRAM_BYTES.get(name)
+        per_kernel[name] = rl
+    dom = per_kernel[dominant]
+    if "ceilings" in dom:
+        c = dom["ceilings"][dom["binding"]]
+        roofline = {"bound": "alu", "binding": dom["binding"], "kernel": "k_%s (trace)" % dominant,
+                    "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"], "frac": c["frac"]}
+    else:
+        fa = dom["fp32_algorithmic"]
+        roofline = {"bound": "alu", "binding": "fp32", "kernel": "k_%s (trace)" % dominant, "achieved": fa["achieved"],
+                    "peak": fp32_peak_tflops(sm_count, mhz), "unit": "TFLOP/s", "frac": fa["frac"]}
+    roofline.update({
+        "traffic": PROFILED_DRAM_BYTES.get(dominant),
+        "traffic_unit": "bytes per launch (ncu dram__bytes_read+write)",
+        "peak_note": "issue: %d SMs x 4 warp instructions x %.0f MHz; FP32: %d SMs x 128 lanes x 2 flops x %.0f MHz "
+                     "(max SM clock of the %s peaks file); XU and shared atomics: fr_probe kernels, this run"
+                     % (sm_count, mhz, sm_count, mhz, pk_kind),
+        "counts_per_ray": "ncu instruction counts per ray (profiles/trace_kernel_counts.md)" if counts else None,
+        "probes": {k: v / 1e12 for k, v in ceil.items()}, "probe_unit": "T ops/s (FP32: TFLOP/s)",
+        "per_kernel": per_kernel,
+        "kernel_timing": "library events around each trace kernel in a second graph of the same step "
+                         "(%.1f us per step with those event nodes, %.1f us without), same timed loop"
+                         % (1e3 * statistics.mean(inst_step_ms), 1e3 * statistics.mean(step_ms))})
 
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -350,7 +424,7 @@ def run_ours(args, rank, world, local):
                                           "%.1f s" % (n_sample, dt)}
 
     if not args.no_extra:
-        line["extra"] = extra_workloads(args, flush, world)
+        line["extra"] = extra_workloads(args, flush, world, (sm_count, mhz, ceil))
 
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -359,8 +433,11 @@ def run_ours(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
-def extra_workloads(args, flush, world):
-    """Point source (16M rays) and the batched graph steps, fewer steps each."""
+def extra_workloads(args, flush, world, roof):
+    """Point source (16M rays) and the batched graph steps, fewer steps each; for the first
+    three, the trace kernels' durations (library events in a second graph of the same step),
+    forward-only rays/s from the forward kernel and each kernel's roofline (`roof`: SMs, clock,
+    measured ceilings)."""
     import torch
     from paper_2302_12031_gb300 import api, step
     from paper_2302_12031_gb300 import dist as D
@@ -386,6 +463,32 @@ def extra_workloads(args, flush, world):
         rays_per_s, t = D.replica_throughput(rays, statistics.mean(ms) * 1e-3)
         out[name] = {"rays_per_step": rays, "ms_per_step": 1e3 * t, "rays_per_s": rays_per_s,
                      "steps_per_s": 1.0 / t, "lenses": len(st.problems)}
+        del st
+        # the trace kernels of the same step, timed by library events in a second graph
+        ev_f = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev_a = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        for e in ev_f + ev_a:
+            e.record()
+        torch.cuda.synchronize()
+        st = step.OptimStep(wls, lr=1e-3, graph=True, options=api.make_options(events=ev_f),
+                            adj_options=api.make_options(events=ev_a))
+        f_ms, a_ms = [], []
+        for _ in range(k + 2):
+            flush()
+            st.step()
+            torch.cuda.synchronize()
+            f_ms.append(ev_f[0].elapsed_time(ev_f[1]))
+            a_ms.append(ev_a[0].elapsed_time(ev_a[1]))
+        f_k, a_k = statistics.mean(f_ms[2:]), statistics.mean(a_ms[2:])
+        case = COUNTED_AS.get(name)
+        counts = COUNTS_PER_RAY.get(case) if COUNTS_PER_RAY and case else None
+        sm_count, mhz, ceil = roof
+        out[name]["forward_kernel_ms"] = f_k
+        out[name]["adjoint_kernel_ms"] = a_k
+        out[name]["forward_rays_per_s"] = rays / (f_k * 1e-3)
+        out[name]["roofline"] = {
+            kind: kernel_roofline(counts[kind] if counts else None, rays, kms, sm_count, mhz, ceil) or {"kernel_ms": kms}
+            for kind, kms in (("forward", f_k), ("adjoint", a_k))}
         del st
         if order_ms is not None:
             st = step.OptimStep(wls, lr=1e-3, graph=True, ray_order=False)
@@ -504,11 +607,51 @@ def run_point_kernels(args):
     print(json.dumps(out), flush=True)
 
 
+# The counting case whose per-ray counts stand for each secondary workload.
+COUNTED_AS = {"point_16M": "point_4M", "grid_8x8_64M_batched_graph": "grid_8x8_4M",
+              "sweep_32_lenses_batched_graph": "sweep_32_lenses_scaled"}
+
+
+def counting_cases():
+    """The cases whose trace kernels the per-ray counts are taken on: the headline collimated
+    workload, and the point-source, grid-of-sources and sweep workloads with fewer rays (the
+    same lenses, screens and schedules; the counts are per ray). Each entry: (name, workloads,
+    ray-order flag)."""
+    from paper_2302_12031_gb300 import workloads as W
+    w3 = W.config(3)
+    w3["n_rays"] = 1 << 22
+    w4 = W.config(4)
+    w4["n_rays"] = 64 << 16
+    sweep = W.design_sweep(32, seed=6, min_rays=1 << 16, max_rays=1 << 20)
+    return [("collimated_2048x2048", [W.config(2)], False), ("point_4M", [w3], True),
+            ("grid_8x8_4M", [w4], True), ("sweep_32_lenses_scaled", sweep, True)]
+
+
+def run_counts(args):
+    """Each counting case: one forward and one adjoint launch of its step's trace kernels, in
+    the order of counting_cases()."""
+    import torch
+    from paper_2302_12031_gb300 import step
+    for name, wls, order in counting_cases():
+        st = step.OptimStep(wls, lr=1e-3, graph=False, ray_order=order)
+        torch.cuda.synchronize()
+        st._clear()
+        st._forward()
+        st._loss()
+        st._adjoint()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "rays": st.n_rays}), flush=True)
+        del st
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     from paper_2302_12031_gb300 import dist as D
     rank, world, local = D.env()
-    if args.point_kernels:
+    if args.counts:
+        run_counts(args)
+    elif args.point_kernels:
         run_point_kernels(args)
     elif args.impl == "reference":
         run_reference(args, rank, world)

@@ -70,7 +70,7 @@ enum {
   FR_RAY_TIR = 3,           /* total internal reflection at the freeform (culled, Sec. 2.2) */
   FR_RAY_OFF_SCREEN = 4,    /* missed the open interior screen |X|<R_x, |Y|<R_y */
   FR_RAY_INVALID = 5,       /* freeform below the entry face where the ray enters */
-  FR_RAY_NEWTON_FAIL = 6,   /* point source: Newton did not meet the tolerance */
+  FR_RAY_NEWTON_FAIL = 6,   /* point source: the intersection did not converge in its evaluations */
   FR_RAY_NCAUSES = 8
 };
 
@@ -124,7 +124,9 @@ typedef struct fr_options {
   int32_t deterministic;    /* 1: accumulate in int64 fixed point; results are bit-identical
                                from run to run and independent of the launch schedule */
   int32_t accumulate;       /* 1: add into E_out / dLdP_out instead of overwriting them */
-  int32_t newton_max_iter;  /* 0 -> 8 */
+  int32_t newton_max_iter;  /* 0 -> 8: Newton iterations on the bracket that isolates the
+                               smallest root (Sec. 2.2.1; the certified march that finds the
+                               bracket takes at most 32 evaluations more) */
   float newton_tol;         /* 0 -> 1e-6, absolute, on the ray parameter */
   int32_t warps_per_cta;    /* 0 -> tuned; 1..32 */
   int32_t rays_per_lane;    /* 0 -> tuned; 1..64 */
@@ -160,7 +162,7 @@ typedef struct fr_stats {
 typedef struct fr_ray_record {
   int32_t status;        /* FR_RAY_* */
   int32_t span_i, span_j;/* knot span index of the freeform hit (u_i0 <= u < u_i0+1) */
-  int32_t newton_iters;  /* point source: Newton iterations used */
+  int32_t newton_iters;  /* point source: Newton iterations used on the isolating bracket */
   float u, v;            /* freeform hit, parameter space */
   float x, y, z;         /* freeform hit */
   float dx, dy, dz;      /* direction inside the glass */
@@ -192,7 +194,9 @@ fr_status fr_create(fr_handle** out);
 fr_status fr_destroy(fr_handle* h);
 
 /* Message of the last failure on this handle ("" if none). Valid until the next
- * call. With h == NULL: the last failure of fr_create on this host thread. */
+ * call. With h == NULL: the last failure on this host thread of a call made
+ * without a handle (fr_create, fr_trace_forward_static; the latter clears it
+ * when it starts, so after a successful call it is ""). */
 const char* fr_last_error(const fr_handle* h);
 
 /* ABI version (FR_ABI_VERSION) of the loaded library. */
@@ -369,6 +373,24 @@ fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_d
  * Returns FR_ERR_TIMEOUT if the work has not finished by then. */
 fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms);
 
+/* Throughput probe: a measurement aid for the roofline of the trace kernels,
+ * not an operation of the paper. Launches `blocks` x `threads` threads
+ * (threads a multiple of 32, at most 1024) of one probe kernel on `stream`,
+ * each doing `iters` rounds of independent operations of one kind:
+ *   0 FP32 FMA, 1 packed FP32 FMA pairs (fma.rn.f32x2): *ops_out = flops (FMA = 2);
+ *   2 ex2.approx, 3 rsqrt.approx, 4 float -> int -> float conversions:
+ *     *ops_out = thread operations on the XU pipe;
+ *   5 u32, 6 f32 shared-memory atomic adds at random addresses of a 64 KB
+ *     table: *ops_out = atomic thread operations;
+ *   7 16-byte float4 reductions (red.global.add.v4.f32) at random addresses
+ *     of buf: *ops_out = reductions.
+ * buf (device, n_buf >= 4 floats, caller-owned; for kind 7 n_buf is 4 times
+ * a power of two) receives per-thread results (kinds 0-6) or the reductions.
+ * *ops_out (host) is written before the launch; the caller times the launch
+ * (CUDA events on `stream`) and divides. */
+fr_status fr_probe(fr_handle* h, int32_t kind, int32_t blocks, int32_t threads, int32_t iters, float* buf,
+                   int32_t n_buf, double* ops_out, void* stream);
+
 /* Forward trace that allocates nothing (the paper has no counterpart; this is
  * an interface for callers that cannot allocate device memory: code running in
  * a host process whose device memory is owned by another allocator or budget,
@@ -376,10 +398,15 @@ fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms);
  * and plug-ins that may only use the buffers they are handed).
  * Same arguments and results as fr_trace_forward, without a handle: the
  * caller passes the lens, source, screen and the output E_out (and stats_out);
- * the scratch memory this trace needs (the int64 accumulator of deterministic
- * mode) lives in one static device array of 1 MiB that every GPU loading the
- * library holds until the process exits. No cudaMalloc, cudaFree or other
- * allocating call is made.
+ * the scratch memory this trace needs (the int64 accumulator of the
+ * fixed-point kernel) lives in one static device array of 1 MiB that every GPU
+ * loading the library holds until the process exits. No cudaMalloc, cudaFree
+ * or other allocating call is made. The kernel, its schedule and so its
+ * results are those of fr_trace_forward for every lens it takes (flat or
+ * freeform entry face, any source), with one exception: a float-mode problem
+ * whose grid fits neither in shared memory nor in the array as fixed point
+ * (more than 122,000 extended cells, not a point source) deposits with float
+ * atomics in global memory, the same sums in another rounding order.
  *  - Limits: control nets up to 32x32 (as fr_trace_forward); in deterministic
  *    mode the extended grid (nx+nu_x-1)*(ny+nu_y-1) may have at most 122,000
  *    cells. Larger problems are rejected with FR_ERR_WORKSPACE and a message.

@@ -121,6 +121,8 @@ _SIGNATURES = {
     "fr_ray_order": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p,
                                C.c_void_p]),
     "fr_zero_list": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint64), C.c_int32, C.c_void_p]),
+    "fr_probe": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
+                           C.POINTER(C.c_double), C.c_void_p]),
     "fr_trace_forward_static": (C.c_int, [C.POINTER(LensDesc), C.POINTER(SourceDesc), C.POINTER(TargetDesc),
                                           C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(Options),
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -315,6 +317,14 @@ def fr_stream_wait(h, timeout_ms, stream=None):
     h.check(lib().fr_stream_wait(h.ptr, _stream(stream), timeout_ms))
 
 
+def fr_probe(h, kind, blocks, threads, iters, buf, stream=None):
+    """Launch throughput probe `kind` (see the header); returns its operation count."""
+    ops = C.c_double()
+    h.check(lib().fr_probe(h.ptr, kind, blocks, threads, iters, _ptr(buf), buf.numel(), C.byref(ops),
+                           _stream(stream)))
+    return ops.value
+
+
 def fr_trace_forward_static(lens, source, target, n_rays, seed, ray_begin, ray_count, options, E_out,
                             stats_out=None, stream=None):
     """fr_trace_forward without a handle and without any allocation (see the header)."""
@@ -330,8 +340,9 @@ def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newto
                  rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0), window_cells=0,
                  ray_order=None):
     """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel;
-    `ray_order` = the tensor of Problem.ray_order() (the options keep its address: keep the
-    tensor alive while they are used); `window_cells` bounds the window of hist_mode 3."""
+    `ray_order` = the tensor of Problem.ray_order() (the options hold a reference to it;
+    copies of the structure made by ctypes do not); `window_cells` bounds the window of
+    hist_mode 3."""
     o = Options()
     o.deterministic = int(deterministic)
     o.accumulate = int(accumulate)
@@ -347,6 +358,8 @@ def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newto
         if ray_order.dtype != torch.int32 or not ray_order.is_cuda or not ray_order.is_contiguous():
             raise ValueError("ray_order must be a contiguous int32 CUDA tensor (uint32 ids)")
         o.ray_order = ray_order.data_ptr()
+        o.ray_order_numel = ray_order.numel()   # checked against the problem by Problem's calls
+        o.ray_order_tensor = ray_order          # the options keep the order alive while they live
     if events is not None:
         o.event_begin = events[0].cuda_event
         o.event_end = events[1].cuda_event
@@ -401,6 +414,15 @@ class Problem:
         self.nx, self.ny, self.nu_x, self.nu_y = tgt["nx"], tgt["ny"], tgt["nu_x"], tgt["nu_y"]
         self.device = self.ctrl_z.device
 
+    def check_options(self, options):
+        """Refuses options whose ray order (make_options(ray_order=...)) was built for another
+        number of rays: the kernels read n_rays + 1 words of it."""
+        if options is not None and options.ray_order:
+            n = getattr(options, "ray_order_numel", None)
+            if n != self.n_rays + 1:
+                raise ValueError("ray_order has %s elements, this problem needs n_rays + 1 = %d"
+                                 % (n, self.n_rays + 1))
+
     def set_ctrl(self, ctrl_z):
         """Point the lens descriptor at another control-height tensor."""
         self.ctrl_z = ctrl_z.contiguous()
@@ -425,6 +447,7 @@ class Problem:
         h = h or default_handle()
         if E is None:
             E = torch.empty(self.ext_shape, dtype=torch.float32, device=self.device)
+        self.check_options(options)
         fr_trace_forward(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                          options, E, stats)
         return E
@@ -446,6 +469,7 @@ class Problem:
         if dLdP is None:
             shape = self.ctrl_shape if self.entry_shape is None else (self.n_params(),)
             dLdP = torch.empty(shape, dtype=torch.float32, device=self.device)
+        self.check_options(options)
         fr_trace_adjoint(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                          options, dLdE.contiguous(), dLdP, stats)
         if self.entry_shape is None:
@@ -463,6 +487,7 @@ class Problem:
         n_dirs = 1 if single else dP.shape[0]
         if dE is None:
             dE = torch.empty((n_dirs,) + self.ext_shape, dtype=torch.float32, device=self.device)
+        self.check_options(options)
         fr_trace_tangent(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                          options, dP, n_dirs, dE, stats)
         return dE[0] if single else dE
@@ -473,6 +498,7 @@ class Problem:
         if ray_count is None:
             ray_count = self.n_rays - ray_begin
         raw = torch.empty((max(1, ray_count), C.sizeof(RayRecord)), dtype=torch.uint8, device=self.device)
+        self.check_options(options)
         fr_trace_debug(h, self.lens, self.source, self.target, self.n_rays, self.seed, ray_begin, ray_count,
                        options, raw)
         return records_to_numpy(raw[:ray_count].cpu().numpy())

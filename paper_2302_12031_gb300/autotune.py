@@ -33,11 +33,11 @@ def candidates(kind, source_kind):
     """Schedules worth trying; the first is the library default."""
     out = [dict(warps_per_cta=0, rays_per_lane=0, ctas_per_sm=0, hist_mode=0)]
     # warps per CTA within each kernel's launch bounds (larger requests are capped): the
-    # collimated forward takes up to 14, the collimated adjoint 10, the point-source
+    # collimated forward takes up to 12, the collimated adjoint 10, the point-source
     # forward's window form 20 (one CTA per SM), other variants 8
     collimated = source_kind == api.FR_SOURCE_COLLIMATED
     if kind == "forward":
-        warps = (8, 12, 14) if collimated else (8, 16, 20)
+        warps = (8, 10, 12) if collimated else (8, 16, 20)
     else:
         warps = (8, 10) if collimated else (4, 8)
     for w in warps:

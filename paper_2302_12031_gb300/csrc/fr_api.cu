@@ -189,6 +189,11 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
       return set_error(h, FR_ERR_INVALID_ARG, "collimated grid side above 2^24");
     it->cols = S->cols;
     it->rows = S->rows;
+    const uint64_t c = (uint64_t)S->cols, lo = begin, hi = begin + count;
+    it->row_lo = (uint32_t)(lo / c);
+    it->row_hi = hi > lo ? (uint32_t)((hi - 1) / c + 1) : it->row_lo;
+    it->col_lo = (uint32_t)(lo - (uint64_t)it->row_lo * c);
+    it->col_hi = hi > lo ? (uint32_t)(hi - (uint64_t)(it->row_hi - 1) * c) : 0u;
     it->jitter = S->jitter ? 1 : 0;
     it->gnx = it->gny = 1;
   } else if (S->kind == FR_SOURCE_POINT) {
@@ -279,24 +284,24 @@ void schedule_item(Item* it, int warps, const fr_options& o) {
 }
 
 // Warps per CTA: the most the trace kernels' launch bounds allow with two
-// CTAs per SM. The collimated forward takes 14 in float mode with filter sizes
-// 1 and 3 (12 with 5), 12 deterministic (8 with 5), the single-lens collimated
-// float adjoint with filter sizes 1 and 3 takes 10, every other variant 8.
+// CTAs per SM. The collimated forward takes 12 (8 deterministic with filter
+// size 5), the single-lens collimated float adjoint with filter sizes 1 and 3
+// takes 10, every other variant 8.
 // kind: the source of a single lens with a flat entry face, -1 for a batch or
-// a two-face lens. (Collimated 2048^2 rays on GB300: forward 61.1 us with 12
-// warps, 59.1 us with 14; adjoint 79.9 us with 8, 76.6 us with 10. The
-// point-source adjoint at 10 warps spills and took 1040 us in the ray order
-// against 1005 us at 8.)
+// a two-face lens. (Collimated 2048^2 rays on GB300, before the column
+// lockstep: forward 61.1 us with 12 warps, 59.1 us with 14; adjoint 79.9 us
+// with 8, 76.6 us with 10. The point-source adjoint at 10 warps spills and
+// took 1040 us in the ray order against 1005 us at 8.)
 int pick_warps(const fr_options& o, bool adjoint, int kind, bool det, int nu) {
   int cap = 8;
-  if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = nu <= 3 ? (det ? 12 : 14) : (det ? 8 : 12);
+  if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = nu <= 3 ? 12 : (det ? 8 : 12);
   else if (adjoint && kind == FR_SOURCE_COLLIMATED && !det && nu <= 3) cap = 10;
   return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, cap) : cap;
 }
 
 bool want_smem_hist(const Item& it, const fr_options& o, bool det) {
   const size_t hist = (size_t)it.ncol * it.nrow * (det ? 8 : 4);
-  const size_t tables = (size_t)(it.nsu * it.nsv + it.nsu + it.nsv) * 4 * sizeof(float4);
+  const size_t tables = fr::lens_tables_bytes(it);
   if (hist + tables > 200 * 1024) return false;
   if (o.hist_mode == 1) return false;
   if (o.hist_mode == 2) return true;
@@ -854,6 +859,22 @@ fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_d
   return FR_OK;
 }
 
+fr_status fr_probe(fr_handle* h, int32_t kind, int32_t blocks, int32_t threads, int32_t iters, float* buf,
+                   int32_t n_buf, double* ops_out, void* stream) {
+  if (!h) return FR_ERR_INVALID_ARG;
+  h->err.clear();
+  if (kind < 0 || kind > 7) return set_error(h, FR_ERR_INVALID_ARG, "probe kind must be 0..7");
+  if (blocks < 1 || blocks > (1 << 20) || threads < 32 || threads > 1024 || threads % 32 != 0 || iters < 1)
+    return set_error(h, FR_ERR_INVALID_ARG, "probe launch: 1..2^20 blocks of 32..1024 threads (multiple of 32)");
+  if (!buf || !ops_out || n_buf < 4) return set_error(h, FR_ERR_INVALID_ARG, "probe buffer of >= 4 floats needed");
+  if (kind == 7 && ((n_buf & 3) != 0 || ((n_buf / 4) & (n_buf / 4 - 1)) != 0))
+    return set_error(h, FR_ERR_INVALID_ARG, "reduction probe: n_buf must be 4 times a power of two");
+  *ops_out = fr::probe_ops(kind, blocks, threads, iters);
+  cudaError_t e = fr::launch_probe(kind, blocks, threads, iters, buf, n_buf, as_stream(stream));
+  if (e != cudaSuccess) return cuda_error(h, e, "probe kernel");
+  return FR_OK;
+}
+
 fr_status fr_zero(fr_handle* h, void* ptr, uint64_t bytes, void* stream) {
   if (!h) return FR_ERR_INVALID_ARG;
   h->err.clear();
@@ -884,6 +905,9 @@ fr_status fr_stream_wait(fr_handle* h, void* stream, int32_t timeout_ms) {
 namespace {
 
 constexpr size_t kStaticScratchBytes = 1u << 20;
+// Cells of the largest extended grid whose int64 accumulator the array holds
+// (8 bytes a cell, with room for the alignment of the plan).
+constexpr int kStaticMaxFixCells = 122000;
 constexpr int kStaticMaxDevices = 64;
 
 // The scratch of fr_trace_forward_static. In host code this name is only a
@@ -931,6 +955,8 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
                                              const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
                                              uint64_t ray_begin, uint64_t ray_count, const fr_options* options,
                                              float* E_out, fr_stats* stats_out, void* stream) {
+  NvtxRange nvtx_range("fr_trace_forward_static");
+  g_err.clear();
   const fr_options o = defaults(options);
   if (!E_out) return set_error(nullptr, FR_ERR_INVALID_ARG, "E_out is null");
   Item it;
@@ -940,33 +966,40 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
   StaticDevice* dev = nullptr;
   s = static_setup(&dev);
   if (s != FR_OK) return s;
-  const bool det = o.deterministic != 0;
-  if (det && it.ncol * it.nrow > 122000)
+  const int cells = it.ncol * it.nrow;
+  bool det = o.deterministic != 0;
+  if (det && cells > kStaticMaxFixCells)
     return set_error(nullptr, FR_ERR_WORKSPACE,
-                     "deterministic mode: the extended grid has %d cells, the static scratch holds at most 122000",
-                     it.ncol * it.nrow);
+                     "deterministic mode: the extended grid has %d cells, the static scratch holds at most %d",
+                     cells, kStaticMaxFixCells);
+  // The schedule of fr_trace_forward (run_trace): a point-source grid that
+  // does not fit in shared memory takes the window form; any other such grid
+  // the fixed-point kernel, here while its accumulator fits the static array
+  // (beyond that, float atomics: the same sums in another rounding order).
+  const bool window = plan_window(&it, o, dev->smem_optin);
+  if (!det && !window && !want_smem_hist(it, o, false) && cells <= kStaticMaxFixCells) det = true;
   const ItemWs w = plan(it, 0, det, false);
   if (w.end > kStaticScratchBytes)
-    return set_error(nullptr, FR_ERR_WORKSPACE,
-                     "the problem needs %zu bytes of scratch, more than the %zu of the static array (in "
-                     "deterministic mode the extended grid may have at most 122000 cells; it has %d)",
-                     w.end, kStaticScratchBytes, it.ncol * it.nrow);
+    return set_error(nullptr, FR_ERR_WORKSPACE, "the problem needs %zu bytes of scratch, more than the %zu of the "
+                     "static array", w.end, kStaticScratchBytes);
   cudaStream_t st = as_stream(stream);
   unsigned char* base = dev->scratch;
   it.Efix = reinterpret_cast<unsigned long long*>(base + w.efix);
   it.E = E_out;
   it.stats = stats_out;
-  const int warps = pick_warps(o, false, it.kind, det, it.nu);
+  const int win_cap = it.nu <= 3 ? 20 : 16;
+  const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, win_cap) : win_cap)
+                           : pick_warps(o, false, it.two_face ? -1 : it.kind, det, it.nu);
   schedule_item(&it, warps, o);
-  it.smem_hist = want_smem_hist(it, o, det) ? 1 : 0;
+  it.smem_hist = window ? 2 : (want_smem_hist(it, o, det) ? 1 : 0);
   const size_t smem = fr::fwd_smem_bytes(it, det);
   cudaError_t e = cudaSuccess;
-  if (det) e = cudaMemsetAsync(it.Efix, 0, (size_t)it.ncol * it.nrow * 8, st);
-  else if (!o.accumulate) e = cudaMemsetAsync(it.E, 0, (size_t)it.ncol * it.nrow * 4, st);
+  if (det) e = cudaMemsetAsync(it.Efix, 0, (size_t)cells * 8, st);
+  else if (!o.accumulate) e = cudaMemsetAsync(it.E, 0, (size_t)cells * 4, st);
   if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaMemsetAsync");
   if (it.max_ctas > 0) {
-    const int occ = fr::forward_occupancy(warps * 32, smem, det, false, it.nu,
-                                          it.kind == FR_SOURCE_COLLIMATED ? 1 : 2);
+    const int kinds = it.two_face ? 4 : (it.kind == FR_SOURCE_COLLIMATED ? 1 : 2);
+    const int occ = fr::forward_occupancy(warps * 32, smem, det, false, it.nu, kinds);
     if (occ <= 0 || smem + 1024 > (size_t)dev->smem_optin)
       return set_error(nullptr, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
     const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
@@ -981,9 +1014,8 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
     if (e != cudaSuccess) return cuda_error(nullptr, e, "forward kernel");
   }
   if (det) {
-    e = fr::launch_fix_to_float(it.Efix, it.E, (size_t)it.ncol * it.nrow, 1.0f / it.fixE, o.accumulate, st);
+    e = fr::launch_fix_to_float(it.Efix, it.E, (size_t)cells, 1.0f / it.fixE, o.accumulate, st);
     if (e != cudaSuccess) return cuda_error(nullptr, e, "fixed-point conversion");
   }
   return FR_OK;
 }
-

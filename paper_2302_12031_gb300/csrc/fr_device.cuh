@@ -47,7 +47,8 @@ __device__ __forceinline__ float unit23(uint32_t w) {
 }
 
 // PTX approximate instructions (single MUFU operations): 2^x with a relative
-// error below 2^-22, 1/x within 1 ulp. Both flush denormals to zero.
+// error below 2^-22, 1/x within 1 ulp, sqrt below 2^-23 relative. All flush
+// denormals to zero.
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -56,6 +57,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __device__ __forceinline__ float fast_rcp(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// Square root with a relative error below 2^-23 (one MUFU operation).
+__device__ __forceinline__ float fast_sqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -123,6 +130,8 @@ struct LensSmem {
   float4* bv;      // [nsv][4]
   int* zkey;       // [2]: min and max control height (convex hull, Sec. 2.1.2) as
                    // order-preserving integer keys (point sources only; see zbounds)
+  float4* hull;    // [nsu*nsv] (nets that rays must intersect): per patch (zmin, zmax, Bs, Bt),
+                   // see patch_hull
 };
 
 // Float <-> int key with the same order (for shared-memory atomicMin/Max).
@@ -139,24 +148,80 @@ __device__ __forceinline__ void zbounds(const LensSmem& s, float* zmin, float* z
   *zmax = key_float(s.zkey[1]);
 }
 
-__host__ __device__ inline size_t lens_smem_bytes(int nsu, int nsv) {
-  return (size_t)(nsu * nsv + nsu + nsv) * 4 * sizeof(float4) + 16;
+// Bytes of one net's tables; `hull`: with the per-patch bounds of the
+// intersection (nets that rays must intersect: the exit net of a point source,
+// both nets of a two-face lens).
+__host__ __device__ inline size_t lens_smem_bytes(int nsu, int nsv, bool hull) {
+  return (size_t)(nsu * nsv * (hull ? 5 : 4) + (nsu + nsv) * 4) * sizeof(float4) + 16;
 }
+
+// Whether an item's nets carry the intersection bounds.
+__host__ __device__ inline bool needs_hull(const Item& it) { return it.kind == FR_SOURCE_POINT || it.two_face; }
 
 // Bytes of all lens tables of an item (the exit net's, then the entry net's).
 __host__ __device__ inline size_t tables_bytes(const Item& it) {
-  size_t b = (lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15;
-  if (it.two_face) b += (lens_smem_bytes(it.nsu_in, it.nsv_in) + 15) & ~(size_t)15;
+  const bool h = needs_hull(it);
+  size_t b = (lens_smem_bytes(it.nsu, it.nsv, h) + 15) & ~(size_t)15;
+  if (it.two_face) b += (lens_smem_bytes(it.nsu_in, it.nsv_in, h) + 15) & ~(size_t)15;
   return b;
 }
 
-__device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv) {
+__device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv, bool hull) {
   LensSmem s;
   s.patch = reinterpret_cast<float4*>(base);
   s.bu = s.patch + nsu * nsv * 4;
   s.bv = s.bu + nsu * 4;
   s.zkey = reinterpret_cast<int*>(s.bv + nsv * 4);
+  s.hull = hull ? s.bv + nsv * 4 + 1 : nullptr;   // after the 16 bytes of zkey
   return s;
+}
+
+// Bounds of one bicubic patch for the intersection, from its own control net
+// in the Bernstein (Bezier) basis, b_ij, obtained from the power form C[e][f]:
+// along each direction b_i = sum_{e <= i} binom(i,e)/binom(3,e) c_e. By the
+// convex-hull property of the Bernstein basis (the patch form of Sec. 2.1.2's
+// argument) Z lies in [min b, max b] on the patch, and its second derivatives in
+// patch coordinates are bounded by the hull of the differenced net:
+//   |Z_ss| <= 6 max |b_{i+2,j} - 2 b_{i+1,j} + b_ij|, |Z_tt| likewise,
+//   |Z_st| <= 9 max |b_{i+1,j+1} - b_{i+1,j} - b_{i,j+1} + b_ij|.
+// Along a line (s, t) = (s0 + a tau, t0 + b tau) this gives
+//   |d2Z/dtau2| <= Z_ss a^2 + 2 |Z_st| |a b| + Z_tt b^2 <= Bs a^2 + Bt b^2,
+// Bs = Mss + Mst, Bt = Mtt + Mst (2|ab| <= a^2 + b^2). The bounds are widened
+// a little for FP32 rounding. Returns (zmin, zmax, Bs, Bt).
+__device__ inline float4 patch_hull(const float (&C)[4][4]) {
+  float T[4][4], B[4][4];
+  const float third = 1.0f / 3.0f;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {   // along s
+    T[0][f] = C[0][f];
+    T[1][f] = fmaf(third, C[1][f], C[0][f]);
+    T[2][f] = fmaf(third, C[2][f], fmaf(2.0f * third, C[1][f], C[0][f]));
+    T[3][f] = C[0][f] + C[1][f] + C[2][f] + C[3][f];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {   // along t
+    B[i][0] = T[i][0];
+    B[i][1] = fmaf(third, T[i][1], T[i][0]);
+    B[i][2] = fmaf(third, T[i][2], fmaf(2.0f * third, T[i][1], T[i][0]));
+    B[i][3] = T[i][0] + T[i][1] + T[i][2] + T[i][3];
+  }
+  float zmn = B[0][0], zmx = B[0][0], mss = 0.0f, mtt = 0.0f, mst = 0.0f, babs = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      zmn = fminf(zmn, B[i][j]);
+      zmx = fmaxf(zmx, B[i][j]);
+      babs = fmaxf(babs, fabsf(B[i][j]));
+      if (i < 2) mss = fmaxf(mss, fabsf(B[i + 2][j] - 2.0f * B[i + 1][j] + B[i][j]));
+      if (j < 2) mtt = fmaxf(mtt, fabsf(B[i][j + 2] - 2.0f * B[i][j + 1] + B[i][j]));
+      if (i < 3 && j < 3) mst = fmaxf(mst, fabsf(B[i + 1][j + 1] - B[i + 1][j] - B[i][j + 1] + B[i][j]));
+    }
+  const float pad = 4e-6f * (1.0f + babs);   // rounding of the conversions above
+  mss = fmaf(6.0f, mss, 24.0f * pad);
+  mtt = fmaf(6.0f, mtt, 24.0f * pad);
+  mst = fmaf(9.0f, mst, 36.0f * pad);
+  return make_float4(zmn - pad, zmx + pad, mss + mst, mtt + mst);
 }
 
 // Every thread of the CTA takes part; ends with __syncthreads.
@@ -205,14 +270,15 @@ __device__ inline void build_net_tables(const float* ctrl, int ncv, int nsu, int
     const float ue[4][4] = {{u0.x, u1.x, u2.x, u3.x}, {u0.y, u1.y, u2.y, u3.y},
                             {u0.z, u1.z, u2.z, u3.z}, {u0.w, u1.w, u2.w, u3.w}};  // ue[e][a]
     float4* out = s.patch + (size_t)p * 4;
+    float C[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      float c[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f)
-        c[f] = fmaf(ue[e][0], T[0][f], fmaf(ue[e][1], T[1][f], fmaf(ue[e][2], T[2][f], ue[e][3] * T[3][f])));
-      out[e] = make_float4(c[0], c[1], c[2], c[3]);
+        C[e][f] = fmaf(ue[e][0], T[0][f], fmaf(ue[e][1], T[1][f], fmaf(ue[e][2], T[2][f], ue[e][3] * T[3][f])));
+      out[e] = make_float4(C[e][0], C[e][1], C[e][2], C[e][3]);
     }
+    if (s.hull) s.hull[p] = patch_hull(C);
   }
   if (bounds) {
 #pragma unroll
@@ -239,9 +305,15 @@ __device__ inline void build_two_face_tables(const Item& it, const LensSmem& s, 
   build_net_tables(it.ctrl_in, it.ncv_in, it.nsu_in, it.nsv_in, true, e);
 }
 
+// The exit net's tables of an item at the start of shared memory.
+__device__ inline LensSmem carve_exit(unsigned char* base, const Item& it) {
+  return carve_lens(base, it.nsu, it.nsv, needs_hull(it));
+}
+
 // The entry net's tables follow the exit net's.
 __device__ inline LensSmem carve_entry(unsigned char* base, const Item& it) {
-  return carve_lens(base + ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15), it.nsu_in, it.nsv_in);
+  const bool h = needs_hull(it);
+  return carve_lens(base + ((lens_smem_bytes(it.nsu, it.nsv, h) + 15) & ~(size_t)15), it.nsu_in, it.nsv_in, h);
 }
 
 __device__ __forceinline__ void locate(float u, int ns, int* k, float* s) {
@@ -406,7 +478,83 @@ __device__ __forceinline__ void trace_collimated(const Item& it, const LensSmem&
   collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zs, Zt, r);
 }
 
-// Along one grid row t is fixed: the row cubics of the current patch,
+// Collimated cell-centre rays along one grid row: t (and with it the v
+// basis) is fixed, and u = (col + 1/2)/cols advances by 1/cols from ray to
+// ray. The walk takes u in span units, us = u nsu = (col + 1/2) nsu / cols,
+// keeps the current patch k (stepped when us passes its right knot, no
+// per-ray span search) and the row cubics of that patch,
+// r_e(t) = sum_f C[e][f] t^f and their t-derivatives, which serve every ray of
+// the row in it.
+struct RowWalk {
+  int k, l;
+  float v, t, y;
+  uint32_t col0;        // the first cell's column
+  float dus, hdus, kf;  // us step per column, half of it, k as a float
+  float r0, r1, r2, r3, d0, d1, d2, d3;
+
+  __device__ __forceinline__ void load(const Item& it, const LensSmem& ls) {
+    const float4* q = ls.patch + (size_t)(k * it.nsv + l) * 4;
+    cubic_d(q[0], t, &r0, &d0);
+    cubic_d(q[1], t, &r1, &d1);
+    cubic_d(q[2], t, &r2, &d2);
+    cubic_d(q[3], t, &r3, &d3);
+  }
+
+  // The walk from cell (row, col).
+  __device__ __forceinline__ void begin(const Item& it, const LensSmem& ls, uint32_t row, uint32_t col,
+                                        float inv_cols, float inv_rows) {
+    v = ((float)row + 0.5f) * inv_rows;
+    y = fmaf(2.0f, v, -1.0f) * it.ry;
+    locate(v, it.nsv, &l, &t);
+    col0 = col;
+    dus = inv_cols * (float)it.nsu;
+    hdus = 0.5f * dus;
+    k = min((int)fmaf((float)col, dus, hdus), it.nsu - 1);
+    kf = (float)k;
+    load(it, ls);
+  }
+
+  // The j-th ray of the walk. us is a function of the ray's column alone (the
+  // same rounding whichever lane traces it: deterministic mode stays bit-exact
+  // across schedules).
+  __device__ __forceinline__ void trace(const Item& it, const LensSmem& ls, uint32_t j, RayFwd& r) {
+    const float us = fmaf((float)(col0 + j), dus, hdus);
+    if (us >= kf + 1.0f && k < it.nsu - 1) {
+      do {
+        ++k;
+        kf += 1.0f;
+      } while (us >= kf + 1.0f && k < it.nsu - 1);
+      load(it, ls);
+    }
+    const float s = us - kf;
+    r.k = k;
+    r.l = l;
+    r.s = s;
+    r.t = t;
+    const float a = fmaf(s, r3, r2);
+    const float b = fmaf(s, a, r1);
+    const float db = fmaf(s, r3, a);
+    const float Z = fmaf(s, b, r0);
+    const float Zs = fmaf(s, db, b);
+    const float Zt = fmaf(s, fmaf(s, fmaf(s, d3, d2), d1), d0);
+    r.u = us * (1.0f / (float)it.nsu);
+    r.v = v;
+    r.x = fmaf(us, 2.0f * it.rx / (float)it.nsu, -it.rx);
+    r.y = y;
+    r.z = Z;
+    r.Zs = Zs;
+    r.Zt = Zt;
+    r.dx = 0.0f;
+    r.dy = 0.0f;
+    r.dz = 1.0f;
+    r.T1 = 1.0f - it.R0;   // normal incidence on the flat entry face
+    r.iters = 0;
+    exit_and_propagate<true>(it, r);
+  }
+};
+
+// The adjoint's walk along a lane's run of cells (the forward's is RowWalk in
+// column lockstep): along one grid row t is fixed: the row cubics of the current patch,
 // r_e(t) = sum_f C[e][f] t^f and their t-derivatives, serve every ray of the
 // row that falls in that patch.
 struct RowPatch {
@@ -452,6 +600,59 @@ __device__ __forceinline__ void trace_collimated_row(const Item& it, const LensS
   collimated_at(it, u, rp.v, rp.y, Z, Zs, Zt, r);
 }
 
+// Collimated cell-centre rays in column lockstep (forward trace): the rows of the call's cell range are taken in blocks of 32, one
+// row per lane, and the columns of the blocks, block after block, are split
+// evenly over the item's warps. At every step the lanes of a warp trace the
+// same column of 32 neighbouring rows, so their footprints move on to the next
+// pixel column, and their rays into the next patch, at nearly the same step:
+// the register sums are flushed, the dL/dE footprint re-read and the patch
+// cubics loaded by the whole warp at once rather than lane after lane.
+struct Lockstep {
+  uint64_t s, s1;   // this warp's column steps [s, s1)
+
+  // The column steps of the call's rows: blocks of 32 rows times the columns.
+  static __device__ __forceinline__ uint64_t steps(const Item& it) {
+    return (uint64_t)((it.row_hi - it.row_lo + 31) / 32) * (uint64_t)it.cols;
+  }
+
+  __device__ __forceinline__ void init(const Item& it, int warps) {
+    const uint64_t S = steps(it);
+    const uint64_t W = (uint64_t)(it.cta_end - it.cta_begin) * (uint64_t)warps;
+    const uint64_t gw = (uint64_t)((int)blockIdx.x - it.cta_begin) * (uint64_t)warps + (threadIdx.x >> 5);
+    s = S * gw / W;
+    s1 = S * (gw + 1) / W;
+  }
+
+  // The next run of this lane, cells (row, col + j) for j in [j0, j1) (empty
+  // for a lane past the last row or outside the call's range); false when the
+  // warp's share is done. Every lane of a warp returns the same col.
+  __device__ __forceinline__ bool next(const Item& it, uint32_t* row, uint32_t* col, uint32_t* j0, uint32_t* j1) {
+    if (s >= s1) return false;
+    const uint32_t cols = (uint32_t)it.cols;
+    const uint32_t rb = (uint32_t)(s / cols);
+    const uint32_t c0 = (uint32_t)(s - (uint64_t)rb * cols);
+    const uint32_t n = (uint32_t)min((uint64_t)(cols - c0), s1 - s);
+    s += n;
+    const uint32_t r = it.row_lo + rb * 32u + (threadIdx.x & 31u);
+    uint32_t a = 0, b = r < it.row_hi ? n : 0u;
+    if (r == it.row_lo && it.col_lo > c0) a = min(it.col_lo - c0, n);
+    if (r + 1 == it.row_hi) b = it.col_hi > c0 ? min(it.col_hi - c0, b) : 0u;
+    *row = r;
+    *col = c0;
+    *j0 = a;
+    *j1 = max(a, b);
+    return true;
+  }
+
+  // Most cells one CTA of `warps` warps can take (for fixed-point bounds).
+  static __device__ __forceinline__ uint64_t max_per_cta(const Item& it, int warps) {
+    const uint64_t S = steps(it);
+    const uint64_t W = (uint64_t)(it.cta_end - it.cta_begin) * (uint64_t)warps;
+    const uint64_t ci = (uint64_t)((int)blockIdx.x - it.cta_begin);
+    return 32 * (S * (ci + 1) * warps / W - S * ci * warps / W);
+  }
+};
+
 // f(t) = Z(o_uv + d_uv t) - o_z - d_z t (Eq. surfaceintersect) and df/dt.
 __device__ __forceinline__ void f_eval(const Item& it, const LensSmem& ls, float ou, float ov, float du, float dv,
                                        float oz, float dz, float t, RayFwd& r, float* f, float* fp) {
@@ -461,6 +662,275 @@ __device__ __forceinline__ void f_eval(const Item& it, const LensSmem& ls, float
   patch_eval(ls.patch + (size_t)(r.k * it.nsv + r.l) * 4, r.s, r.t, &Z, &r.Zs, &r.Zt);
   *f = Z - fmaf(dz, t, oz);
   *fp = fmaf(r.Zs, du * (float)it.nsu, fmaf(r.Zt, dv * (float)it.nsv, -dz));
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.2.1, Eq. surfaceintersect: the hit is the SMALLEST positive root of
+// f(t) = Z(o_uv + d_uv t) - o_z - d_z t over the domain. f > 0 while the ray is
+// below the surface. The root is found in two phases:
+//  1. A certified march from the bottom of the convex-hull slab: the patches
+//     (knot span products) the ray's (u, v) path crosses are visited in order
+//     of t; a patch whose lowest point (patch_hull) the ray only reaches after
+//     leaving it holds no root and is skipped; inside a patch, from a point t
+//     with f(t) > 0 and slope g = f'(t), the bound |f''| <= M of patch_hull
+//     gives f(t + d) >= f(t) + g d - M d^2 / 2 > 0 for every d below the
+//     positive root d* of that quadratic, so [t, t + d*) holds no root and the
+//     march moves to t + d*. (For a transverse root d* tends to the Newton step:
+//     the march converges quadratically from the left.)
+//  2. As soon as g < 0 and 2 M f < g^2, f is strictly decreasing on
+//     [t, t + 2f/|g|] (f' <= g + 2 M f/|g| < 0 there) and negative at its end,
+//     so that interval holds exactly one root, the first: safeguarded Newton
+//     (at most newton_max iterations, until a step is below the tolerance) runs
+//     on that bracket. When the bracket would reach past the patch, f at the
+//     patch's edge decides whether the root lies before it.
+// ---------------------------------------------------------------------------
+
+// The ray's (u, v, z) as functions of its parameter t on one net.
+struct NetLine {
+  float ou, ov, du, dv, oz, dz;
+};
+
+enum { ROOT_FOUND = 0, ROOT_NONE = 1, ROOT_FAIL = 2 };
+
+// Evaluations the march may take before Newton's bracket is found.
+constexpr int kMarchMax = 32;   // evaluations of the march, besides Newton's
+
+// The walk over the patches of one net along the ray: the current patch
+// (k, l), where the ray leaves it (tx, and whether through a u edge), and the
+// bound M of |f''| on it (patch_hull).
+struct PatchWalk {
+  int k, l;
+  float tx, M;
+  bool exit_u;
+
+  // Enters patch (k, l) at t: sets tx and M, and returns the first t in the
+  // patch that may be a root (the ray reaching the patch's lowest point).
+  __device__ __forceinline__ float enter(const float4* hull, int nsv, const NetLine& q, float inv_du, float inv_dv,
+                                         float inv_ns_u, float inv_ns_v, float inv_dz, float a2, float b2, float t,
+                                         float tb) {
+    const float txu = q.du != 0.0f ? ((float)(k + (q.du > 0.0f ? 1 : 0)) * inv_ns_u - q.ou) * inv_du : INFINITY;
+    const float txv = q.dv != 0.0f ? ((float)(l + (q.dv > 0.0f ? 1 : 0)) * inv_ns_v - q.ov) * inv_dv : INFINITY;
+    exit_u = txu <= txv;
+    tx = fminf(fminf(txu, txv), tb);
+    const float4 h = hull[k * nsv + l];
+    M = fmaf(h.z, a2, h.w * b2);
+    return fmaxf(t, (h.x - q.oz) * inv_dz);
+  }
+};
+
+// f(t) and f'(t) on a net whose power-form patches are `patch` (the same
+// arithmetic as f_eval and f_eval_in, without a ray record).
+__device__ __forceinline__ void net_f(const float4* patch, int nsu, int nsv, const NetLine& q, float t, float* f,
+                                      float* fp) {
+  int k, l;
+  float s, u, Z, Zs, Zt;
+  locate(fmaf(q.du, t, q.ou), nsu, &k, &s);
+  locate(fmaf(q.dv, t, q.ov), nsv, &l, &u);
+  patch_eval(patch + (size_t)(k * nsv + l) * 4, s, u, &Z, &Zs, &Zt);
+  *f = Z - fmaf(q.dz, t, q.oz);
+  *fp = fmaf(Zs, q.du * (float)nsu, fmaf(Zt, q.dv * (float)nsv, -q.dz));
+}
+
+// The march: the smallest root of f on [ta, tb] (f(ta) >= 0): ROOT_FOUND
+// with t, ROOT_NONE when the ray reaches tb first, ROOT_FAIL when the march or
+// Newton runs out of evaluations. One loop with one evaluation per pass
+// serves both phases, so that the lanes of a warp evaluate together whichever
+// phase each is in. Out of line: the quick path (first_root) rarely needs it.
+static __device__ __noinline__ int first_root_march(const float4* patch, const float4* hull, int nsu, int nsv, NetLine q,
+                                             float ta, float tb, int newton_max, float tol, float* t_out, int* iters) {
+  const float fnsu = (float)nsu, fnsv = (float)nsv;
+  const float a = q.du * fnsu, b = q.dv * fnsv;   // ds/dt, dt/dt in patch units
+  const float a2 = a * a, b2 = b * b;
+  const float inv_dz = fast_rcp(q.dz);
+  const float inv_du = q.du != 0.0f ? fast_rcp(q.du) : 0.0f, inv_dv = q.dv != 0.0f ? fast_rcp(q.dv) : 0.0f;
+  const float inv_ns_u = fast_rcp(fnsu), inv_ns_v = fast_rcp(fnsv);
+  PatchWalk w;
+  w.k = min(max((int)(fmaf(q.du, ta, q.ou) * fnsu), 0), nsu - 1);
+  w.l = min(max((int)(fmaf(q.dv, ta, q.ov) * fnsv), 0), nsv - 1);
+  *iters = 0;
+  // The first patch that may hold a root; a patch whose lowest point the ray
+  // only reaches after leaving it is passed without an evaluation.
+  float t = w.enter(hull, nsv, q, inv_du, inv_dv, inv_ns_u, inv_ns_v, inv_dz, a2, b2, ta, tb);
+  for (int visit = 0; t >= w.tx; ++visit) {
+    if (w.tx >= tb || visit > nsu + nsv) return ROOT_NONE;
+    if (w.exit_u) w.k += q.du > 0.0f ? 1 : -1;
+    else w.l += q.dv > 0.0f ? 1 : -1;
+    if (w.k < 0 || w.k >= nsu || w.l < 0 || w.l >= nsv) return ROOT_NONE;
+    t = w.enter(hull, nsv, q, inv_du, inv_dv, inv_ns_u, inv_ns_v, inv_dz, a2, b2, w.tx, tb);
+  }
+  int phase = 0;   // 0 march, 1 f at the patch's edge, 2 Newton on [lo, hi]
+  float lo = t, hi = t, flo = 0.0f, glo = 0.0f, tprev = t;
+  int nn = 0;
+  for (int pass = 0; pass < kMarchMax + newton_max; ++pass) {
+    float f, g;
+    net_f(patch, nsu, nsv, q, t, &f, &g);
+    if (phase == 2) {
+      ++nn;
+      if (f > 0.0f) lo = t; else hi = t;
+      if (fabsf(t - tprev) <= tol || f == 0.0f) {
+        *t_out = t;
+        *iters = nn;
+        return ROOT_FOUND;
+      }
+      if (nn >= newton_max) return ROOT_FAIL;
+      float tn = t - __fdividef(f, g);
+      // The bracket is closed: an exact root on its edge (Newton landing on the
+      // root leaves f within rounding of 0 on either side) is kept, not bisected.
+      if (!(g < 0.0f) || !(tn >= lo && tn <= hi)) tn = 0.5f * (lo + hi);
+      tprev = t;
+      t = tn;
+      continue;
+    }
+    if (phase == 1) {   // f at the edge of a patch on which f decreases strictly from lo
+      if (f == 0.0f) {
+        *t_out = t;
+        return ROOT_FOUND;
+      }
+      if (f < 0.0f) {   // the root lies in [lo, edge]: Newton from lo
+        phase = 2;
+        hi = t;
+        float tn = lo - __fdividef(flo, glo);
+        if (!(tn >= lo && tn <= hi)) tn = 0.5f * (lo + hi);
+        tprev = lo;
+        t = tn;
+        continue;
+      }
+      phase = 0;   // no root up to the edge: on to the next patch
+    } else {
+      if (!(f > 0.0f)) {   // on the root within rounding
+        *t_out = t;
+        return ROOT_FOUND;
+      }
+      if (g < 0.0f && 2.0f * w.M * f < g * g) {
+        // f decreases strictly on [t, t + 2f/|g|] and is negative at its end
+        const float n = f * fast_rcp(-g);
+        lo = t;
+        if (t + 2.0f * n <= w.tx) {
+          phase = 2;
+          hi = t + 2.0f * n;
+          tprev = t;
+          t += n;   // the first Newton step
+        } else {
+          phase = 1;
+          flo = f;
+          glo = g;
+          t = w.tx;
+        }
+        continue;
+      }
+      // certified step: f + g d - M d^2 / 2 > 0 for 0 <= d < d*
+      const float r = fast_sqrt(fmaf(g, g, 2.0f * w.M * f));
+      t += g <= 0.0f ? 2.0f * f * fast_rcp(r - g) : (w.M > 0.0f ? (g + r) * fast_rcp(w.M) : INFINITY);
+      if (t < w.tx) continue;
+    }
+    // leave the patch at its edge; pass the patches the ray stays below
+    t = w.tx;
+    for (int visit = 0; t >= w.tx; ++visit) {
+      if (w.tx >= tb || visit > nsu + nsv) return ROOT_NONE;
+      if (w.exit_u) w.k += q.du > 0.0f ? 1 : -1;
+      else w.l += q.dv > 0.0f ? 1 : -1;
+      if (w.k < 0 || w.k >= nsu || w.l < 0 || w.l >= nsv) return ROOT_NONE;
+      t = w.enter(hull, nsv, q, inv_du, inv_dv, inv_ns_u, inv_ns_v, inv_dz, a2, b2, w.tx, tb);
+    }
+  }
+  return ROOT_FAIL;
+}
+
+// Whether [ta, te) holds no root of f, given f(te) = fe >= 0 and f'(te) = ge
+// (te a root Newton found, fe = 0, or the side of the domain, fe > 0), from the
+// patch bounds alone (no evaluation of f): the patches the ray crosses before
+// the first one whose lowest point it reaches (tc) hold none, and from tc on,
+// with |f''| <= Mmax over every patch crossed, f(t) >= q(d) = fe - ge d -
+// Mmax d^2 / 2 for d = te - t; q is concave, so q > 0 on [0, te - tc] follows
+// from q(0) = fe >= 0 (and ge < 0 when fe = 0) and q(te - tc) > 0.
+__device__ __forceinline__ bool no_root_before(const float4* hull, int nsu, int nsv, const NetLine& q, float ta,
+                                               float te, float fe, float ge) {
+  if (!(fe > 0.0f) && !(fe == 0.0f && ge < 0.0f)) return false;
+  // a margin of 12% on the curvature bound for the rounding of f, f' and the bounds in FP32
+  auto holds = [&](float D, float M) { return fe - ge * D - 0.56f * M * D * D > 0.0f; };
+  const float fnsu = (float)nsu, fnsv = (float)nsv;
+  const float a = q.du * fnsu, b = q.dv * fnsv;
+  const float a2 = a * a, b2 = b * b;
+  const float inv_dz = fast_rcp(q.dz);
+  {   // the usual case: the ray is over one patch from ta to te
+    const int k0 = min(max((int)(fmaf(q.du, ta, q.ou) * fnsu), 0), nsu - 1);
+    const int l0 = min(max((int)(fmaf(q.dv, ta, q.ov) * fnsv), 0), nsv - 1);
+    const int k1 = min(max((int)(fmaf(q.du, te, q.ou) * fnsu), 0), nsu - 1);
+    const int l1 = min(max((int)(fmaf(q.dv, te, q.ov) * fnsv), 0), nsv - 1);
+    if (k0 == k1 && l0 == l1) {
+      const float4 h = hull[k1 * nsv + l1];
+      const float tc = fmaxf(ta, (h.x - q.oz) * inv_dz);
+      return tc >= te || holds(te - tc, fmaf(h.z, a2, h.w * b2));
+    }
+  }
+  const float inv_du = q.du != 0.0f ? fast_rcp(q.du) : 0.0f, inv_dv = q.dv != 0.0f ? fast_rcp(q.dv) : 0.0f;
+  PatchWalk w;
+  w.k = min(max((int)(fmaf(q.du, ta, q.ou) * fnsu), 0), nsu - 1);
+  w.l = min(max((int)(fmaf(q.dv, ta, q.ov) * fnsv), 0), nsv - 1);
+  float t = ta, tc = INFINITY, Mmax = 0.0f;
+  for (int visit = 0; visit <= nsu + nsv; ++visit) {
+    const float tz = w.enter(hull, nsv, q, inv_du, inv_dv, 1.0f / fnsu, 1.0f / fnsv, inv_dz, a2, b2, t, te);
+    if (tc < INFINITY || tz < w.tx) {   // from the first patch the ray may meet on
+      tc = fminf(tc, tz);
+      Mmax = fmaxf(Mmax, w.M);
+    }
+    if (w.tx >= te) break;
+    t = w.tx;
+    if (w.exit_u) w.k += q.du > 0.0f ? 1 : -1;
+    else w.l += q.dv > 0.0f ? 1 : -1;
+    if (w.k < 0 || w.k >= nsu || w.l < 0 || w.l >= nsv) break;
+  }
+  return tc >= te || holds(te - tc, Mmax);
+}
+
+// The smallest root of f on [ta, tb] (f(ta) >= 0), as first_root_march
+// defines it, found the quick way where that is safe: safeguarded Newton from
+// the middle of [ta, tb], when f(tb) <= 0 brackets a root, then the patch
+// bounds certify that no root lies before the one Newton found
+// (no_root_before); a ray that reaches a side of the domain with f > 0 is
+// certified the same way to cross nothing before it. Where a certificate fails
+// (the bounds cannot exclude a crossing, as on steep or strongly curved
+// surfaces) or Newton does not converge, the march decides.
+template <class Eval>
+__device__ __forceinline__ int first_root(const float4* patch, const float4* hull, int nsu, int nsv, const NetLine& q,
+                                          float ta, float tb, bool tb_is_top, int newton_max, float tol, Eval eval,
+                                          float* t_out, float* fp_out, int* iters) {
+  float f, g;
+  bool bracketed = true;
+  if (!tb_is_top) {   // the slab's top has f <= 0 (convex hull); a side of the domain may not
+    eval(tb, &f, &g);
+    bracketed = !(f > 0.0f);
+    // the ray leaves through the side with f > 0: no root if the bounds show none before
+    if (!bracketed && no_root_before(hull, nsu, nsv, q, ta, tb, f, g)) return ROOT_NONE;
+  }
+  if (bracketed) {
+    float lo = ta, hi = tb;
+    float t = 0.5f * (ta + tb);
+    eval(t, &f, &g);
+    if (f > 0.0f) lo = t; else hi = t;
+    bool converged = (f == 0.0f);
+    int n = 0;
+    for (; n < newton_max && !converged; ++n) {
+      float tn = t - __fdividef(f, g);
+      // The bracket is closed: an exact root on its edge (Newton landing on the
+      // root leaves f within rounding of 0 on either side) is kept, not bisected.
+      if (!(g < 0.0f) || !(tn >= lo && tn <= hi)) tn = 0.5f * (lo + hi);
+      const float step = fabsf(tn - t);
+      t = tn;
+      eval(t, &f, &g);
+      if (f > 0.0f) lo = t; else hi = t;
+      if (step <= tol || f == 0.0f) converged = true;
+    }
+    if (converged && no_root_before(hull, nsu, nsv, q, ta, t, 0.0f, g)) {
+      *t_out = t;
+      *fp_out = g;
+      *iters = n;
+      return ROOT_FOUND;
+    }
+  }
+  const int st = first_root_march(patch, hull, nsu, nsv, q, ta, tb, newton_max, tol, t_out, iters);
+  if (st == ROOT_FOUND) eval(*t_out, &f, fp_out);   // the caller's record at the root
+  return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -523,7 +993,8 @@ __device__ __forceinline__ float mesh_height(const Item& it, const LensSmem& ls,
 // t (a grid walk), each cell's two triangles tested; the first cell with a hit
 // holds the first hit. The inside test has a margin of 1e-4 cell widths so that
 // FP32 rounding cannot let a ray slip between two triangles; near an edge both
-// may accept and the smaller t is kept. At most NU + NV cells are visited. On
+// may accept and the smaller t is kept; no hit is taken past tb (the side of
+// the lens or the top of the slab). At most NU + NV cells are visited. On
 // a hit fills tstar, gp (= dg/dt of g = mesh - ray height), the cell,
 // triangle and local coordinates, and the cell count in iters.
 __device__ __forceinline__ bool mesh_intersect(const Item& it, const LensSmem& ls, float ou, float ov, float du,
@@ -556,7 +1027,9 @@ __device__ __forceinline__ bool mesh_intersect(const Item& it, const LensSmem& l
       // c0 + ca (a0 + da t) + cb (b0 + db t) = oz + dz t
       const float den = dz - fmaf(ca, da, cb * db);
       const float t = (fmaf(ca, a0, fmaf(cb, b0, c0)) - oz) / den;
-      if (!(t >= 0.0f) || !(t < best)) continue;
+      // The hit must lie over the domain: the inside test's margin must not
+      // accept a point past the side of the lens (t > tb) on a boundary cell.
+      if (!(t >= 0.0f) || !(t < best) || !(t <= tb)) continue;
       const float a = fmaf(da, t, a0), b = fmaf(db, t, b0);
       const bool in = up ? (a <= 1.0f + eps && b <= 1.0f + eps && a + b >= 1.0f - eps)
                          : (a >= -eps && b >= -eps && a + b <= 1.0f + eps);
@@ -701,34 +1174,20 @@ __device__ __forceinline__ void exit_hit(const Item& it, const LensSmem& ls, flo
     exit_and_propagate<false>(it, r);
     return;
   }
-  if (tb < t_hi) {
-    f_eval(it, ls, ou, ov, du, dv, oz, r.dz, tb, r, &f, &fp);
-    if (f > 0.0f) { r.status = FR_RAY_OUT_OF_DOMAIN; return; }   // leaves the side first
-  }
   // f(ta) >= 0 by the convex hull unless the slab starts at the entry face,
   // where the freeform may lie below it.
   if (ta == 0.0f) {
     f_eval(it, ls, ou, ov, du, dv, oz, r.dz, 0.0f, r, &f, &fp);
     if (f < 0.0f) { r.status = FR_RAY_INVALID; return; }
   }
-  // Newton from the middle of the bracket, with bisection as the safeguard.
-  float t = 0.5f * (ta + tb);
-  f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
-  if (f > 0.0f) ta = t; else tb = t;
-  bool converged = (f == 0.0f);
-  for (int n = 0; n < it.newton_max && !converged; ++n) {
-    float tn = t - __fdividef(f, fp);
-    // The bracket is closed: an exact root on its edge (Newton landing on the
-    // root leaves f within rounding of 0 on either side) is kept, not bisected.
-    if (!(fp < 0.0f) || !(tn >= ta && tn <= tb)) tn = 0.5f * (ta + tb);
-    const float step = fabsf(tn - t);
-    t = tn;
-    f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, &f, &fp);
-    r.iters = n + 1;
-    if (f > 0.0f) ta = t; else tb = t;
-    if (step <= it.newton_tol || f == 0.0f) converged = true;
-  }
-  if (!converged) { r.status = FR_RAY_NEWTON_FAIL; return; }
+  // The smallest root: certified march, then Newton on a bracket that isolates it.
+  const NetLine q{ou, ov, du, dv, oz, r.dz};
+  auto eval = [&](float t, float* fv, float* gv) { f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, fv, gv); };
+  float t;
+  const int found = first_root(ls.patch, ls.hull, it.nsu, it.nsv, q, ta, tb, !(tb < t_hi), it.newton_max,
+                               it.newton_tol, eval, &t, &fp, &r.iters);
+  if (found == ROOT_NONE) { r.status = FR_RAY_OUT_OF_DOMAIN; return; }   // leaves the side first
+  if (found == ROOT_FAIL) { r.status = FR_RAY_NEWTON_FAIL; return; }
   r.tstar = t;
   r.gp = fp;
   r.u = fmaf(du, t, ou);
@@ -831,30 +1290,21 @@ __device__ __forceinline__ void trace_two_face(const Item& it, const LensSmem& l
     if (du < 0.0f) t_dom = fminf(t_dom, -ou / du);
     if (dv > 0.0f) t_dom = fminf(t_dom, (1.0f - ov) / dv);
     if (dv < 0.0f) t_dom = fminf(t_dom, -ov / dv);
-    float tb = fminf(t_hi, t_dom);
+    const float tb = fminf(t_hi, t_dom);
     float f, fp;
-    if (tb < t_hi) {
-      f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, tb, e, &f, &fp);
-      if (f > 0.0f) { r.status = FR_RAY_APERTURE_MISS; return; }   // leaves through the side first
-    }
     if (ta == 0.0f) {
       f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, 0.0f, e, &f, &fp);
       if (f < 0.0f) { r.status = FR_RAY_INVALID; return; }
     }
-    float t = 0.5f * (ta + tb);
-    f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, t, e, &f, &fp);
-    if (f > 0.0f) ta = t; else tb = t;
-    bool converged = (f == 0.0f);
-    for (int n = 0; n < it.newton_max && !converged; ++n) {
-      float tn = t - __fdividef(f, fp);
-      if (!(fp < 0.0f) || !(tn >= ta && tn <= tb)) tn = 0.5f * (ta + tb);   // closed, as in exit_hit
-      const float step = fabsf(tn - t);
-      t = tn;
-      f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, t, e, &f, &fp);
-      if (f > 0.0f) ta = t; else tb = t;
-      if (step <= it.newton_tol || f == 0.0f) converged = true;
-    }
-    if (!converged) { r.status = FR_RAY_NEWTON_FAIL; return; }
+    // The smallest root, as for the exit face (first_root).
+    const NetLine q{ou, ov, du, dv, it.pz, e.d0z};
+    auto eval = [&](float t, float* fv, float* gv) { f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, t, e, fv, gv); };
+    float t;
+    int iters_in = 0;
+    const int found = first_root(li.patch, li.hull, it.nsu_in, it.nsv_in, q, ta, tb, !(tb < t_hi), it.newton_max,
+                                 it.newton_tol, eval, &t, &fp, &iters_in);
+    if (found == ROOT_NONE) { r.status = FR_RAY_APERTURE_MISS; return; }   // leaves through the side first
+    if (found == ROOT_FAIL) { r.status = FR_RAY_NEWTON_FAIL; return; }
     e.tin = t;
     e.gpin = fp;
     e.ox = fmaf(e.d0x, t, sx);
@@ -897,6 +1347,42 @@ struct Foot {
   float rsx, rsy;       // 1 / sum f
 };
 
+// Both axes at once: the x and y work of the filter runs as packed FP32 pairs
+// (one add, multiply or FMA instruction for the two axes), except the
+// exponentials, floors and clamps.
+template <int NU>
+__device__ __forceinline__ bool footprint(const Item& it, float X, float Y, Foot<NU>& f) {
+  constexpr int h = (NU - 1) / 2;
+  const float2 g = __ffma2_rn(make_float2(X, Y), make_float2(it.inv_wx, it.inv_wy), make_float2(it.gx_off, it.gy_off));
+  const float flx = fminf(fmaxf(floorf(g.x), (float)h), (float)(it.nx + h - 1));
+  const float fly = fminf(fmaxf(floorf(g.y), (float)h), (float)(it.ny + h - 1));
+  f.ie = (int)flx - h;
+  f.je = (int)fly - h;
+  // g - (first + 0.5), in pixels, for each axis
+  const float2 d0 = __fadd2_rn(__fadd2_rn(g, make_float2(-flx, -fly)), make_float2((float)h - 0.5f, (float)h - 0.5f));
+  f.dx0 = d0.x;
+  f.dy0 = d0.y;
+  const float2 na = make_float2(-it.ax, -it.ay), ncut = make_float2(-it.cut, -it.cut);
+  float2 sum = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int a = 0; a < NU; ++a) {
+    // Outside the support |d| >= nu/2 the exponential is at most `cut`, so the
+    // clamp at 0 is the support test.
+    const float2 d = __fadd2_rn(d0, make_float2(-(float)a, -(float)a));
+    const float2 e = __fmul2_rn(__fmul2_rn(na, d), d);
+    float2 v = __fadd2_rn(make_float2(ex2_approx(e.x), ex2_approx(e.y)), ncut);
+    v.x = fmaxf(v.x, 0.0f);
+    v.y = fmaxf(v.y, 0.0f);
+    f.fx[a] = v.x;
+    f.fy[a] = v.y;
+    sum = __fadd2_rn(sum, v);
+  }
+  // For nu >= 3 the hit's own pixel is well inside the support: sum > 0.
+  f.rsx = (NU >= 3 || sum.x > 0.0f) ? fast_rcp(sum.x) : 0.0f;
+  f.rsy = (NU >= 3 || sum.y > 0.0f) ? fast_rcp(sum.y) : 0.0f;
+  return NU >= 3 || (f.rsx > 0.0f && f.rsy > 0.0f);   // nu = 1 exactly on a pixel edge: all f = 0
+}
+
 template <int NU>
 __device__ __forceinline__ void axis_footprint(float g, int n, float a2, float cut, int* first, float* d0, float* f,
                                                float* rs) {
@@ -918,8 +1404,11 @@ __device__ __forceinline__ void axis_footprint(float g, int n, float a2, float c
   *rs = (NU >= 3 || sum > 0.0f) ? fast_rcp(sum) : 0.0f;
 }
 
+// The same footprint one axis at a time (the adjoint and tangent traces, whose
+// register budget the packed pairs of `footprint` would strain); bit for bit
+// the same values.
 template <int NU>
-__device__ __forceinline__ bool footprint(const Item& it, float X, float Y, Foot<NU>& f) {
+__device__ __forceinline__ bool footprint_scalar(const Item& it, float X, float Y, Foot<NU>& f) {
   const float gx = fmaf(X, it.inv_wx, it.gx_off);
   const float gy = fmaf(Y, it.inv_wy, it.gy_off);
   axis_footprint<NU>(gx, it.nx, it.ax, it.cut, &f.ie, &f.dx0, f.fx, &f.rsx);

@@ -32,6 +32,9 @@ struct Item {
   int nparam;                   // control heights: ncu ncv (+ ncu_in ncv_in); dL/dP has this many
   // Source (Sec. 2.2.1).
   int kind, jitter, cols, rows;
+  uint32_t row_lo, row_hi;      // collimated: the rows of the call's cells [ray_begin, ray_end),
+  uint32_t col_lo, col_hi;      // which start at column col_lo of row_lo and end before
+                                // column col_hi of row_hi - 1
   float px, py, pz;             // source position (grid centre)
   float omc_max;                // 1 - cos(phi_max)
   int gnx, gny;
@@ -156,6 +159,10 @@ int tangent_occupancy(int threads, size_t smem, int nu);
 cudaError_t configure_tangent(int optin);
 cudaError_t configure_forward(int optin);
 cudaError_t configure_adjoint(int optin);
+
+// Throughput probes (fr_probe): operations of one launch, and the launch.
+double probe_ops(int kind, int blocks, int threads, int iters);
+cudaError_t launch_probe(int kind, int blocks, int threads, int iters, float* out, int n_out, cudaStream_t st);
 
 // Occupancy of the trace kernels for a block size and dynamic shared memory.
 // kinds: 1 collimated, 2 point source (single-lens launches); batches use both.

@@ -67,7 +67,7 @@ __device__ __forceinline__ void adjoint_ray(const Item& it, const LensSmem& ls, 
                                             const float (&Nv)[4], const float (&dNv)[4], GradAcc<DET>& acc,
                                             const GradOut& go) {
   Foot<NU> f;
-  if (!footprint<NU>(it, r.X, r.Y, f)) return;
+  if (!footprint_scalar<NU>(it, r.X, r.Y, f)) return;
   if (f.ie != gc.ie || f.je != gc.je) {
 #pragma unroll
     for (int b = 0; b < NU; ++b)
@@ -169,7 +169,7 @@ __device__ __forceinline__ void adjoint_ray_moments(const Item& it, const LensSm
                                                     uint32_t row, GCache<NU>& gc, RowMoments& m,
                                                     const float (&Nv)[4], const float (&dNv)[4], float* sg) {
   Foot<NU> f;
-  if (!footprint<NU>(it, r.X, r.Y, f)) return;
+  if (!footprint_scalar<NU>(it, r.X, r.Y, f)) return;
   if (f.ie != gc.ie || f.je != gc.je) {
 #pragma unroll
     for (int b = 0; b < NU; ++b)
@@ -266,7 +266,7 @@ __device__ void run_adjoint_lane_two(const Item& it, const LensSmem& ls, const L
     cnt.add(r.status, s_cnt);
     if (r.status != FR_RAY_ON_SCREEN) continue;
     Foot<NU> f;
-    if (!footprint<NU>(it, r.X, r.Y, f)) continue;
+    if (!footprint_scalar<NU>(it, r.X, r.Y, f)) continue;
     if (f.ie != gc.ie || f.je != gc.je) {
 #pragma unroll
       for (int bb = 0; bb < NU; ++bb)
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 32
   while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
   const Item& it = L.items[ii];
   extern __shared__ __align__(16) unsigned char smem[];
-  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  const LensSmem ls = carve_exit(smem, it);
   const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;
   unsigned char* grad_raw = smem + tables_bytes(it);
   GradOut go;

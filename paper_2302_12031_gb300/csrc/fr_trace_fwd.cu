@@ -159,19 +159,30 @@ __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const T
 #pragma unroll
       for (int a = 0; a < NU; ++a) acc.v[b][a] = 0;
   }
-  const float Kx = r.w * it.inv_area * f.rsx;
+  // kx_a = w/(w_x w_y) F^x_a, ky_b = F^y_b, as packed pairs
+  const float2 K = make_float2(r.w * it.inv_area * f.rsx, f.rsy);
   float kx[NU], ky[NU];
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    kx[a] = f.fx[a] * Kx;
-    ky[a] = f.fy[a] * f.rsy;
+    const float2 k2 = __fmul2_rn(make_float2(f.fx[a], f.fy[a]), K);
+    kx[a] = k2.x;
+    ky[a] = k2.y;
   }
 #pragma unroll
   for (int b = 0; b < NU; ++b) {
+    if constexpr (DET) {
 #pragma unroll
-    for (int a = 0; a < NU; ++a) {
-      if constexpr (DET) acc.v[b][a] += __float2ll_rn(kx[a] * ky[b] * it.fixE);
-      else acc.v[b][a] = fmaf(kx[a], ky[b], acc.v[b][a]);
+      for (int a = 0; a < NU; ++a) acc.v[b][a] += __float2ll_rn(kx[a] * ky[b] * it.fixE);
+    } else {
+      // acc_ba += kx_a ky_b, two cells of the row per instruction
+#pragma unroll
+      for (int a = 0; a + 1 < NU; a += 2) {
+        const float2 s2 = __ffma2_rn(make_float2(kx[a], kx[a + 1]), make_float2(ky[b], ky[b]),
+                                     make_float2(acc.v[b][a], acc.v[b][a + 1]));
+        acc.v[b][a] = s2.x;
+        acc.v[b][a + 1] = s2.y;
+      }
+      if (NU & 1) acc.v[b][NU - 1] = fmaf(kx[NU - 1], ky[b], acc.v[b][NU - 1]);
     }
   }
 }
@@ -228,30 +239,35 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
       cnt.add(r.status, s_cnt);
       if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
     }
+  } else if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED) && !it.jitter) {
+    // cell centres in column lockstep (the lanes' shares are not lane_range's)
+    const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+    Lockstep lk;
+    lk.init(it, blockDim.x >> 5);
+    uint32_t row, col, j0, j1;
+    while (lk.next(it, &row, &col, &j0, &j1)) {
+      RowWalk w;
+      w.begin(it, ls, row, col, inv_cols, inv_rows);
+      for (uint32_t j = j0; j < j1; ++j) {
+        RayFwd r;
+        w.trace(it, ls, j, r);
+        cnt.add(r.status, s_cnt);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
+      }
+    }
   } else if (a < b) {
     if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED)) {
+      // jittered rays: the lane's run of ids
       const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
       uint32_t row = (uint32_t)(a / (uint64_t)it.cols);
       uint32_t col = (uint32_t)(a - (uint64_t)row * (uint64_t)it.cols);
       const uint32_t n = (uint32_t)(b - a);
-      if (!it.jitter) {
-        RowPatch rp;
-        rp.row = 0xffffffffu;
-        for (uint32_t j = 0; j < n; ++j) {
-          RayFwd r;
-          trace_collimated_row(it, ls, row, col, inv_cols, inv_rows, rp, r);
-          cnt.add(r.status, s_cnt);
-          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
-          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
-        }
-      } else {
-        for (uint32_t j = 0; j < n; ++j) {
-          RayFwd r;
-          trace_collimated(it, ls, row, col, a + j, inv_cols, inv_rows, r);
-          cnt.add(r.status, s_cnt);
-          if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
-          if (++col == (uint32_t)it.cols) { col = 0; ++row; }
-        }
+      for (uint32_t j = 0; j < n; ++j) {
+        RayFwd r;
+        trace_collimated(it, ls, row, col, a + j, inv_cols, inv_rows, r);
+        cnt.add(r.status, s_cnt);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
+        if (++col == (uint32_t)it.cols) { col = 0; ++row; }
       }
     } else if (KINDS & 2) {
       for (uint64_t id = a; id < b; ++id) {
@@ -267,14 +283,14 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Launch bounds: two CTAs per SM of up to 448 (collimated, float, filter
-// sizes 1 and 3), 384 (collimated: float with size 5, deterministic with 1 and
-// 3), 256 (collimated deterministic with 5; batches); the single point-source
+// Launch bounds: two CTAs per SM of up to 384 (collimated: float with filter
+// sizes 1, 3 and 5, deterministic with 1 and 3), 256 (collimated deterministic
+// with 5; batches); the single point-source
 // kernel also runs one CTA per SM of 640 threads (filter sizes 1, 3) or 512
 // (size 5) in the window form. The variants of filter sizes 1 and 3 do not
 // spill; those of size 5 spill 150-200 bytes at any two-CTA bound.
 template <int CAP, bool DET, int NU, int KINDS>
-__global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? (DET ? 384 : 448) : (DET ? 256 : 384))
+__global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? 384 : (DET ? 256 : 384))
                                              : (KINDS == 2 ? (!DET && NU <= 3 ? 640 : 512) : 256),
                                   KINDS == 2 ? 1 : 2)
     k_forward(const __grid_constant__ Launch<CAP> L) {
@@ -283,7 +299,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? (DET ? 384 : 448) : (D
   while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
   const Item& it = L.items[ii];
   extern __shared__ __align__(16) unsigned char smem[];
-  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  const LensSmem ls = carve_exit(smem, it);
   const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;
   unsigned char* hist_raw = smem + tables_bytes(it);
   const int ncell = it.ncol * it.nrow;
@@ -309,8 +325,10 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? (DET ? 384 : 448) : (D
     const uint64_t n = it.ray_end - it.ray_begin;
     const uint64_t G = (uint64_t)(it.cta_end - it.cta_begin);
     const uint64_t ci = (uint64_t)((int)blockIdx.x - it.cta_begin);
+    const bool lockstep = it.kind == FR_SOURCE_COLLIMATED && !it.jitter && !((KINDS & 4) && it.two_face);
     const float rays = (float)((KINDS & 2) && it.order ? OrderCursor::max_per_cta(it, L.warps)
-                                                        : n * (ci + 1) / G - n * ci / G) + 1.0f;
+                               : lockstep ? Lockstep::max_per_cta(it, L.warps)
+                                          : n * (ci + 1) / G - n * ci / G) + 1.0f;
     int e = 0;
     frexpf(rays * it.omega0 * it.inv_area, &e);
     tg.sh_scale = ldexpf(1.0f, 31 - e);
@@ -411,7 +429,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? (DET ? 384 : 448) : (D
 // The full record of every ray of [ray_begin, ray_end), one thread per ray.
 __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
+  const LensSmem ls = carve_exit(smem, it);
   const LensSmem li = it.two_face ? carve_entry(smem, it) : ls;
   if (it.two_face) build_two_face_tables(it, ls, li);
   else build_lens_tables(it, ls);

@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
                                                     const float* __restrict__ dP, int n_dirs,
                                                     float* __restrict__ dE) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const LensSmem ls = carve_lens(smem, it.nsu, it.nsv);
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15));
+  const LensSmem ls = carve_exit(smem, it);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem + ((lens_smem_bytes(it.nsu, it.nsv, needs_hull(it)) + 15) & ~(size_t)15));
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
   const int nctrl = it.ncu * it.ncv;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
     cnt.add(r.status, cnt_dst);
     if (r.status != FR_RAY_ON_SCREEN || m == 0u) continue;
     Foot<NU> f;
-    if (!footprint<NU>(it, r.X, r.Y, f)) continue;
+    if (!footprint_scalar<NU>(it, r.X, r.Y, f)) continue;
     float Nu[4], dNu[4], Nv[4], dNv[4];
     basis_eval(ls.bu + r.k * 4, r.s, Nu, dNu);
     basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
@@ -264,7 +264,7 @@ TanKernel pick_tangent(int nu) {
 }  // namespace
 
 size_t tan_smem_bytes(const Item& it) {
-  return ((lens_smem_bytes(it.nsu, it.nsv) + 15) & ~(size_t)15) + (size_t)it.nsu * it.nsv * 4;
+  return ((lens_smem_bytes(it.nsu, it.nsv, needs_hull(it)) + 15) & ~(size_t)15) + (size_t)it.nsu * it.nsv * 4;
 }
 
 cudaError_t launch_tangent(const Item& it, int warps, int grid, size_t smem, const float* dP, int n_dirs, float* dE,

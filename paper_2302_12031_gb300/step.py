@@ -91,6 +91,7 @@ class OptimStep:
         if self.order is not None:
             for o in (self._fwd_opts, self._adj_opts):
                 o.ray_order = self.order.data_ptr()
+                o.ray_order_numel = self.order.numel()
         self.P_host = self.loss_host = None
         self.graph = None
         if graph:

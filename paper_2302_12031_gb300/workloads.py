@@ -130,6 +130,22 @@ def point(name, n_rays, n_ctrl, bins, height_seed, ray_seed, target_seed,
     return wl
 
 
+def wall_lens(name, n_rays, bins=32, n_ctrl=16, low=0.2, high=2.0, split=13, ray_seed=11):
+    """A point source under a lens whose exit face has a step ("wall") across u:
+    control heights `low` for the rows i < split and `high` from there on.
+
+    The B-spline turns the step into a wall steeper than the glass rays, so a
+    ray that meets the low part just before the wall passes under the wall and
+    crosses the surface again: f(t) of the intersection (Sec. 2.2.1) has
+    several roots, and the hit is the smallest one. Otherwise as `point`.
+    """
+    wl = point(name, n_rays, n_ctrl, bins, 1, ray_seed, 1, with_target=False)
+    P = np.full((n_ctrl, n_ctrl), float(low))
+    P[split:, :] = float(high)
+    wl["lens"]["P"] = P
+    return wl
+
+
 def config(k, with_target=True):
     """The five workloads of the measurement plan, k = 1..5 (k = 5 is a list)."""
     if k == 1:

@@ -83,3 +83,18 @@ def test_options_marshalling_without_gpu(freeray):
         freeray.make_options(ray_order=torch.zeros(9, dtype=torch.int32))        # host memory
     with pytest.raises(ValueError):
         freeray.make_options(ray_order=torch.zeros(9, dtype=torch.int64))        # not 32-bit ids
+
+
+def test_ray_order_length_is_checked_against_the_problem(freeray):
+    import types
+    pb = types.SimpleNamespace(n_rays=10)
+    o = freeray.make_options()
+    freeray.Problem.check_options(pb, o)                  # no order: nothing to check
+    o.ray_order = 0x1000                                  # an address set without its length
+    with pytest.raises(ValueError):
+        freeray.Problem.check_options(pb, o)
+    o.ray_order_numel = 9                                 # built for 8 rays
+    with pytest.raises(ValueError):
+        freeray.Problem.check_options(pb, o)
+    o.ray_order_numel = 11                                # n_rays + 1
+    freeray.Problem.check_options(pb, o)

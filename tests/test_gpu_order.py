@@ -218,3 +218,22 @@ def test_full_size_point_workload_in_order():
     g_det = pb.adjoint(d, api.make_options(deterministic=True)).double().cpu().numpy()
     g_ord = pb.adjoint(d, api.make_options(ray_order=order)).double().cpu().numpy()
     assert rel_l2(g_ord, g_det) < 1e-5
+
+
+def test_full_size_grid_of_sources_float_matches_deterministic():
+    # the 64M-ray 8 x 8 grid of point sources as the optimisation step traces
+    # it (window form with u32 fixed point in shared memory, ray order) against
+    # the deterministic traces: the u32 quantum grows with the rays per CTA,
+    # and this is the largest single-lens workload
+    wl = W.config(4)
+    pb = api.Problem(wl)
+    order = pb.ray_order()
+    s0, s1 = api.new_stats(), api.new_stats()
+    E_det = pb.forward(api.make_options(deterministic=True), stats=s0).double().cpu().numpy()
+    E_ord = pb.forward(api.make_options(ray_order=order), stats=s1).double().cpu().numpy()
+    assert torch.equal(s0, s1)
+    assert rel_l2(E_ord, E_det) < 1e-5
+    d = torch.as_tensor(random_dLdE(wl, 11), dtype=torch.float32, device="cuda")
+    g_det = pb.adjoint(d, api.make_options(deterministic=True)).double().cpu().numpy()
+    g_ord = pb.adjoint(d, api.make_options(ray_order=order)).double().cpu().numpy()
+    assert rel_l2(g_ord, g_det) < 1e-5

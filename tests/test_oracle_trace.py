@@ -225,3 +225,34 @@ def test_root_is_the_smallest_positive_root(oracle):
         assert np.all(f[:-100] > 0.0)             # no earlier crossing
         checked += 1
     assert checked > 20
+
+
+def _crossings(spl, lens, o, d, t_end, n=20001):
+    """f(t) = Z - z on a dense grid of [0, t_end] (scipy's B-spline, not the oracle's)."""
+    ts = np.linspace(0.0, t_end, n)
+    u = np.clip((o[0] + d[0] * ts) / (2 * lens["rx"]) + 0.5, 0, 1)
+    v = np.clip((o[1] + d[1] * ts) / (2 * lens["ry"]) + 0.5, 0, 1)
+    return ts, spl(np.stack([u, v], axis=1)) - (o[2] + d[2] * ts)
+
+
+def test_root_is_the_first_of_several_on_a_wall_lens(oracle):
+    # A lens with a wall steeper than the rays: many rays cross the low part,
+    # pass under the wall and cross it again. The hit is the first crossing.
+    wl = W.wall_lens("wall", 1024)
+    lens = wl["lens"]
+    rec = oracle.trace_records(wl)
+    spl = NdBSpline((oracle.knots(lens["n1"], 3), oracle.knots(lens["n2"], 3)), lens["P"], 3)
+    zmax = lens["P"].max()
+    several = 0
+    for rid in range(1024):
+        r = rec[rid]
+        st, o, d, _ = oracle.point_ray(wl, rid)
+        if st != 0 or r["status"] not in (0, 3, 4):
+            continue
+        ts, f = _crossings(spl, lens, o, d, (zmax - o[2]) / d[2] * 1.001)
+        first = np.argmax(f <= 0.0)
+        assert f[first] <= 0.0 and np.all(f[:first] > 0.0)
+        assert ts[first - 1] <= r["t"] <= ts[first] + 1e-12       # the first sign change holds the root
+        if np.count_nonzero(np.diff(np.sign(f[first:])) != 0) > 0:
+            several += 1
+    assert several > 50

@@ -3,8 +3,9 @@ device memory (its scratch is a static device array inside the library).
 
 Checked through the C ABI against fr_trace_forward on two calls in a row, in
 float mode (within the irradiance tolerance of the parity tests) and in
-deterministic mode (bit for bit), and for the rejection of a problem larger
-than the static array. This file is collected last on purpose.
+deterministic mode (bit for bit), for flat and freeform entry faces and for a
+point-source grid beyond shared memory (the window form), and for the
+rejection of a problem larger than the static array. This file is collected last on purpose.
 """
 import ctypes as C
 
@@ -26,10 +27,22 @@ def _static_call(pb, options, E, stats=None, begin=0, count=api.ALL_RAYS):
         C.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
+def _workload(which):
+    if which == "collimated":
+        return W.config(1)
+    if which == "point":
+        return W.point("p", 6 * 4096, 24, 96, 4, 4, 4)
+    if which == "point-256":        # grid beyond shared memory: the window form in float mode
+        return W.point("p", 1 << 16, 24, 256, 4, 4, 4)
+    if which == "two-face-collimated":
+        return W.with_entry_face(W.collimated("c", 256, 8, 32, 1, 2), 6, 0.01, 9)
+    return W.with_entry_face(W.point("p", 1 << 15, 12, 32, 3, 4, 5), 6, 0.01, 9)
+
+
 @pytest.mark.parametrize("deterministic", [False, True])
-@pytest.mark.parametrize("which", ["collimated", "point"])
+@pytest.mark.parametrize("which", ["collimated", "point", "point-256", "two-face-collimated", "two-face-point"])
 def test_static_forward_matches_handle_forward_twice(deterministic, which):
-    wl = W.config(1) if which == "collimated" else W.point("p", 6 * 4096, 24, 96, 4, 4, 4)
+    wl = _workload(which)
     pb = api.Problem(wl)
     opt = api.make_options(deterministic=deterministic)
     ref_stats = api.new_stats()
