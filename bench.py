@@ -35,17 +35,19 @@ L2_FLUSH_BYTES = 256 << 20          # larger than the 129 MB L2
 # Algorithmic FP32 work per collimated ray, counted from the formulas the
 # kernels evaluate (FMA = 2 flops; +, -, *, exp2, rsqrt, reciprocal = 1):
 # forward = trace 62 + filter 46 + deposit 26; adjoint = trace 62 + filter 46
-# + reverse pass 161 + gradient moments 21 (breakdown in the design doc).
+# + reverse pass 161 + gradient moments 21.
 FLOPS_FWD_COLLIMATED = 134
 FLOPS_ADJ_COLLIMATED = 290
 # DRAM bytes (read + write) per launch of each trace kernel on this workload,
-# from the ncu capture summarised in profiles/trace_kernels_collimated_2048x2048.md.
+# from one ncu capture of the collimated 2048x2048 workload (dram__bytes_read.sum +
+# dram__bytes_write.sum of each trace kernel launch).
 # Set to None whenever the kernel changes after that capture.
 PROFILED_DRAM_BYTES = {"forward": 108544, "adjoint": 136192}
 
 
 # Per-ray work of each trace kernel on the cases of counting_cases(), from one
-# `ncu --metrics` capture of `python bench.py --counts` (profiles/trace_kernel_counts.md):
+# `ncu --metrics` capture of `python bench.py --counts` (the counts per launch divided by
+# the case's rays):
 #   warp: warp instructions issued; fp32: FP32 flops executed (FFMA 2, FADD and FMUL 1,
 #   their packed pairs twice that); xu: thread operations on the XU pipe (MUFU and
 #   conversions); satom: shared-memory atomic warp instructions. None where the kernels
@@ -391,7 +393,7 @@ def run_ours(args, rank, world, local):
         "peak_note": "issue: %d SMs x 4 warp instructions x %.0f MHz; FP32: %d SMs x 128 lanes x 2 flops x %.0f MHz "
                      "(max SM clock of the %s peaks file); XU and shared atomics: fr_probe kernels, this run"
                      % (sm_count, mhz, sm_count, mhz, pk_kind),
-        "counts_per_ray": "ncu instruction counts per ray (profiles/trace_kernel_counts.md)" if counts else None,
+        "counts_per_ray": "ncu instruction counts per ray of `bench.py --counts`" if counts else None,
         "probes": {k: v / 1e12 for k, v in ceil.items()}, "probe_unit": "T ops/s (FP32: TFLOP/s)",
         "per_kernel": per_kernel,
         "kernel_timing": "library events around each trace kernel in a second graph of the same step "

@@ -22,9 +22,13 @@
  *    is kept in the handle (fr_last_error). No exception crosses the ABI and no
  *    kernel traps: per-ray anomalies are counted in fr_stats.
  *  - Calls taking an fr_handle allocate device scratch memory in the handle the
- *    first time a larger problem is seen. That allocation is refused with
+ *    first time a larger problem is seen (the fixed-point accumulators, and for
+ *    a point source intersected by Newton a list of 4 bytes per traced ray: the
+ *    rays whose smallest root needs the certified march are traced again by a
+ *    second kernel right after the first). That allocation is refused with
  *    FR_ERR_WORKSPACE while `stream` is being captured into a CUDA graph, so a
- *    call of the same size must run once before capture.
+ *    call of the same size must run once before capture. A point-source call
+ *    traces at most 2^32 - 1 rays.
  *  - A handle is not thread-safe; use one handle per host thread.
  *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported;
  *    control nets from 4x4 to 32x32; filter sizes nu_x = nu_y in {1, 3, 5}.
@@ -124,9 +128,9 @@ typedef struct fr_options {
   int32_t deterministic;    /* 1: accumulate in int64 fixed point; results are bit-identical
                                from run to run and independent of the launch schedule */
   int32_t accumulate;       /* 1: add into E_out / dLdP_out instead of overwriting them */
-  int32_t newton_max_iter;  /* 0 -> 8: Newton iterations on the bracket that isolates the
-                               smallest root (Sec. 2.2.1; the certified march that finds the
-                               bracket takes at most 32 evaluations more) */
+  int32_t newton_max_iter;  /* 0 -> 8: Newton iterations towards the smallest root
+                               (Sec. 2.2.1; where the bounds cannot certify Newton's root the
+                               certified march takes at most 32 evaluations more) */
   float newton_tol;         /* 0 -> 1e-6, absolute, on the ray parameter */
   int32_t warps_per_cta;    /* 0 -> tuned; 1..32 */
   int32_t rays_per_lane;    /* 0 -> tuned; 1..64 */
@@ -162,7 +166,7 @@ typedef struct fr_stats {
 typedef struct fr_ray_record {
   int32_t status;        /* FR_RAY_* */
   int32_t span_i, span_j;/* knot span index of the freeform hit (u_i0 <= u < u_i0+1) */
-  int32_t newton_iters;  /* point source: Newton iterations used on the isolating bracket */
+  int32_t newton_iters;  /* point source: Newton iterations used */
   float u, v;            /* freeform hit, parameter space */
   float x, y, z;         /* freeform hit */
   float dx, dy, dz;      /* direction inside the glass */

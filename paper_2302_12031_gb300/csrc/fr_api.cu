@@ -43,7 +43,12 @@ struct NvtxRange {
 };
 
 constexpr size_t kAlign = 256;
-constexpr size_t kHeaderBytes = kAlign;   // reserved at the start of the workspace
+// Reserved at the start of the workspace: the counters of the deferred lists
+// (two words per item of a launch: the count and the deferred pass's CTA
+// ticket), zeroed when the workspace is allocated and left at zero by every
+// deferred pass.
+constexpr size_t kHeaderBytes = 4 * kAlign;
+static_assert(kHeaderBytes >= 2 * sizeof(uint32_t) * fr::kMaxItems, "deferred-list counters");
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -82,10 +87,15 @@ fr_options defaults(const fr_options* o) {
 }
 
 // Per-item offsets into the workspace: the int64 accumulators of deterministic
-// mode and max |dL/dE|.
+// mode, max |dL/dE| and the deferred list of a point source (4 bytes a ray of
+// the call: the worst case, every ray deferred).
 struct ItemWs {
-  size_t efix, pfix, gmax, end;
+  size_t efix, pfix, gmax, defer, end;
 };
+
+// Whether the hot trace kernels may defer an item's rays (single-face point
+// sources intersected by Newton).
+bool may_defer(const Item& it) { return it.kind == FR_SOURCE_POINT && !it.two_face && it.mesh_nu == 0; }
 
 ItemWs plan(const Item& it, size_t at, bool det_fwd, bool det_adj) {
   ItemWs w;
@@ -95,6 +105,8 @@ ItemWs plan(const Item& it, size_t at, bool det_fwd, bool det_adj) {
   if (det_adj) at = align_up(at + (size_t)it.nparam * sizeof(unsigned long long));
   w.gmax = at;
   at = align_up(at + sizeof(float));
+  w.defer = at;
+  if (may_defer(it)) at = align_up(at + (it.ray_end - it.ray_begin) * sizeof(uint32_t));
   w.end = at;
   return w;
 }
@@ -115,6 +127,7 @@ fr_status ensure_workspace(fr_handle* h, size_t bytes, cudaStream_t st) {
   }
   const size_t want = std::max<size_t>(bytes, 1 << 20);
   FR_CUDA(h, cudaMalloc(&h->ws, want), "cudaMalloc(workspace)");
+  FR_CUDA(h, cudaMemset(h->ws, 0, kHeaderBytes), "cudaMemset(workspace header)");
   h->ws_bytes = want;
   return FR_OK;
 }
@@ -137,6 +150,8 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   if (begin > n_rays) return set_error(h, FR_ERR_INVALID_ARG, "ray_begin beyond n_rays");
   if (count == UINT64_MAX) count = n_rays - begin;
   if (count > n_rays - begin) return set_error(h, FR_ERR_INVALID_ARG, "ray range beyond n_rays");
+  if (S && S->kind == FR_SOURCE_POINT && count > 0xffffffffull)
+    return set_error(h, FR_ERR_UNSUPPORTED, "a point-source call traces at most 2^32 - 1 rays");
   if (!(T->Rx > 0.0f) || !(T->Ry > 0.0f) || !finite(T->Rx) || !finite(T->Ry) || !finite(T->z_screen))
     return set_error(h, FR_ERR_INVALID_ARG, "screen half-widths must be positive and finite");
   if (T->nx < 1 || T->ny < 1 || T->nx > 4096 || T->ny > 4096)
@@ -418,6 +433,8 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     it.Efix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].efix);
     it.Pfix = reinterpret_cast<unsigned long long*>(h->ws + ws[i].pfix);
     it.gmax = reinterpret_cast<float*>(h->ws + ws[i].gmax);
+    it.defer_n = reinterpret_cast<uint32_t*>(h->ws) + 2 * i;   // (item 0's also holds the pass's ticket)
+    if (may_defer(it)) it.defer = reinterpret_cast<uint32_t*>(h->ws + ws[i].defer);
     schedule_item(&it, warps, o);
     if (!adjoint) it.smem_hist = (window || batch_window[i]) ? 2 : (want_smem_hist(it, o, det) ? 1 : 0);
     smem = std::max(smem, adjoint ? fr::adj_smem_bytes(it, det) : fr::fwd_smem_bytes(it, det));
@@ -500,6 +517,20 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
                             : fr::launch_forward<CAP>(L, grid, smem, det, st,
                                                       h->pdl && h->pdl_early && !det && o.accumulate);
     if (e != cudaSuccess) return cuda_error(h, e, adjoint ? "adjoint kernel" : "forward kernel");
+    // The deferred pass: the rays whose intersection the hot kernel left to
+    // the march (none on most lenses: the pass then only reads its counters).
+    bool any_defer = false;
+    size_t tables = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+      any_defer |= L.items[i].defer != nullptr;
+      tables = std::max(tables, fr::lens_tables_bytes(items[i]));
+    }
+    if (any_defer) {
+      const int dgrid = std::max(1, h->sm_count * 2);
+      e = adjoint ? fr::launch_adjoint_deferred<CAP>(L, dgrid, tables, det, st)
+                  : fr::launch_forward_deferred<CAP>(L, dgrid, tables, det, st);
+      if (e != cudaSuccess) return cuda_error(h, e, "deferred trace kernel");
+    }
     if (o.event_end)
       FR_CUDA(h, cudaEventRecordWithFlags((cudaEvent_t)o.event_end, st, rec_flags), "cudaEventRecord");
   }
@@ -998,7 +1029,9 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
   else if (!o.accumulate) e = cudaMemsetAsync(it.E, 0, (size_t)cells * 4, st);
   if (e != cudaSuccess) return cuda_error(nullptr, e, "cudaMemsetAsync");
   if (it.max_ctas > 0) {
-    const int kinds = it.two_face ? 4 : (it.kind == FR_SOURCE_COLLIMATED ? 1 : 2);
+    // point sources march in the kernel: no deferred list (its worst case
+    // would not fit the static array)
+    const int kinds = it.two_face ? 4 : (it.kind == FR_SOURCE_COLLIMATED ? 1 : 8);
     const int occ = fr::forward_occupancy(warps * 32, smem, det, false, it.nu, kinds);
     if (occ <= 0 || smem + 1024 > (size_t)dev->smem_optin)
       return set_error(nullptr, FR_ERR_UNSUPPORTED, "trace kernel does not fit on an SM (%zu B shared)", smem);
@@ -1010,7 +1043,7 @@ extern "C" fr_status fr_trace_forward_static(const fr_lens_desc* lens, const fr_
     L.n_items = 1;
     L.warps = warps;
     L.items[0] = it;
-    e = fr::launch_forward<1>(L, it.cta_end, smem, det, st, false);
+    e = fr::launch_forward<1>(L, it.cta_end, smem, det, st, false, true);
     if (e != cudaSuccess) return cuda_error(nullptr, e, "forward kernel");
   }
   if (det) {

@@ -128,8 +128,9 @@ struct LensSmem {
   float4* patch;   // [nsu*nsv][4]: row e holds C[e][0..3] of Z = sum_{e,f} C[e][f] s^e t^f
   float4* bu;      // [nsu][4]: coefficients of N_{k+a}(s) in powers of s
   float4* bv;      // [nsv][4]
-  int* zkey;       // [2]: min and max control height (convex hull, Sec. 2.1.2) as
-                   // order-preserving integer keys (point sources only; see zbounds)
+  int* zkey;       // [4]: min and max control height (convex hull, Sec. 2.1.2) as
+                   // order-preserving integer keys, then the net's bounds on |Z_s|
+                   // and |Z_t| as float bits (point sources only; see zbounds, slopes)
   float4* hull;    // [nsu*nsv] (nets that rays must intersect): per patch (zmin, zmax, Bs, Bt),
                    // see patch_hull
 };
@@ -146,6 +147,13 @@ __device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((
 __device__ __forceinline__ void zbounds(const LensSmem& s, float* zmin, float* zmax) {
   *zmin = key_float(s.zkey[0]);
   *zmax = key_float(s.zkey[1]);
+}
+
+// Bounds on |dZ/ds| and |dZ/dt| (patch coordinates) over the whole net (valid
+// after build_net_tables for nets with hull tables).
+__device__ __forceinline__ void slopes(const LensSmem& s, float* gs, float* gt) {
+  *gs = __int_as_float(s.zkey[2]);
+  *gt = __int_as_float(s.zkey[3]);
 }
 
 // Bytes of one net's tables; `hull`: with the per-patch bounds of the
@@ -187,8 +195,9 @@ __device__ inline LensSmem carve_lens(unsigned char* base, int nsu, int nsv, boo
 // Along a line (s, t) = (s0 + a tau, t0 + b tau) this gives
 //   |d2Z/dtau2| <= Z_ss a^2 + 2 |Z_st| |a b| + Z_tt b^2 <= Bs a^2 + Bt b^2,
 // Bs = Mss + Mst, Bt = Mtt + Mst (2|ab| <= a^2 + b^2). The bounds are widened
-// a little for FP32 rounding. Returns (zmin, zmax, Bs, Bt).
-__device__ inline float4 patch_hull(const float (&C)[4][4]) {
+// a little for FP32 rounding. Returns (zmin, zmax, Bs, Bt); *ms, *mt bound
+// |Z_s| and |Z_t| on the patch (3 times the largest first difference).
+__device__ inline float4 patch_hull(const float (&C)[4][4], float* ms, float* mt) {
   float T[4][4], B[4][4];
   const float third = 1.0f / 3.0f;
 #pragma unroll
@@ -205,7 +214,7 @@ __device__ inline float4 patch_hull(const float (&C)[4][4]) {
     B[i][2] = fmaf(third, T[i][2], fmaf(2.0f * third, T[i][1], T[i][0]));
     B[i][3] = T[i][0] + T[i][1] + T[i][2] + T[i][3];
   }
-  float zmn = B[0][0], zmx = B[0][0], mss = 0.0f, mtt = 0.0f, mst = 0.0f, babs = 0.0f;
+  float zmn = B[0][0], zmx = B[0][0], mss = 0.0f, mtt = 0.0f, mst = 0.0f, babs = 0.0f, m1s = 0.0f, m1t = 0.0f;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -216,11 +225,15 @@ __device__ inline float4 patch_hull(const float (&C)[4][4]) {
       if (i < 2) mss = fmaxf(mss, fabsf(B[i + 2][j] - 2.0f * B[i + 1][j] + B[i][j]));
       if (j < 2) mtt = fmaxf(mtt, fabsf(B[i][j + 2] - 2.0f * B[i][j + 1] + B[i][j]));
       if (i < 3 && j < 3) mst = fmaxf(mst, fabsf(B[i + 1][j + 1] - B[i + 1][j] - B[i][j + 1] + B[i][j]));
+      if (i < 3) m1s = fmaxf(m1s, fabsf(B[i + 1][j] - B[i][j]));
+      if (j < 3) m1t = fmaxf(m1t, fabsf(B[i][j + 1] - B[i][j]));
     }
   const float pad = 4e-6f * (1.0f + babs);   // rounding of the conversions above
   mss = fmaf(6.0f, mss, 24.0f * pad);
   mtt = fmaf(6.0f, mtt, 24.0f * pad);
   mst = fmaf(9.0f, mst, 36.0f * pad);
+  *ms = fmaf(3.0f, m1s, 6.0f * pad);   // |Z_s| <= 3 max |b_{i+1,j} - b_ij|
+  *mt = fmaf(3.0f, m1t, 6.0f * pad);
   return make_float4(zmn - pad, zmx + pad, mss + mst, mtt + mst);
 }
 
@@ -234,6 +247,8 @@ __device__ inline void build_net_tables(const float* ctrl, int ncv, int nsu, int
   if (bounds && threadIdx.x == 0) {
     s.zkey[0] = 0x7fffffff;
     s.zkey[1] = (int)0x80000000;
+    s.zkey[2] = 0;   // +0.0f
+    s.zkey[3] = 0;
   }
   for (int q = threadIdx.x; q < nsu + nsv; q += blockDim.x) {
     const bool isu = q < nsu;
@@ -246,7 +261,7 @@ __device__ inline void build_net_tables(const float* ctrl, int ncv, int nsu, int
   }
   __syncthreads();
   const int npatch = nsu * nsv;
-  float zmn = INFINITY, zmx = -INFINITY;
+  float zmn = INFINITY, zmx = -INFINITY, gs = 0.0f, gt = 0.0f;
   for (int p = threadIdx.x; p < npatch; p += blockDim.x) {
     const int k = p / nsv, l = p - k * nsv;
     float T[4][4];   // T[a][f] = sum_b P[k+a][l+b] Bv_l[b][f]
@@ -278,7 +293,12 @@ __device__ inline void build_net_tables(const float* ctrl, int ncv, int nsu, int
         C[e][f] = fmaf(ue[e][0], T[0][f], fmaf(ue[e][1], T[1][f], fmaf(ue[e][2], T[2][f], ue[e][3] * T[3][f])));
       out[e] = make_float4(C[e][0], C[e][1], C[e][2], C[e][3]);
     }
-    if (s.hull) s.hull[p] = patch_hull(C);
+    if (s.hull) {
+      float ms, mt;
+      s.hull[p] = patch_hull(C, &ms, &mt);
+      gs = fmaxf(gs, ms);
+      gt = fmaxf(gt, mt);
+    }
   }
   if (bounds) {
 #pragma unroll
@@ -286,9 +306,21 @@ __device__ inline void build_net_tables(const float* ctrl, int ncv, int nsu, int
       zmn = fminf(zmn, __shfl_xor_sync(0xffffffffu, zmn, o));
       zmx = fmaxf(zmx, __shfl_xor_sync(0xffffffffu, zmx, o));
     }
+    gs = fmaxf(gs, __shfl_xor_sync(0xffffffffu, gs, 16));
+    gs = fmaxf(gs, __shfl_xor_sync(0xffffffffu, gs, 8));
+    gs = fmaxf(gs, __shfl_xor_sync(0xffffffffu, gs, 4));
+    gs = fmaxf(gs, __shfl_xor_sync(0xffffffffu, gs, 2));
+    gs = fmaxf(gs, __shfl_xor_sync(0xffffffffu, gs, 1));
+    gt = fmaxf(gt, __shfl_xor_sync(0xffffffffu, gt, 16));
+    gt = fmaxf(gt, __shfl_xor_sync(0xffffffffu, gt, 8));
+    gt = fmaxf(gt, __shfl_xor_sync(0xffffffffu, gt, 4));
+    gt = fmaxf(gt, __shfl_xor_sync(0xffffffffu, gt, 2));
+    gt = fmaxf(gt, __shfl_xor_sync(0xffffffffu, gt, 1));
     if ((threadIdx.x & 31) == 0 && zmn <= zmx) {
       atomicMin(&s.zkey[0], float_key(zmn));
       atomicMax(&s.zkey[1], float_key(zmx));
+      atomicMax(&s.zkey[2], __float_as_int(gs));   // non-negative floats order as their bits
+      atomicMax(&s.zkey[3], __float_as_int(gt));
     }
   }
   __syncthreads();
@@ -372,6 +404,11 @@ __device__ __forceinline__ void basis_eval(const float4* tab, float s, float N[4
 // ---------------------------------------------------------------------------
 // One ray up to the screen (Secs. 2.2-2.3); forward and adjoint run this code.
 // ---------------------------------------------------------------------------
+// Status of a ray whose intersection a hot trace kernel leaves to the deferred
+// pass (first_root<false> returned ROOT_DEFER); never reported: that pass
+// traces the ray again and counts its real status.
+constexpr int kRayDeferred = FR_RAY_NCAUSES - 1;
+
 struct RayFwd {
   int status;
   int iters;
@@ -690,7 +727,7 @@ struct NetLine {
   float ou, ov, du, dv, oz, dz;
 };
 
-enum { ROOT_FOUND = 0, ROOT_NONE = 1, ROOT_FAIL = 2 };
+enum { ROOT_FOUND = 0, ROOT_NONE = 1, ROOT_FAIL = 2, ROOT_DEFER = 3 };
 
 // Evaluations the march may take before Newton's bracket is found.
 constexpr int kMarchMax = 32;   // evaluations of the march, besides Newton's
@@ -884,24 +921,28 @@ __device__ __forceinline__ bool no_root_before(const float4* hull, int nsu, int 
 }
 
 // The smallest root of f on [ta, tb] (f(ta) >= 0), as first_root_march
-// defines it, found the quick way where that is safe: safeguarded Newton from
-// the middle of [ta, tb], when f(tb) <= 0 brackets a root, then the patch
-// bounds certify that no root lies before the one Newton found
-// (no_root_before); a ray that reaches a side of the domain with f > 0 is
-// certified the same way to cross nothing before it. Where a certificate fails
-// (the bounds cannot exclude a crossing, as on steep or strongly curved
-// surfaces) or Newton does not converge, the march decides.
-template <class Eval>
+// defines it, found the quick way where that is safe. When the net's slope
+// bounds (gs >= |Z_s|, gt >= |Z_t|) make f strictly decreasing along the
+// whole ray (gs |ds/dt| + gt |dt/dt| < d_z), f has at most one root: f(tb) > 0
+// at a side of the domain means none, else safeguarded Newton from the middle
+// of [ta, tb] finds it. Otherwise the patch bounds must certify the result
+// (no_root_before): that no root lies before the one Newton found, or before
+// the side. Where that fails, or Newton does not converge, the march decides
+// (MARCH), or the ray is handed back as ROOT_DEFER for a later pass that
+// marches (the hot kernels keep the march's code out of their loops).
+template <bool MARCH, class Eval>
 __device__ __forceinline__ int first_root(const float4* patch, const float4* hull, int nsu, int nsv, const NetLine& q,
-                                          float ta, float tb, bool tb_is_top, int newton_max, float tol, Eval eval,
-                                          float* t_out, float* fp_out, int* iters) {
+                                          float ta, float tb, bool tb_is_top, float gs, float gt, int newton_max,
+                                          float tol, Eval eval, float* t_out, float* fp_out, int* iters) {
+  const bool mono = fmaf(gs, fabsf(q.du * (float)nsu), gt * fabsf(q.dv * (float)nsv)) < 0.999f * q.dz;
   float f, g;
   bool bracketed = true;
   if (!tb_is_top) {   // the slab's top has f <= 0 (convex hull); a side of the domain may not
     eval(tb, &f, &g);
     bracketed = !(f > 0.0f);
-    // the ray leaves through the side with f > 0: no root if the bounds show none before
-    if (!bracketed && no_root_before(hull, nsu, nsv, q, ta, tb, f, g)) return ROOT_NONE;
+    // the ray leaves through the side with f > 0: no root if f is monotone, or
+    // if the bounds show none before
+    if (!bracketed && (mono || no_root_before(hull, nsu, nsv, q, ta, tb, f, g))) return ROOT_NONE;
   }
   if (bracketed) {
     float lo = ta, hi = tb;
@@ -921,16 +962,20 @@ __device__ __forceinline__ int first_root(const float4* patch, const float4* hul
       if (f > 0.0f) lo = t; else hi = t;
       if (step <= tol || f == 0.0f) converged = true;
     }
-    if (converged && no_root_before(hull, nsu, nsv, q, ta, t, 0.0f, g)) {
+    if (converged && (mono || no_root_before(hull, nsu, nsv, q, ta, t, 0.0f, g))) {
       *t_out = t;
       *fp_out = g;
       *iters = n;
       return ROOT_FOUND;
     }
   }
-  const int st = first_root_march(patch, hull, nsu, nsv, q, ta, tb, newton_max, tol, t_out, iters);
-  if (st == ROOT_FOUND) eval(*t_out, &f, fp_out);   // the caller's record at the root
-  return st;
+  if constexpr (!MARCH) {
+    return ROOT_DEFER;
+  } else {
+    const int st = first_root_march(patch, hull, nsu, nsv, q, ta, tb, newton_max, tol, t_out, iters);
+    if (st == ROOT_FOUND) eval(*t_out, &f, fp_out);   // the caller's record at the root
+    return st;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1132,6 +1177,7 @@ __device__ __forceinline__ void source_ray(const Item& it, uint64_t id, float* s
 // The ray inside the glass, from (ox, oy, oz) along (r.dx, r.dy, r.dz), meets
 // the exit freeform (a4): safeguarded Newton on f(t) bracketed by the convex
 // hull of the control heights (Sec. 2.1.2), or the triangle mesh; then a5-a6.
+template <bool MARCH>
 __device__ __forceinline__ void exit_hit(const Item& it, const LensSmem& ls, float ox, float oy, float oz, float zmin,
                                          float zmax, RayFwd& r) {
   // Bracket: the slab zmin <= z <= zmax, widened a little for FP32 rounding,
@@ -1184,10 +1230,13 @@ __device__ __forceinline__ void exit_hit(const Item& it, const LensSmem& ls, flo
   const NetLine q{ou, ov, du, dv, oz, r.dz};
   auto eval = [&](float t, float* fv, float* gv) { f_eval(it, ls, ou, ov, du, dv, oz, r.dz, t, r, fv, gv); };
   float t;
-  const int found = first_root(ls.patch, ls.hull, it.nsu, it.nsv, q, ta, tb, !(tb < t_hi), it.newton_max,
-                               it.newton_tol, eval, &t, &fp, &r.iters);
+  float gs, gt;
+  slopes(ls, &gs, &gt);
+  const int found = first_root<MARCH>(ls.patch, ls.hull, it.nsu, it.nsv, q, ta, tb, !(tb < t_hi), gs, gt,
+                                      it.newton_max, it.newton_tol, eval, &t, &fp, &r.iters);
   if (found == ROOT_NONE) { r.status = FR_RAY_OUT_OF_DOMAIN; return; }   // leaves the side first
   if (found == ROOT_FAIL) { r.status = FR_RAY_NEWTON_FAIL; return; }
+  if (found == ROOT_DEFER) { r.status = kRayDeferred; return; }
   r.tstar = t;
   r.gp = fp;
   r.u = fmaf(du, t, ou);
@@ -1200,6 +1249,7 @@ __device__ __forceinline__ void exit_hit(const Item& it, const LensSmem& ls, flo
 
 // Point source (a1, a2, a4-a6): Philox direction uniform in the cone, flat
 // entry face, Snell + Schlick into the glass, then the exit freeform.
+template <bool MARCH>
 __device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, uint64_t id, float zmin, float zmax,
                                             RayFwd& r) {
   r.iters = 0;
@@ -1215,7 +1265,7 @@ __device__ __forceinline__ void trace_point(const Item& it, const LensSmem& ls, 
   r.dz = sqrtf(fmaf(-eta1 * eta1, sphi * sphi, 1.0f));
   const float om2 = omc * omc;
   r.T1 = (1.0f - it.R0) * fmaf(-om2 * om2, omc, 1.0f);
-  exit_hit(it, ls, ox, oy, oz, zmin, zmax, r);
+  exit_hit<MARCH>(it, ls, ox, oy, oz, zmin, zmax, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -1301,8 +1351,10 @@ __device__ __forceinline__ void trace_two_face(const Item& it, const LensSmem& l
     auto eval = [&](float t, float* fv, float* gv) { f_eval_in(it, li, ou, ov, du, dv, it.pz, e.d0z, t, e, fv, gv); };
     float t;
     int iters_in = 0;
-    const int found = first_root(li.patch, li.hull, it.nsu_in, it.nsv_in, q, ta, tb, !(tb < t_hi), it.newton_max,
-                                 it.newton_tol, eval, &t, &fp, &iters_in);
+    float gs, gt;
+    slopes(li, &gs, &gt);
+    const int found = first_root<true>(li.patch, li.hull, it.nsu_in, it.nsv_in, q, ta, tb, !(tb < t_hi), gs, gt,
+                                       it.newton_max, it.newton_tol, eval, &t, &fp, &iters_in);
     if (found == ROOT_NONE) { r.status = FR_RAY_APERTURE_MISS; return; }   // leaves through the side first
     if (found == ROOT_FAIL) { r.status = FR_RAY_NEWTON_FAIL; return; }
     e.tin = t;
@@ -1332,7 +1384,7 @@ __device__ __forceinline__ void trace_two_face(const Item& it, const LensSmem& l
   r.T1 = (1.0f - it.R0) * fmaf(-om2 * om2, omc, 1.0f);
   float zmin, zmax;
   zbounds(ls, &zmin, &zmax);
-  exit_hit(it, ls, e.ox, e.oy, e.oz, zmin, zmax, r);
+  exit_hit<true>(it, ls, e.ox, e.oy, e.oz, zmin, zmax, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -1754,6 +1806,12 @@ struct OrderCursor {
     return (chunks + lanes - 1) / lanes * kOrderChunk * (uint64_t)warps * 32;
   }
 };
+
+// Appends ray `id` of a hot trace kernel to the item's deferred list.
+__device__ __forceinline__ void defer_ray(const Item& it, uint64_t id) {
+  const uint32_t slot = atomicAdd(it.defer_n, 1u);
+  it.defer[slot] = (uint32_t)(id - it.ray_begin);
+}
 
 // One thread of the item's first CTA adds the ordered aperture misses to the
 // CTA's cause counters (s_cnt may be null: no counts asked for).

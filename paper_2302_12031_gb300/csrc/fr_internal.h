@@ -43,6 +43,11 @@ struct Item {
   uint64_t seed, n_rays;
   uint64_t ray_begin, ray_end;  // rays traced by this call
   const uint32_t* order;        // point sources: the ray at position p is order[p] (NULL: p)
+  // Point sources in the hot trace kernels: rays whose intersection needs the
+  // march (first_root) are appended here, as offsets from ray_begin, for the
+  // deferred pass; defer_n[0] counts them (the deferred pass resets it).
+  uint32_t* defer;
+  uint32_t* defer_n;
   float omega0;                 // flux / n_rays
   // Screen and filter (Sec. 2.3).
   float z_screen, Rx, Ry;
@@ -115,8 +120,11 @@ size_t lens_tables_bytes(const Item& it);   // the lens tables part of it
 size_t adj_smem_bytes(const Item& it, bool det);
 
 // Launchers (return the CUDA error of the launch).
+// march: a single point-source lens whose intersections march in the kernel
+// (no deferred pass; the allocation-free entry point).
 template <int CAP>
-cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl);
+cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl,
+                           bool march = false);
 // Zeroes up to kMaxZero buffers (sizes in bytes) in one launch.
 constexpr int kMaxZero = 80;   // a batch's 64 grids and its dL/dP, with room
 struct ZeroList {
@@ -164,8 +172,16 @@ cudaError_t configure_adjoint(int optin);
 double probe_ops(int kind, int blocks, int threads, int iters);
 cudaError_t launch_probe(int kind, int blocks, int threads, int iters, float* out, int n_out, cudaStream_t st);
 
+// The deferred pass after a hot point-source trace launch (same Launch, det
+// and filter size): traces the items' deferred rays with the march.
+template <int CAP>
+cudaError_t launch_forward_deferred(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
+template <int CAP>
+cudaError_t launch_adjoint_deferred(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st);
+
 // Occupancy of the trace kernels for a block size and dynamic shared memory.
-// kinds: 1 collimated, 2 point source (single-lens launches); batches use both.
+// kinds: 1 collimated, 2 point source, 4 two-face lens, 8 point source marching in
+// the kernel (single-lens launches); batches use both of 1 and 2.
 int forward_occupancy(int threads, size_t smem, bool det, bool batch, int nu, int kinds);
 int adjoint_occupancy(int threads, size_t smem, bool det, bool batch, int nu, int kinds);
 

@@ -311,7 +311,11 @@ __device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, const LensS
       oc.advance();
       if (oc.valid()) next = __ldg(it.order + oc.p);
       RayFwd r;
-      trace_point(it, ls, id, zmin, zmax, r);
+      trace_point<false>(it, ls, id, zmin, zmax, r);
+      if (r.status == kRayDeferred) {
+        defer_ray(it, id);
+        continue;
+      }
       cnt.add(r.status, s_cnt);
       if (r.status == FR_RAY_ON_SCREEN) {
         basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
@@ -380,7 +384,11 @@ __device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, const LensS
       float Nv[4], dNv[4];
       for (uint64_t id = a; id < b; ++id) {
         RayFwd r;
-        trace_point(it, ls, id, zmin, zmax, r);
+        trace_point<false>(it, ls, id, zmin, zmax, r);
+        if (r.status == kRayDeferred) {
+          defer_ray(it, id);
+          continue;
+        }
         cnt.add(r.status, s_cnt);
         if (r.status == FR_RAY_ON_SCREEN) {
           basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
@@ -454,6 +462,72 @@ __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 32
   RayCount::publish(s_cnt, it.stats);
 }
 
+// The deferred pass of the adjoint: each item's deferred rays traced again
+// with the march, one ray per thread, reversed, and their dL/dP terms added
+// straight into global memory (the float gradient or the int64 accumulator at
+// the adjoint kernel's scale); statuses counted here; the last CTA resets the
+// lists' counters.
+template <int CAP, bool DET, int NU>
+__global__ void __launch_bounds__(256) k_adjoint_deferred(const __grid_constant__ Launch<CAP> L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  for (int ii = 0; ii < L.n_items; ++ii) {
+    const Item& it = L.items[ii];
+    if (!it.defer) continue;
+    const uint32_t n = *(volatile const uint32_t*)it.defer_n;
+    if (n == 0) continue;
+    const LensSmem ls = carve_exit(smem, it);
+    if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+    build_lens_tables(it, ls);   // ends with __syncthreads
+    float zmin, zmax;
+    zbounds(ls, &zmin, &zmax);
+    GradOut go;
+    go.sg_f = it.dLdP;
+    go.sg_q = it.Pfix;
+    go.fixP = 0.0f;
+    if constexpr (DET) {   // the scale of k_adjoint
+      const float unit = *it.gmax * it.fixP_unit;
+      int e = 0;
+      if (unit > 0.0f) frexpf(unit, &e);
+      go.fixP = unit > 0.0f ? ldexpf(1.0f, 40 - e) : 1.0f;
+    }
+    RayCount cnt;
+    cnt.on_screen = 0u;
+    unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+    GradAcc<DET> acc;
+    acc.k = -1;
+    GCache<NU> gc;
+    gc.ie = gc.je = -1;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      RayFwd r;
+      trace_point<true>(it, ls, it.ray_begin + it.defer[i], zmin, zmax, r);
+      cnt.add(r.status, cnt_dst);
+      if (r.status == FR_RAY_ON_SCREEN) {
+        float Nv[4], dNv[4];
+        basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+        adjoint_ray<NU, DET, false>(it, ls, r, gc, Nv, dNv, acc, go);
+      }
+    }
+    grad_flush<DET>(acc, it.ncv, go.sg_f, go.sg_q);
+    cnt.reduce_into(cnt_dst);
+    __syncthreads();
+    RayCount::publish(s_cnt, it.stats);
+    __syncthreads();   // the tables of the next item reuse the shared memory
+  }
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int done = atomicAdd(L.items[0].defer_n + 1, 1u);
+    s_last = done + 1 == gridDim.x;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < (unsigned int)L.n_items) {
+    const Item& it = L.items[threadIdx.x];
+    if (it.defer) *it.defer_n = 0u;
+    if (threadIdx.x == 0) L.items[0].defer_n[1] = 0u;
+  }
+}
+
 // Deterministic mode: int64 fixed point -> float gradient, with the scale the
 // adjoint kernel used (recomputed from the same device value).
 __global__ void k_grad_fix_to_float(const __grid_constant__ Item it, int accumulate) {
@@ -503,6 +577,24 @@ cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det
 template cudaError_t launch_adjoint<1>(const Launch<1>&, int, size_t, bool, cudaStream_t, bool);
 template cudaError_t launch_adjoint<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t, bool);
 
+template <int CAP>
+using AdjDeferredKernel = void (*)(Launch<CAP>);
+
+template <int CAP>
+AdjDeferredKernel<CAP> pick_adjoint_deferred(bool det, int nu) {
+  if (det) return nu == 1 ? k_adjoint_deferred<CAP, true, 1> : (nu == 3 ? k_adjoint_deferred<CAP, true, 3>
+                                                                          : k_adjoint_deferred<CAP, true, 5>);
+  return nu == 1 ? k_adjoint_deferred<CAP, false, 1> : (nu == 3 ? k_adjoint_deferred<CAP, false, 3>
+                                                                 : k_adjoint_deferred<CAP, false, 5>);
+}
+
+template <int CAP>
+cudaError_t launch_adjoint_deferred(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
+  return launch_k(pick_adjoint_deferred<CAP>(det, L.items[0].nu), dim3(grid), dim3(256), smem, st, false, L);
+}
+template cudaError_t launch_adjoint_deferred<1>(const Launch<1>&, int, size_t, bool, cudaStream_t);
+template cudaError_t launch_adjoint_deferred<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t);
+
 cudaError_t launch_grad_fix_to_float(const Item& it, int accumulate, cudaStream_t st) {
   const int n = it.nparam;
   k_grad_fix_to_float<<<(n + 255) / 256, 256, 0, st>>>(it, accumulate);
@@ -531,6 +623,8 @@ cudaError_t configure_adjoint(int optin) {
       for (int kinds = 1; kinds <= 4; kinds *= 2)
         if ((e = allow_max_smem(pick_adjoint<1>(det != 0, nu, kinds), optin))) return e;
       if ((e = allow_max_smem(pick_adjoint<kMaxItems>(det != 0, nu, 3), optin))) return e;
+      if ((e = allow_max_smem(pick_adjoint_deferred<1>(det != 0, nu), optin))) return e;
+      if ((e = allow_max_smem(pick_adjoint_deferred<kMaxItems>(det != 0, nu), optin))) return e;
     }
   return cudaSuccess;
 }

@@ -189,9 +189,11 @@ __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const T
 
 // KINDS: bit 0 = the kernel handles collimated items, bit 1 = point-source items.
 // KINDS bit 2: the kernel also handles two-face lenses (entry tables in li).
+// KINDS bit 3: point-source intersections march in the kernel (no deferred pass).
 template <int NU, bool DET, int KINDS>
 __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li, const Target& tg, uint64_t a,
                          uint64_t b, float zmin, float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb) {
+  constexpr bool MARCH = (KINDS & 8) != 0;
   // Kernels that take point-source items may run the window form (float mode).
   constexpr bool WINK = (KINDS & 2) != 0;
   FootAcc<NU, DET> acc;
@@ -235,7 +237,11 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
       oc.advance();
       if (oc.valid()) next = __ldg(it.order + oc.p);
       RayFwd r;
-      trace_point(it, ls, id, zmin, zmax, r);
+      trace_point<MARCH>(it, ls, id, zmin, zmax, r);
+      if (!MARCH && r.status == kRayDeferred) {
+        defer_ray(it, id);
+        continue;
+      }
       cnt.add(r.status, s_cnt);
       if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
     }
@@ -272,7 +278,11 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
     } else if (KINDS & 2) {
       for (uint64_t id = a; id < b; ++id) {
         RayFwd r;
-        trace_point(it, ls, id, zmin, zmax, r);
+        trace_point<MARCH>(it, ls, id, zmin, zmax, r);
+        if (!MARCH && r.status == kRayDeferred) {
+          defer_ray(it, id);
+          continue;
+        }
         cnt.add(r.status, s_cnt);
         if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
       }
@@ -291,8 +301,8 @@ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t
 // spill; those of size 5 spill 150-200 bytes at any two-CTA bound.
 template <int CAP, bool DET, int NU, int KINDS>
 __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? 384 : (DET ? 256 : 384))
-                                             : (KINDS == 2 ? (!DET && NU <= 3 ? 640 : 512) : 256),
-                                  KINDS == 2 ? 1 : 2)
+                                             : ((KINDS & 7) == 2 ? (!DET && NU <= 3 ? 640 : 512) : 256),
+                                  (KINDS & 7) == 2 ? 1 : 2)
     k_forward(const __grid_constant__ Launch<CAP> L) {
   pdl_trigger();   // the loss kernel may start launching; it waits for this one to end
   int ii = 0;
@@ -426,6 +436,65 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? 384 : (DET ? 256 : 384
   RayCount::publish(s_cnt, it.stats);
 }
 
+// The deferred pass of the forward trace: the rays of each item's deferred
+// list (hot kernel rays whose intersection needs the march) traced again with
+// the march, one ray per thread, deposited straight into global memory (float
+// atomics into E, or int64 into the fixed-point accumulator); their statuses
+// are counted here. The last CTA resets the lists' counters for the next call.
+template <int CAP, bool DET, int NU>
+__global__ void __launch_bounds__(256) k_forward_deferred(const __grid_constant__ Launch<CAP> L) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  for (int ii = 0; ii < L.n_items; ++ii) {
+    const Item& it = L.items[ii];
+    if (!it.defer) continue;
+    const uint32_t n = *(volatile const uint32_t*)it.defer_n;
+    if (n == 0) continue;
+    const LensSmem ls = carve_exit(smem, it);
+    if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+    build_lens_tables(it, ls);   // ends with __syncthreads
+    float zmin, zmax;
+    zbounds(ls, &zmin, &zmax);
+    Target tg;
+    tg.smem = false;
+    tg.win = false;
+    tg.vec = false;
+    tg.ncol = it.ncol;
+    tg.gl_f = it.E;
+    tg.gl_q = it.Efix;
+    Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
+    RayCount cnt;
+    cnt.on_screen = 0u;
+    unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+    FootAcc<NU, DET> acc;
+    acc.ie = -1;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      RayFwd r;
+      trace_point<true>(it, ls, it.ray_begin + it.defer[i], zmin, zmax, r);
+      cnt.add(r.status, cnt_dst);
+      if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, false>(it, r, tg, acc, bb);
+    }
+    acc_flush<NU, DET, false>(acc, tg, bb);
+    cnt.reduce_into(cnt_dst);
+    __syncthreads();
+    RayCount::publish(s_cnt, it.stats);
+    __syncthreads();   // the tables of the next item reuse the shared memory
+  }
+  // every CTA has read the counters: the last one resets them
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int done = atomicAdd(L.items[0].defer_n + 1, 1u);
+    s_last = done + 1 == gridDim.x;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < (unsigned int)L.n_items) {
+    const Item& it = L.items[threadIdx.x];
+    if (it.defer) *it.defer_n = 0u;
+    if (threadIdx.x == 0) L.items[0].defer_n[1] = 0u;
+  }
+}
+
 // The full record of every ray of [ray_begin, ray_end), one thread per ray.
 __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -453,7 +522,7 @@ __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, 
   } else {
     float zmin, zmax;
     zbounds(ls, &zmin, &zmax);
-    trace_point(it, ls, id, zmin, zmax, r);
+    trace_point<true>(it, ls, id, zmin, zmax, r);
   }
   fr_ray_record rec;
   rec.status = r.status;
@@ -504,6 +573,7 @@ template <>
 FwdKernel<1> pick_forward<1>(bool det, int nu, int kinds) {
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
   if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
+  if (kinds == 8) return det ? pick_nu<1, true, 10>(nu) : pick_nu<1, false, 10>(nu);  // point, march in the kernel
   return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
 }
 template <>
@@ -512,13 +582,33 @@ FwdKernel<kMaxItems> pick_forward<kMaxItems>(bool det, int nu, int) {
 }
 
 template <int CAP>
-cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl) {
+cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl,
+                           bool march) {
   const int threads = 32 * L.warps;
-  const int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
+  int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
+  if (march && kinds == 2) kinds = 8;
   return launch_k(pick_forward<CAP>(det, L.items[0].nu, kinds), dim3(grid), dim3(threads), smem, st, pdl, L);
 }
-template cudaError_t launch_forward<1>(const Launch<1>&, int, size_t, bool, cudaStream_t, bool);
-template cudaError_t launch_forward<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t, bool);
+template cudaError_t launch_forward<1>(const Launch<1>&, int, size_t, bool, cudaStream_t, bool, bool);
+template cudaError_t launch_forward<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t, bool, bool);
+
+template <int CAP>
+using FwdDeferredKernel = void (*)(Launch<CAP>);
+
+template <int CAP>
+FwdDeferredKernel<CAP> pick_forward_deferred(bool det, int nu) {
+  if (det) return nu == 1 ? k_forward_deferred<CAP, true, 1> : (nu == 3 ? k_forward_deferred<CAP, true, 3>
+                                                                          : k_forward_deferred<CAP, true, 5>);
+  return nu == 1 ? k_forward_deferred<CAP, false, 1> : (nu == 3 ? k_forward_deferred<CAP, false, 3>
+                                                                 : k_forward_deferred<CAP, false, 5>);
+}
+
+template <int CAP>
+cudaError_t launch_forward_deferred(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st) {
+  return launch_k(pick_forward_deferred<CAP>(det, L.items[0].nu), dim3(grid), dim3(256), smem, st, false, L);
+}
+template cudaError_t launch_forward_deferred<1>(const Launch<1>&, int, size_t, bool, cudaStream_t);
+template cudaError_t launch_forward_deferred<kMaxItems>(const Launch<kMaxItems>&, int, size_t, bool, cudaStream_t);
 
 cudaError_t launch_debug(const Item& it, fr_ray_record* out, cudaStream_t st) {
   const uint64_t n = it.ray_end - it.ray_begin;
@@ -551,9 +641,11 @@ cudaError_t configure_forward(int optin) {
   if ((e = allow_max_smem(k_debug, optin))) return e;
   for (int det = 0; det < 2; ++det)
     for (int nu = 1; nu <= 5; nu += 2) {
-      for (int kinds = 1; kinds <= 4; kinds *= 2)
+      for (int kinds = 1; kinds <= 8; kinds *= 2)
         if ((e = allow_max_smem(pick_forward<1>(det != 0, nu, kinds), optin))) return e;
       if ((e = allow_max_smem(pick_forward<kMaxItems>(det != 0, nu, 3), optin))) return e;
+      if ((e = allow_max_smem(pick_forward_deferred<1>(det != 0, nu), optin))) return e;
+      if ((e = allow_max_smem(pick_forward_deferred<kMaxItems>(det != 0, nu), optin))) return e;
     }
   return cudaSuccess;
 }

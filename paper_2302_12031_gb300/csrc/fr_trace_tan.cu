@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
       float zmin, zmax;
       zbounds(ls, &zmin, &zmax);
       if (it.order) id = __ldg(it.order + j);
-      trace_point(it, ls, id, zmin, zmax, r);
+      trace_point<true>(it, ls, id, zmin, zmax, r);
       m = 0u;
       if (r.status == FR_RAY_ON_SCREEN) {
         m = s_mask[r.k * it.nsv + r.l];

@@ -275,6 +275,10 @@ class OptimStep:
     def launches_per_step(self):
         n_items = len(self.problems)
         det = bool(self.options is not None and self.options.deterministic)
-        fwd = 1 + (n_items if det else 0)                 # trace (+ fixed->float)
-        adj = 1 + (2 * n_items if det else 0)             # trace (+ absmax, fixed->float)
+        mesh = bool(self.options is not None and self.options.mesh_nu > 0)
+        # point sources with a flat entry face, intersected by Newton: a deferred pass after each trace
+        deferred = int(not mesh and any(pb.source.kind == api.FR_SOURCE_POINT and pb.entry_shape is None
+                                        for pb in self.problems))
+        fwd = 1 + deferred + (n_items if det else 0)      # trace (+ deferred pass) (+ fixed->float)
+        adj = 1 + deferred + (2 * n_items if det else 0)  # trace (+ deferred pass) (+ absmax, fixed->float)
         return 1 + fwd + n_items + adj + 1                # clearing kernel + ... + one loss per lens + Adam
