@@ -42,7 +42,7 @@ FLOPS_ADJ_COLLIMATED = 290
 # from one ncu capture of the collimated 2048x2048 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of each trace kernel launch).
 # Set to None whenever the kernel changes after that capture.
-PROFILED_DRAM_BYTES = {"forward": 108544, "adjoint": 136192}
+PROFILED_DRAM_BYTES = {"forward": 130560, "adjoint": 139008}
 
 
 # Per-ray work of each trace kernel on the cases of counting_cases(), from one
@@ -52,7 +52,24 @@ PROFILED_DRAM_BYTES = {"forward": 108544, "adjoint": 136192}
 #   their packed pairs twice that); xu: thread operations on the XU pipe (MUFU and
 #   conversions); satom: shared-memory atomic warp instructions. None where the kernels
 #   changed after that capture.
-COUNTS_PER_RAY = None
+COUNTS_PER_RAY = {
+    "collimated_2048x2048": {
+        "forward": {"warp": 8.919, "fp32": 139.2, "xu": 19.87, "satom": 0.257},
+        "adjoint": {"warp": 14.673, "fp32": 280.3, "xu": 16.88, "satom": 0.153},
+    },
+    "point_4M": {
+        "forward": {"warp": 23.321, "fp32": 405.5, "xu": 39.05, "satom": 0.225},
+        "adjoint": {"warp": 48.029, "fp32": 716.4, "xu": 38.92, "satom": 0.554},
+    },
+    "grid_8x8_4M": {
+        "forward": {"warp": 28.072, "fp32": 403.6, "xu": 43.93, "satom": 0.250},
+        "adjoint": {"warp": 43.074, "fp32": 716.0, "xu": 43.28, "satom": 0.808},
+    },
+    "sweep_32_lenses_scaled": {
+        "forward": {"warp": 23.340, "fp32": 348.8, "xu": 33.98, "satom": 0.235},
+        "adjoint": {"warp": 40.370, "fp32": 607.5, "xu": 32.95, "satom": 0.550},
+    },
+}
 
 
 def parse():
@@ -446,9 +463,27 @@ def extra_workloads(args, flush, world, roof):
     from paper_2302_12031_gb300 import workloads as W
     out = {}
     k = max(3, args.steps // 4)
+    autotune_fields = ("warps_per_cta", "rays_per_lane", "ctas_per_sm", "batch_waves")
     for name, wls in (("point_16M", W.config(3)), ("grid_8x8_64M_batched_graph", W.config(4)),
                       ("sweep_32_lenses_batched_graph", W.config(5))):
-        st = step.OptimStep(wls, lr=1e-3, graph=True)      # point sources: traced in the coherent ray order
+        opts = {}
+        if name.startswith("sweep"):
+            # the batch's schedule (waves of CTAs, warps, rays per lane) from the autotuner,
+            # on the ray orders the step traces the point sources in
+            from paper_2302_12031_gb300 import autotune
+            pbs = [api.Problem(w) for w in wls]
+            orders = [pb.ray_order() if pb.source.kind == api.FR_SOURCE_POINT else None for pb in pbs]
+            cache = autotune.Cache()
+            sched = {}
+            for kind in ("forward", "adjoint"):
+                o = autotune.tune_batch(pbs, kind, orders, cache=cache, flush=flush)
+                opts[kind] = o
+                hit = cache.get(autotune.batch_key(pbs, kind, False, torch.cuda.get_device_name()))
+                sched[kind] = dict(hit)
+            del pbs, orders
+            torch.cuda.empty_cache()
+        st = step.OptimStep(wls, lr=1e-3, graph=True, options=opts.get("forward"),
+                            adj_options=opts.get("adjoint"))   # point sources: traced in the coherent ray order
         order_ms = None
         if any(o is not None for o in st.orders):
             # the orders depend on the sources and apertures only: built once per problem (time of the
@@ -465,6 +500,8 @@ def extra_workloads(args, flush, world, roof):
         rays_per_s, t = D.replica_throughput(rays, statistics.mean(ms) * 1e-3)
         out[name] = {"rays_per_step": rays, "ms_per_step": 1e3 * t, "rays_per_s": rays_per_s,
                      "steps_per_s": 1.0 / t, "lenses": len(st.problems)}
+        if opts:
+            out[name]["schedule"] = sched
         del st
         # the trace kernels of the same step, timed by library events in a second graph
         ev_f = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -472,8 +509,14 @@ def extra_workloads(args, flush, world, roof):
         for e in ev_f + ev_a:
             e.record()
         torch.cuda.synchronize()
-        st = step.OptimStep(wls, lr=1e-3, graph=True, options=api.make_options(events=ev_f),
-                            adj_options=api.make_options(events=ev_a))
+        def with_events(o, ev):
+            e = api.make_options(events=ev)
+            if o is not None:
+                for f in autotune_fields:
+                    setattr(e, f, getattr(o, f))
+            return e
+        st = step.OptimStep(wls, lr=1e-3, graph=True, options=with_events(opts.get("forward"), ev_f),
+                            adj_options=with_events(opts.get("adjoint"), ev_a))
         f_ms, a_ms = [], []
         for _ in range(k + 2):
             flush()

@@ -51,8 +51,9 @@
 extern "C" {
 #endif
 
-/* Version 2: fr_options.ray_order and window_cells, fr_batch_item.ray_order. */
-#define FR_ABI_VERSION 2
+/* Version 2: fr_options.ray_order and window_cells, fr_batch_item.ray_order.
+ * Version 3: fr_options.batch_waves (in place of a reserved word). */
+#define FR_ABI_VERSION 3
 
 typedef enum fr_status {
   FR_OK = 0,
@@ -154,7 +155,10 @@ typedef struct fr_options {
                                (FR_ERR_INVALID_ARG else); NULL: id order */
   int32_t window_cells;     /* hist_mode 3: at most this many cells in the window; 0 -> as
                                many as shared memory holds */
-  int32_t reserved[3];
+  int32_t batch_waves;      /* batched calls: the launch holds this many waves of CTAs (items
+                               get CTAs in proportion to their cost, so unequal items balance
+                               over the waves); 0 -> 8, at most 64 */
+  int32_t reserved[2];
 } fr_options;
 
 /* Per-cause ray counts (device, uint64). Kernels add to it; zero it first. */

@@ -53,7 +53,7 @@ class Options(C.Structure):
                 ("ctas_per_sm", C.c_int32), ("hist_mode", C.c_int32),
                 ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
                 ("mesh_nu", C.c_int32), ("mesh_nv", C.c_int32), ("ray_order", C.c_void_p),
-                ("window_cells", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("window_cells", C.c_int32), ("batch_waves", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Stats(C.Structure):
@@ -129,7 +129,7 @@ _SIGNATURES = {
 }
 
 _lib = None
-ABI_VERSION = 2   # FR_ABI_VERSION of include/freeray.h: the structures' layout
+ABI_VERSION = 3   # FR_ABI_VERSION of include/freeray.h: the structures' layout
 
 
 def lib():
@@ -338,7 +338,7 @@ def fr_trace_forward_static(lens, source, target, n_rays, seed, ray_begin, ray_c
 
 def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newton_tol=0.0, warps_per_cta=0,
                  rays_per_lane=0, ctas_per_sm=0, hist_mode=0, events=None, mesh=(0, 0), window_cells=0,
-                 ray_order=None):
+                 ray_order=None, batch_waves=0):
     """fr_options; `events` = (begin, end) torch.cuda.Event pair to time the trace kernel;
     `ray_order` = the tensor of Problem.ray_order() (the options hold a reference to it;
     copies of the structure made by ctypes do not); `window_cells` bounds the window of
@@ -354,6 +354,7 @@ def make_options(deterministic=False, accumulate=False, newton_max_iter=0, newto
     o.hist_mode = hist_mode
     o.mesh_nu, o.mesh_nv = mesh
     o.window_cells = window_cells
+    o.batch_waves = batch_waves
     if ray_order is not None:
         if ray_order.dtype != torch.int32 or not ray_order.is_cuda or not ray_order.is_contiguous():
             raise ValueError("ray_order must be a contiguous int32 CUDA tensor (uint32 ids)")

@@ -3,10 +3,13 @@
 For one problem it times a set of candidate schedules (warps per CTA, minimum
 rays per lane, CTAs per SM, histogram placement) of the forward and the adjoint
 trace kernels, each replayed from a CUDA graph with the kernel bracketed by the
-library's own events, and keeps the fastest. Choices are cached in a JSON file
-keyed by the device name and the problem's shape, so a problem of the same
-shape is not tuned twice.
+library's own events, and keeps the fastest; for a batch of lenses traced in
+one launch (tune_batch), the waves of CTAs the launch holds, warps per CTA,
+rays per lane and CTAs per SM. Choices are cached in a JSON file keyed by the
+device name and the problems' shapes, so a problem of the same shape is not
+tuned twice.
 """
+import hashlib
 import json
 import os
 import statistics
@@ -18,6 +21,7 @@ from . import api
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
 OPTION_FIELDS = ("warps_per_cta", "rays_per_lane", "ctas_per_sm", "hist_mode")
+BATCH_FIELDS = ("warps_per_cta", "rays_per_lane", "ctas_per_sm", "batch_waves")
 
 
 def problem_key(pb, kind, deterministic, device_name):
@@ -136,4 +140,59 @@ def tune(pb, kind="forward", deterministic=False, reps=7, cache=None, flush=None
         timings.append((cand, t))
     best, t = pick_best(timings)
     cache.put(key, dict(best, ms=t))
+    return api.make_options(deterministic=deterministic, **best)
+
+
+def batch_key(problems, kind, deterministic, device_name):
+    """Cache key of a batch: the hash of its problems' keys, in order."""
+    joined = "/".join(problem_key(pb, kind, deterministic, device_name) for pb in problems)
+    return "batch|%s|%s|%d|%s" % (device_name, kind, int(deterministic), hashlib.sha1(joined.encode()).hexdigest())
+
+
+def batch_candidates():
+    """Schedules of a batched launch worth trying; the first is the library default
+    (eight waves of CTAs, 8 warps, the kernels' occupancy)."""
+    out = [dict(warps_per_cta=0, rays_per_lane=0, ctas_per_sm=0, batch_waves=0)]
+    for waves in (4, 8, 16, 32):
+        for warps in (4, 8):
+            for rpl in (0, 16):
+                out.append(dict(warps_per_cta=warps, rays_per_lane=rpl, ctas_per_sm=0, batch_waves=waves))
+    return out
+
+
+def tune_batch(problems, kind="forward", orders=None, deterministic=False, reps=5, cache=None, flush=None, h=None):
+    """Best fr_options for tracing `problems` (api.Problem list) in one batched launch;
+    `orders`: their ray orders (None entries for id order), as the optimisation step traces them."""
+    h = h or api.default_handle()
+    cache = cache if cache is not None else Cache()
+    name = torch.cuda.get_device_name()
+    key = batch_key(problems, kind, deterministic, name)
+    hit = cache.get(key)
+    if hit is not None:
+        return api.make_options(deterministic=deterministic, **{k: hit[k] for k in BATCH_FIELDS})
+    orders = orders if orders is not None else [None] * len(problems)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for e in ev:
+        e.record()
+    bufs = []
+    for pb in problems:
+        if kind == "forward":
+            bufs.append(dict(E=torch.zeros(pb.ext_shape, dtype=torch.float32, device=pb.device)))
+        else:
+            bufs.append(dict(dLdE=torch.randn(pb.ext_shape, dtype=torch.float32, device=pb.device),
+                             dLdP=torch.zeros(pb.n_params(), dtype=torch.float32, device=pb.device)))
+    items = [pb.batch_item(ray_order=o, **b) for pb, o, b in zip(problems, orders, bufs)]
+    timings = []
+    for cand in batch_candidates():
+        opt = api.make_options(deterministic=deterministic, events=ev, **cand)
+        fn = api.fr_trace_batch_forward if kind == "forward" else api.fr_trace_batch_adjoint
+        call = lambda: fn(h, items, opt)
+        try:
+            t = _time_kernel(call, ev, reps, flush)
+        except api.FreerayError:
+            t = None
+        timings.append((cand, t))
+    best, t = pick_best(timings)
+    default_ms = timings[0][1]
+    cache.put(key, dict(best, ms=t, default_ms=default_ms))
     return api.make_options(deterministic=deterministic, **best)

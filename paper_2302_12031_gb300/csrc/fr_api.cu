@@ -267,8 +267,8 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   it->newton_tol = o.newton_tol;
   if (o.mesh_nu < 0 || o.mesh_nu > 64 || o.mesh_nv < 0 || o.mesh_nv > 64 || (o.mesh_nu > 0) != (o.mesh_nv > 0))
     return set_error(h, FR_ERR_INVALID_ARG, "mesh_nu, mesh_nv must both be 0 or both 1..64");
-  if (o.hist_mode < 0 || o.hist_mode > 3 || o.window_cells < 0)
-    return set_error(h, FR_ERR_INVALID_ARG, "hist_mode must be 0..3 and window_cells >= 0");
+  if (o.hist_mode < 0 || o.hist_mode > 3 || o.window_cells < 0 || o.batch_waves < 0)
+    return set_error(h, FR_ERR_INVALID_ARG, "hist_mode must be 0..3, window_cells and batch_waves >= 0");
   if (o.ray_order) {
     if (it->kind != FR_SOURCE_POINT)
       return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to point sources");
@@ -487,7 +487,8 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
     // idle until the longest CTA ends (32-lens sweep step: 27.4 ms with one
     // wave and the other batch changes undone, 13.4 ms with four waves, 12.9
     // with eight, 13.0 with sixteen).
-    const int want = std::max<int>(1, h->sm_count * per_sm * (items.size() > 1 ? kBatchWaves : 1));
+    const int waves = o.batch_waves > 0 ? std::min(o.batch_waves, 64) : kBatchWaves;
+    const int want = std::max<int>(1, h->sm_count * per_sm * (items.size() > 1 ? waves : 1));
     if (items.size() == 1) {
       items[0].cta_begin = 0;
       items[0].cta_end = std::min(want, items[0].max_ctas);

@@ -1481,23 +1481,30 @@ __device__ __forceinline__ bool footprint_scalar(const Item& it, float X, float 
 template <int NU>
 __device__ __forceinline__ void filter_grad(const Item& it, const Foot<NU>& f, float (&Fx)[NU], float (&Fy)[NU],
                                             float (&gxa)[NU], float (&gya)[NU]) {
+  // The x and y axes as packed FP32 pairs: each lane of a pair rounds as the
+  // scalar operation would.
   const float ln2 = 0.69314718055994531f;
-  const float kx = -2.0f * (it.ax * ln2) * it.inv_wx, ky = -2.0f * (it.ay * ln2) * it.inv_wy;
-  float Spx = 0.0f, Spy = 0.0f;
+  const float2 k2 = make_float2(-2.0f * (it.ax * ln2) * it.inv_wx, -2.0f * (it.ay * ln2) * it.inv_wy);
+  const float2 d0 = make_float2(f.dx0, f.dy0), rs = make_float2(f.rsx, f.rsy), cut = make_float2(it.cut, it.cut);
+  float2 Sp = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    const float dxa = f.dx0 - (float)a, dya = f.dy0 - (float)a;
-    gxa[a] = f.fx[a] != 0.0f ? kx * dxa * (f.fx[a] + it.cut) : 0.0f;
-    gya[a] = f.fy[a] != 0.0f ? ky * dya * (f.fy[a] + it.cut) : 0.0f;
-    Spx += gxa[a];
-    Spy += gya[a];
-    Fx[a] = f.fx[a] * f.rsx;
-    Fy[a] = f.fy[a] * f.rsy;
+    const float2 fa = make_float2(f.fx[a], f.fy[a]);
+    const float2 d = __fadd2_rn(d0, make_float2(-(float)a, -(float)a));
+    const float2 g = __fmul2_rn(__fmul2_rn(k2, d), __fadd2_rn(fa, cut));
+    gxa[a] = f.fx[a] != 0.0f ? g.x : 0.0f;
+    gya[a] = f.fy[a] != 0.0f ? g.y : 0.0f;
+    Sp = __fadd2_rn(Sp, make_float2(gxa[a], gya[a]));
+    const float2 F = __fmul2_rn(fa, rs);
+    Fx[a] = F.x;
+    Fy[a] = F.y;
   }
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    gxa[a] = NU == 1 ? 0.0f : (gxa[a] - Fx[a] * Spx) * f.rsx;
-    gya[a] = NU == 1 ? 0.0f : (gya[a] - Fy[a] * Spy) * f.rsy;
+    // (g - F S') / S, with the product fused as in the scalar form
+    const float2 v = __fmul2_rn(__ffma2_rn(make_float2(-Fx[a], -Fy[a]), Sp, make_float2(gxa[a], gya[a])), rs);
+    gxa[a] = NU == 1 ? 0.0f : v.x;
+    gya[a] = NU == 1 ? 0.0f : v.y;
   }
 }
 
@@ -1506,24 +1513,26 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, 
                                             const float (&G)[NU][NU], float* zeta, float* Zs_bar, float* Zt_bar) {
   float Fx[NU], Fy[NU], gxa[NU], gya[NU];
   filter_grad<NU>(it, f, Fx, Fy, gxa, gya);
-  float wbar = 0.0f, Xs = 0.0f, Ys = 0.0f;
+  // the footprint contractions, (A, B) and (wbar, Xs) as packed pairs
+  float2 WX = make_float2(0.0f, 0.0f);
+  float Ys = 0.0f;
 #pragma unroll
   for (int a = 0; a < NU; ++a) {
-    float A = 0.0f, B = 0.0f;
+    float2 AB = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int b = 0; b < NU; ++b) {
-      A = fmaf(G[b][a], Fy[b], A);
-      B = fmaf(G[b][a], gya[b], B);
-    }
-    wbar = fmaf(A, Fx[a], wbar);
-    Xs = fmaf(A, gxa[a], Xs);
-    Ys = fmaf(B, Fx[a], Ys);
+    for (int b = 0; b < NU; ++b) AB = __ffma2_rn(make_float2(G[b][a], G[b][a]), make_float2(Fy[b], gya[b]), AB);
+    WX = __ffma2_rn(make_float2(AB.x, AB.x), make_float2(Fx[a], gxa[a]), WX);
+    Ys = fmaf(AB.y, Fx[a], Ys);
   }
+  float wbar = WX.x;
+  const float Xs = WX.y;
   const float K = r.w * it.inv_area;
   wbar *= it.inv_area;
-  const float Xbar = K * Xs, Ybar = K * Ys;
+  const float2 XYbar = __fmul2_rn(make_float2(K, K), make_float2(Xs, Ys));
+  const float Xbar = XYbar.x, Ybar = XYbar.y;
   // Propagation X = x + lam t_x, lam = (z_s - z)/t_z.
-  const float txb = r.lam * Xbar, tyb = r.lam * Ybar;
+  const float2 txyb = __fmul2_rn(make_float2(r.lam, r.lam), XYbar);
+  const float txb = txyb.x, tyb = txyb.y;
   const float lamb = fmaf(Xbar, r.tx, Ybar * r.ty);
   const float inv_tz = fast_rcp(r.tz);
   const float tzb = -lamb * r.lam * inv_tz;

@@ -188,17 +188,24 @@ __device__ __forceinline__ void adjoint_ray_moments(const Item& it, const LensSm
     m.M0 = m.M1 = m.M2 = m.M3 = m.D0 = m.D1 = m.D2 = m.Q0 = m.Q1 = m.Q2 = m.Q3 = 0.0f;
   }
   const float s = r.s, s2 = s * s, s3 = s2 * s;
-  m.M0 += zeta;
-  m.M1 = fmaf(zeta, s, m.M1);
-  m.M2 = fmaf(zeta, s2, m.M2);
-  m.M3 = fmaf(zeta, s3, m.M3);
-  m.D0 += Zsb;
-  m.D1 = fmaf(Zsb, s, m.D1);
-  m.D2 = fmaf(Zsb, s2, m.D2);
+  // the same sums as packed pairs (each lane rounds as the scalar operation)
+  const float2 zd = make_float2(zeta, Zsb);
+  float2 v = __fadd2_rn(make_float2(m.M0, m.D0), zd);
+  m.M0 = v.x;
+  m.D0 = v.y;
+  v = __ffma2_rn(zd, make_float2(s, s), make_float2(m.M1, m.D1));
+  m.M1 = v.x;
+  m.D1 = v.y;
+  v = __ffma2_rn(zd, make_float2(s2, s2), make_float2(m.M2, m.D2));
+  m.M2 = v.x;
+  m.D2 = v.y;
+  v = __ffma2_rn(make_float2(zeta, Ztb), make_float2(s3, s3), make_float2(m.M3, m.Q3));
+  m.M3 = v.x;
+  m.Q3 = v.y;
+  v = __ffma2_rn(make_float2(Ztb, Ztb), make_float2(s, s2), make_float2(m.Q1, m.Q2));
+  m.Q1 = v.x;
+  m.Q2 = v.y;
   m.Q0 += Ztb;
-  m.Q1 = fmaf(Ztb, s, m.Q1);
-  m.Q2 = fmaf(Ztb, s2, m.Q2);
-  m.Q3 = fmaf(Ztb, s3, m.Q3);
 }
 
 // dL/dP_{k+a,l+b} += zeta N_a N_b + Zs_bar N'_a N_b + Zt_bar N_a N'_b at (s, t)

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(freeray):
 
 
 def test_abi_version_without_gpu(freeray):
-    assert freeray.fr_abi_version() == freeray.ABI_VERSION == 2
+    assert freeray.fr_abi_version() == freeray.ABI_VERSION == 3
 
 
 def test_null_handle_is_an_argument_error(freeray):

@@ -21,6 +21,13 @@ def test_cache_round_trip(tmp_path):
     assert autotune.Cache(str(tmp_path / "t.json")).get("k")["warps_per_cta"] == 8
 
 
+def test_batch_candidates_start_with_the_default():
+    cands = autotune.batch_candidates()
+    assert cands[0] == dict(warps_per_cta=0, rays_per_lane=0, ctas_per_sm=0, batch_waves=0)
+    assert all(set(c) == set(autotune.BATCH_FIELDS) for c in cands)
+    assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)      # no candidate twice
+
+
 def test_candidates_start_with_the_default():
     for kind in ("forward", "adjoint"):
         for src in (api.FR_SOURCE_COLLIMATED, api.FR_SOURCE_POINT):

@@ -15,7 +15,7 @@ from tests.gpu_helpers import TOL_E
 pytestmark = pytest.mark.gpu
 
 
-def _oracle_run(wl, n_steps, lr, loss="l2"):
+def _oracle_run(wl, n_steps, lr, loss="l2", eps=1e-8):
     P = wl["lens"]["P"].astype(np.float64).copy()
     m = np.zeros_like(P).ravel()
     v = np.zeros_like(P).ravel()
@@ -26,7 +26,7 @@ def _oracle_run(wl, n_steps, lr, loss="l2"):
         L, d = O.loss_l2(wl, E) if loss == "l2" else O.loss_frobenius(wl, E)
         losses.append(L)
         g = O.trace_gradient(wl, d, P=theta.reshape(P.shape))
-        O.adam_step(theta, m, v, g.ravel(), lr=lr, step=k)
+        O.adam_step(theta, m, v, g.ravel(), lr=lr, step=k, eps=eps)
     return np.array(losses), theta
 
 
@@ -79,3 +79,39 @@ def test_step_with_host_io(graph):
         a.attach_host_io(torch.zeros(a.n_params), None)          # not pinned
     with pytest.raises(ValueError):
         a.attach_host_io(None, torch.zeros(2, dtype=torch.float64).pin_memory())
+
+
+def test_batched_sweep_loss_curves_match_the_oracle():
+    # The design sweep's three smallest lenses (its nets, screens, sources and
+    # seeds, rays scaled down 256 times) optimised in one batched, graph-captured
+    # step: every lens's loss curve and heights against its own oracle run
+    # (Adam is elementwise, so the batch's one Adam over all heights is each
+    # lens's own Adam). With so few rays on 256 x 256 bins many heights have
+    # gradients near the FP32 rounding of the sums; Adam's eps is set to 1e-3 of
+    # the gradients' scale (on both sides), so that those are not driven by
+    # lr-sized steps whose sign is rounding.
+    sweep = W.design_sweep(32, seed=6, min_rays=1 << 12, max_rays=1 << 16)
+    wls = sorted(sweep, key=lambda w: w["n_rays"])[:3]
+    assert len({w["source"]["kind"] for w in sweep}) == 2
+    n_steps, lr = 20, 1e-3
+    scale = []
+    for wl in wls:
+        E, _ = O.trace_forward(wl)
+        _, d = O.loss_l2(wl, E)
+        scale.append(np.abs(O.trace_gradient(wl, d)).max())
+    eps = 1e-3 * min(scale)
+    st = step.OptimStep(wls, lr=lr, graph=True, eps=eps)
+    assert st.batched
+    curves = []
+    for _ in range(n_steps):
+        st.step()
+        curves.append(st.losses().numpy().copy())
+    curves = np.array(curves)                       # (steps, lenses)
+    at = 0
+    for k, wl in enumerate(wls):
+        o_losses, o_theta = _oracle_run(wl, n_steps, lr, eps=eps)
+        rel = np.abs(curves[:, k] - o_losses) / o_losses
+        assert rel.max() < 10 * TOL_E, (k, wl["name"], rel.max())
+        n = o_theta.size
+        assert np.abs(st.P[at:at + n].double().cpu().numpy() - o_theta).max() < 1e-4, k
+        at += n
