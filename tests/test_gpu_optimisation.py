@@ -86,21 +86,18 @@ def test_batched_sweep_loss_curves_match_the_oracle():
     # seeds, rays scaled down 256 times) optimised in one batched, graph-captured
     # step: every lens's loss curve and heights against its own oracle run
     # (Adam is elementwise, so the batch's one Adam over all heights is each
-    # lens's own Adam). With so few rays on 256 x 256 bins many heights have
-    # gradients near the FP32 rounding of the sums; Adam's eps is set to 1e-3 of
-    # the gradients' scale (on both sides), so that those are not driven by
-    # lr-sized steps whose sign is rounding.
+    # lens's own Adam). With about 0.07 rays per pixel, Adam steps of 1e-3
+    # (a tenth of the heights' spread) move footprints across pixel edges, where
+    # the loss is only C0, and the run is chaotic: the FP64 oracle itself,
+    # with its starting heights perturbed by 1e-7, ends 2-5e-2 away, and the
+    # FP32 gradients' 1e-4 differences grow about linearly with the step (at
+    # lr = 5e-5 to 1.1e-3 after 20 steps on the first lens). At lr = 2e-5 the
+    # losses still fall by 6-17% in 20 steps.
     sweep = W.design_sweep(32, seed=6, min_rays=1 << 12, max_rays=1 << 16)
     wls = sorted(sweep, key=lambda w: w["n_rays"])[:3]
     assert len({w["source"]["kind"] for w in sweep}) == 2
-    n_steps, lr = 20, 1e-3
-    scale = []
-    for wl in wls:
-        E, _ = O.trace_forward(wl)
-        _, d = O.loss_l2(wl, E)
-        scale.append(np.abs(O.trace_gradient(wl, d)).max())
-    eps = 1e-3 * min(scale)
-    st = step.OptimStep(wls, lr=lr, graph=True, eps=eps)
+    n_steps, lr = 20, 2e-5
+    st = step.OptimStep(wls, lr=lr, graph=True)
     assert st.batched
     curves = []
     for _ in range(n_steps):
@@ -109,7 +106,8 @@ def test_batched_sweep_loss_curves_match_the_oracle():
     curves = np.array(curves)                       # (steps, lenses)
     at = 0
     for k, wl in enumerate(wls):
-        o_losses, o_theta = _oracle_run(wl, n_steps, lr, eps=eps)
+        o_losses, o_theta = _oracle_run(wl, n_steps, lr)
+        assert o_losses[-1] < 0.97 * o_losses[0]
         rel = np.abs(curves[:, k] - o_losses) / o_losses
         assert rel.max() < 10 * TOL_E, (k, wl["name"], rel.max())
         n = o_theta.size
