@@ -1808,7 +1808,9 @@ struct OrderCursor {
       start();
     }
   }
-  // Most positions one CTA of `warps` warps can take (for fixed-point bounds).
+  // Most positions one CTA of `warps` warps can take (for fixed-point bounds);
+  // also a bound for the traces that deal groups of 32 chunks to the CTAs in
+  // turn (at most warps x that many chunks each).
   static __device__ __forceinline__ uint64_t max_per_cta(const Item& it, int warps) {
     const uint64_t lanes = (uint64_t)(it.cta_end - it.cta_begin) * (uint64_t)warps * 32;
     const uint64_t chunks = (ordered_hits(it) + kOrderChunk - 1) / kOrderChunk;

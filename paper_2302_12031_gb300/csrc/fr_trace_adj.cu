@@ -49,10 +49,46 @@ __device__ __forceinline__ void grad_flush(GradAcc<DET>& acc, int ncv, float* sg
   acc.k = -1;
 }
 
+// Float mode, called by all 32 lanes of a converged warp: the register sums of
+// the lanes that hold sums of the same patch as the first lane with sums are
+// added up by a reduce-scatter over the warp (16 shuffle rounds, after which
+// lane 2j holds the total of term j), one shared atomic per control point; the
+// other lanes flush their own.
+__device__ __forceinline__ void grad_flush_warp(GradAcc<false>& acc, int ncv, float* sg) {
+  const unsigned int full = 0xffffffffu;
+  const unsigned int key = acc.k >= 0 ? (((unsigned int)acc.k << 16) | (unsigned int)acc.l) : full;
+  const unsigned int with_sums = __ballot_sync(full, key != full);
+  if (with_sums == 0u) return;
+  const unsigned int key0 = __shfl_sync(full, key, __ffs(with_sums) - 1);
+  const int k0 = (int)(key0 >> 16), l0 = (int)(key0 & 0xffffu);
+  const unsigned int lane = threadIdx.x & 31u;
+  const bool mine = key == key0;
+  float v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {   // round 1: halves of the 16 terms over lane bit 4
+    const bool hi = (lane & 16u) != 0;
+    const float lo_t = mine ? acc.g[i >> 2][i & 3] : 0.0f;
+    const float hi_t = mine ? acc.g[(i + 8) >> 2][(i + 8) & 3] : 0.0f;
+    v[i] = (hi ? hi_t : lo_t) + __shfl_xor_sync(full, hi ? lo_t : hi_t, 16);
+  }
+#pragma unroll
+  for (int w = 4, bit = 8; w >= 1; w >>= 1, bit >>= 1) {
+    const bool hi = (lane & (unsigned int)bit) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) v[i] = (hi ? v[i + w] : v[i]) + __shfl_xor_sync(full, hi ? v[i] : v[i + w], bit);
+  }
+  const float tot = v[0] + __shfl_xor_sync(full, v[0], 1);
+  const int term = (int)(lane >> 1);   // lane bits 4..1 picked the term's bits 3..0
+  if ((lane & 1u) == 0u && tot != 0.0f) atomicAdd(sg + (k0 + (term >> 2)) * ncv + l0 + (term & 3), tot);
+  if (!mine) grad_flush<false>(acc, ncv, sg, nullptr);
+  acc.k = -1;
+}
+
 struct GradOut {
   float* sg_f;
   unsigned long long* sg_q;
   float fixP;
+  unsigned int* s_group;   // the CTA's next group of ordered chunks (shared memory)
 };
 
 // The footprint of dL/dE, re-read only when the footprint moves.
@@ -306,9 +342,46 @@ __device__ void run_adjoint_lane(const Item& it, const LensSmem& ls, const LensS
   acc.k = -1;
   GCache<NU> gc;
   gc.ie = gc.je = -1;
-  if ((KINDS & 2) && it.order) {
-    // Ray order: chunks dealt over the lanes (OrderCursor), next id loaded one
-    // ray ahead.
+  if ((KINDS & 2) && it.order && !DET) {
+    // Ray order, float mode: groups of 32 neighbouring chunks, CTA c of the
+    // item owning groups c, c + ctas, c + 2 ctas, ... and its warps taking
+    // them one at a time from a shared counter (the cost of a group varies
+    // with the region of the lens it covers; a fixed dealing leaves warps
+    // waiting on the slowest). The lanes walk their chunks of the group in
+    // step and the warp's sums are flushed together at the group's end. Next
+    // id loaded one ray ahead.
+    float Nv[4], dNv[4];
+    const uint64_t H = ordered_hits(it);
+    const uint64_t ctas = (uint64_t)(it.cta_end - it.cta_begin), cta = (uint64_t)((int)blockIdx.x - it.cta_begin);
+    const uint64_t lane = threadIdx.x & 31;
+    for (;;) {
+      unsigned int k = 0u;
+      if (lane == 0) k = atomicAdd(go.s_group, 1u);
+      const uint64_t c0 = (cta + (uint64_t)__shfl_sync(0xffffffffu, k, 0) * ctas) * 32;
+      if (c0 * kOrderChunk >= H) break;
+      const uint64_t p0 = (c0 + lane) * kOrderChunk, hi = min(p0 + kOrderChunk, H);
+      uint32_t next = p0 < hi ? __ldg(it.order + p0) : 0u;
+      for (uint64_t p = p0; p < hi; ++p) {
+        const uint64_t id = next;
+        if (p + 1 < hi) next = __ldg(it.order + p + 1);
+        RayFwd r;
+        trace_point<false>(it, ls, id, zmin, zmax, r);
+        if (r.status == kRayDeferred) {
+          defer_ray(it, id);
+          continue;
+        }
+        cnt.add(r.status, s_cnt);
+        if (r.status == FR_RAY_ON_SCREEN) {
+          basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+          adjoint_ray<NU, DET, false>(it, ls, r, gc, Nv, dNv, acc, go);
+        }
+      }
+      __syncwarp();
+      if constexpr (!DET) grad_flush_warp(acc, it.ncv, go.sg_f);
+    }
+  } else if ((KINDS & 2) && it.order) {
+    // Ray order, fixed point: chunks dealt far apart over the lanes
+    // (OrderCursor), next id loaded one ray ahead.
     float Nv[4], dNv[4];
     OrderCursor oc;
     oc.init(it, true);
@@ -421,7 +494,9 @@ __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 32
   const LensSmem ls = carve_exit(smem, it);
   const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;
   unsigned char* grad_raw = smem + tables_bytes(it);
+  __shared__ unsigned int s_group;
   GradOut go;
+  go.s_group = &s_group;
   go.sg_f = reinterpret_cast<float*>(grad_raw);
   go.sg_q = reinterpret_cast<unsigned long long*>(grad_raw);
   const int nctrl = it.nparam;
@@ -431,6 +506,7 @@ __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 32
   }
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) s_group = 0u;
   pdl_trigger();
   // Launched to overlap the previous kernel: dL/dE only after it ends; the
   // lens too unless the caller has said that kernel does not write it.
@@ -491,6 +567,7 @@ __global__ void __launch_bounds__(256) k_adjoint_deferred(const __grid_constant_
     GradOut go;
     go.sg_f = it.dLdP;
     go.sg_q = it.Pfix;
+    go.s_group = nullptr;
     go.fixP = 0.0f;
     if constexpr (DET) {   // the scale of k_adjoint
       const float unit = *it.gmax * it.fixP_unit;

@@ -192,7 +192,8 @@ __device__ __forceinline__ void deposit(const Item& it, const RayFwd& r, const T
 // KINDS bit 3: point-source intersections march in the kernel (no deferred pass).
 template <int NU, bool DET, int KINDS>
 __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li, const Target& tg, uint64_t a,
-                         uint64_t b, float zmin, float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb) {
+                         uint64_t b, float zmin, float zmax, RayCount& cnt, unsigned int* s_cnt, Bbox& bb,
+                         unsigned int* s_group) {
   constexpr bool MARCH = (KINDS & 8) != 0;
   // Kernels that take point-source items may run the window form (float mode).
   constexpr bool WINK = (KINDS & 2) != 0;
@@ -227,23 +228,35 @@ __device__ void run_lane(const Item& it, const LensSmem& ls, const LensSmem& li,
     }
   }
   if ((KINDS & 2) && it.order) {
-    // Ray order: chunks dealt over the lanes (OrderCursor); the next id is
+    // Ray order: groups of 32 neighbouring chunks, CTA c of the item owning
+    // groups c, c + ctas, c + 2 ctas, ... and its warps taking them one at a
+    // time from a shared counter (the cost of a group varies with the region
+    // of the lens it covers; a fixed dealing leaves warps waiting on the
+    // slowest); lane L of a warp walks chunk L of its group. The next id is
     // loaded one ray ahead, its latency hidden behind the current ray's trace.
-    OrderCursor oc;
-    oc.init(it, false);
-    uint32_t next = oc.valid() ? __ldg(it.order + oc.p) : 0u;
-    while (oc.valid()) {
-      const uint64_t id = next;
-      oc.advance();
-      if (oc.valid()) next = __ldg(it.order + oc.p);
-      RayFwd r;
-      trace_point<MARCH>(it, ls, id, zmin, zmax, r);
-      if (!MARCH && r.status == kRayDeferred) {
-        defer_ray(it, id);
-        continue;
+    const uint64_t H = ordered_hits(it);
+    const uint64_t ctas = (uint64_t)(it.cta_end - it.cta_begin), cta = (uint64_t)((int)blockIdx.x - it.cta_begin);
+    const uint64_t lane = threadIdx.x & 31;
+    for (;;) {
+      __syncwarp();
+      unsigned int k = 0u;
+      if (lane == 0) k = atomicAdd(s_group, 1u);
+      const uint64_t c0 = (cta + (uint64_t)__shfl_sync(0xffffffffu, k, 0) * ctas) * 32;
+      if (c0 * kOrderChunk >= H) break;
+      const uint64_t p0 = (c0 + lane) * kOrderChunk, hi = min(p0 + kOrderChunk, H);
+      uint32_t next = p0 < hi ? __ldg(it.order + p0) : 0u;
+      for (uint64_t p = p0; p < hi; ++p) {
+        const uint64_t id = next;
+        if (p + 1 < hi) next = __ldg(it.order + p + 1);
+        RayFwd r;
+        trace_point<MARCH>(it, ls, id, zmin, zmax, r);
+        if (!MARCH && r.status == kRayDeferred) {
+          defer_ray(it, id);
+          continue;
+        }
+        cnt.add(r.status, s_cnt);
+        if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
       }
-      cnt.add(r.status, s_cnt);
-      if (r.status == FR_RAY_ON_SCREEN) deposit<NU, DET, WINK>(it, r, tg, acc, bb);
     }
   } else if ((KINDS & 1) && ((KINDS & 2) == 0 || it.kind == FR_SOURCE_COLLIMATED) && !it.jitter) {
     // cell centres in column lockstep (the lanes' shares are not lane_range's)
@@ -355,8 +368,10 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? 384 : (DET ? 256 : 384
   }
   __shared__ int s_bb[4];
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  __shared__ unsigned int s_group;
   if (threadIdx.x < 4) s_bb[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) s_group = 0u;
   if ((KINDS & 4) && it.two_face) build_two_face_tables(it, ls, li);   // ends with __syncthreads
   else build_lens_tables(it, ls);
   float zmin = 0.0f, zmax = 0.0f;
@@ -369,7 +384,7 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? 384 : (DET ? 256 : 384
   // for it before the first write to global memory, which with a shared
   // histogram is the final flush, else the first deposit.
   if (!tg.smem) pdl_wait();
-  run_lane<NU, DET, KINDS>(it, ls, li, tg, a, b, zmin, zmax, cnt, cnt_dst, bb);
+  run_lane<NU, DET, KINDS>(it, ls, li, tg, a, b, zmin, zmax, cnt, cnt_dst, bb, &s_group);
   cnt.reduce_into(cnt_dst);
   ordered_misses_into(it, cnt_dst);
   if (tg.smem) pdl_wait();
