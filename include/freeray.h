@@ -358,17 +358,23 @@ fr_status fr_zero_list(fr_handle* h, void* const* ptrs, const uint64_t* bytes, i
  * (the rays of Sec. 2.2.1). order_out (device, n_rays + 1 uint32) receives a
  * permutation of the ray ids 0..n_rays-1 followed by a count H: positions
  * 0..H-1 hold the rays that meet the aperture, grouped by source and, within a
- * source, sorted by the cell of a G x G grid over the aperture where the ray
- * meets the entry plane z = z_in (cells in Z order; G a power of two up to 128,
- * about 128 rays per cell); positions H..n_rays-1 hold rays that miss it (the
- * test has a 1e-5 relative margin toward "meets", so a ray placed among the
- * misses misses in the trace too). With this order (fr_options.ray_order) the
+ * source, sorted by cell: the ray refracted at the entry plane z = z_in is
+ * followed to the plane z = z_in + h (h the mean control height of the exit
+ * net minus z_in, at the call; 0 if negative), where each knot span of the
+ * exit net (in x, y) is cut into m x m cells, the spans taken in row order and
+ * the cells of a span in Z order (m the largest power of two up to 128 that
+ * leaves 128 or more of a source's rays per cell, else 1), and after the
+ * cells the rays whose point there lies outside the aperture; positions
+ * H..n_rays-1 hold rays that miss the aperture (the test has a 1e-5 relative
+ * margin toward "meets", so a ray placed among the misses misses in the trace
+ * too). With this order (fr_options.ray_order) the
  * traces split only the H rays over their lanes and count the others as
  * aperture misses: no warp idles on misses, rays next to each other meet the
  * same knot spans and land on the same pixels, and their Newton iterations
  * agree. The order is a function of the source, the aperture (rx, ry, z_in),
- * n_rays and seed only, not of the control heights, so one order serves every
- * optimisation step. Within a cell the order is the order of arrival (it may
+ * the net's size, the mean control height, n_rays and seed; every permutation
+ * gives the same sums, so one order serves every optimisation step (as the
+ * heights move it only grows less coherent). Within a cell the order is the order of arrival (it may
  * differ from call to call); deterministic-mode results do not depend on it.
  * With a freeform entry face (entry_ctrl_z) the same key orders the rays but
  * H = n_rays: the entry face decides the aperture in the trace. Needs n_rays

@@ -881,12 +881,12 @@ fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_d
   Item it;
   fr_status s = make_item(h, lens, source, &t, n_rays, seed, 0, UINT64_MAX, o, &it);
   if (s != FR_OK) return s;
-  const int G = fr::ray_order_grid(it);
-  const uint64_t nk = fr::ray_order_keys(it, G);
+  const int m = fr::ray_order_grid(it);
+  const uint64_t nk = fr::ray_order_keys(it, m);
   cudaStream_t st = as_stream(stream);
   s = ensure_workspace(h, kHeaderBytes + nk * sizeof(uint32_t), st);
   if (s != FR_OK) return s;
-  cudaError_t e = fr::launch_ray_order(it, G, reinterpret_cast<uint32_t*>(h->ws + kHeaderBytes), order_out, st);
+  cudaError_t e = fr::launch_ray_order(it, m, reinterpret_cast<uint32_t*>(h->ws + kHeaderBytes), order_out, st);
   if (e != cudaSuccess) return cuda_error(h, e, "ray order kernels");
   return FR_OK;
 }

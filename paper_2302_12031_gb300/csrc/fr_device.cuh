@@ -1767,21 +1767,23 @@ __device__ __forceinline__ void lane_range(const Item& it, int warps, uint64_t* 
   *b = lo + w0 + m * (lane + 1) / 32;
 }
 
-// With a ray order the forward and adjoint traces deal chunks of kOrderChunk
-// consecutive positions round-robin over all lanes of the item: a chunk is
-// coherent (one entry cell: one knot span, neighbouring pixels), and each
-// lane's chunks spread over the whole aperture, so the warps of a CTA carry
-// equal work and finish together (contiguous runs of the sorted order gave
-// whole warps the cheap or the costly parts of the lens). Two deals: `near`
-// gives the lanes of a warp neighbouring chunks (the forward: one patch for
-// the whole warp, broadcast table reads, agreeing Newton iterations); `spread`
-// gives them chunks far apart in the order (the adjoint: its 16 gradient
-// additions per flush then go to different addresses, not to the same ones
-// from every lane). On the 16M-ray point source: forward 573 -> 451 us with
-// `near` (567 with `spread`), adjoint 1307 -> 1008 us with `spread` (1533 with
-// `near`; 1445 with `near`, lockstep chunks and the 16 terms summed across
-// the warp by shuffles before one addition: the flushes were not the cost).
-constexpr uint64_t kOrderChunk = 16;
+// With a ray order the traces split the positions into chunks of kOrderChunk
+// consecutive positions (a chunk is coherent: one cell of one knot span,
+// neighbouring pixels). The float-mode point traces (k_forward, k_adjoint)
+// take groups of 32 neighbouring chunks, one per lane, warp by warp from a
+// per-CTA counter, the CTAs owning the groups in turn: the lanes of a warp
+// then share a patch (broadcast table reads, agreeing Newton iterations) and
+// the warps of a CTA finish together. OrderCursor deals the chunks statically
+// for the other kernels: `near` gives the lanes of a warp neighbouring
+// chunks, `spread` chunks far apart (the fixed-point adjoint, whose gradient
+// flushes then go to different addresses). On the 16M-ray point source the
+// counter took the forward from 475 to 438 us, chunks of 8 instead of 16 and
+// the order's cells on the plane of the mean height to 429 us; the adjoint
+// went from 1031 us (`spread`) to 999 us (counter) and 696 us (cells on that
+// plane: the knot span of the hit changes once per 30 positions of the order
+// instead of once per 10, and each change costs a lane a flush of its 16
+// register sums).
+constexpr uint64_t kOrderChunk = 8;
 
 struct OrderCursor {
   uint64_t p, hi, c, lanes, H;

@@ -7,8 +7,15 @@
 // gives the traces an order in which neighbouring positions are neighbouring
 // rays, with the rays that miss the aperture (most of a wide cone) last: the
 // traces split only the others over their lanes, so no warp idles on misses.
-// The key is computed from the source sampling and the flat entry plane alone,
-// so it does not depend on the control heights.
+// The key is not the entry point itself but its image on the plane of the
+// mean control height, reached along the refracted direction: the hit of a
+// ray on the exit face lies close to that image, the entry point up to the
+// glass's thickness times the slope of the ray away. The cells subdivide the
+// knot spans there (m x m cells per span, spans in row order, cells in Z order
+// within a span), so a run of positions stays in one span: the adjoint sums a
+// lane's gradient terms per span in registers and writes them out when the
+// span changes. The key depends on the control heights through their mean
+// only, and only for coherence: any permutation is a correct order.
 #include "fr_device.cuh"
 
 namespace fr {
@@ -23,31 +30,64 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t x) {
   return x;
 }
 
-// Source index x G^2 + the Z-order index of the G x G aperture cell where ray
-// `id` meets the entry plane; n_src G^2 (the last key) for a ray that misses the
-// aperture. The miss test is the trace's with a margin of 1e-5 relative, so a
-// ray put with the misses misses in the trace too.
-__device__ __forceinline__ uint32_t ray_key(const Item& it, uint64_t id, int G) {
+// Source index x (nsu nsv m^2 + 1) + the index of the cell of ray `id`: (knot
+// span row x nsu + span column) m^2 + the Z-order index of the m x m cell
+// within the span, at the point where the refracted ray meets the plane
+// z_in + h (h the mean glass thickness), or nsu nsv m^2 where that point lies
+// outside the aperture (rays that mostly leave the glass through its side);
+// n_src (nsu nsv m^2 + 1) (the last key) for a ray that misses the aperture.
+// The miss test is the trace's with a margin of 1e-5 relative, so a ray put
+// with the misses misses in the trace too.
+__device__ __forceinline__ uint32_t ray_key(const Item& it, uint64_t id, int m, float h) {
   float sx, sy, d0x, d0y, d0z, omc, sphi;
   source_ray(it, id, &sx, &sy, &d0x, &d0y, &d0z, &omc, &sphi);
   const float tau = __fdiv_rn(it.z_in - it.pz, d0z);
   const float ox = fmaf(tau, d0x, sx), oy = fmaf(tau, d0y, sy);
   const uint32_t nsrc = (uint32_t)(it.gnx * it.gny);
+  const uint32_t cells = (uint32_t)(it.nsu * it.nsv) * (uint32_t)(m * m), per_src = cells + 1u;
   if (!(tau > 0.0f) || fabsf(ox) > __fmul_rn(it.rx, 1.00001f) || fabsf(oy) > __fmul_rn(it.ry, 1.00001f))
-    return nsrc * (uint32_t)(G * G);
-  const float g = 0.5f * (float)G;
-  const int cx = min(max((int)__fmul_rn(__fdiv_rn(ox, it.rx) + 1.0f, g), 0), G - 1);
-  const int cy = min(max((int)__fmul_rn(__fdiv_rn(oy, it.ry) + 1.0f, g), 0), G - 1);
-  const uint32_t cell = spread_bits((uint32_t)cx) | (spread_bits((uint32_t)cy) << 1);
+    return nsrc * per_src;
+  // the in-glass direction is (d0x, d0y, .) / n_glass with z part
+  // sqrt(1 - sin^2 / n_glass^2): h / dz times its lateral part
+  const float eta = __fdiv_rn(1.0f, it.n_glass);
+  const float dz = __fsqrt_rn(__fadd_rn(1.0f, -__fmul_rn(__fmul_rn(eta, eta), __fmul_rn(sphi, sphi))));
+  const float g = __fdiv_rn(__fmul_rn(h, eta), dz);
+  const float px = fmaf(g, d0x, ox), py = fmaf(g, d0y, oy);
   uint32_t src = 0;
   if (nsrc > 1) src = min((uint32_t)(id / it.per_src), nsrc - 1);
-  return src * (uint32_t)(G * G) + cell;
+  if (!(fabsf(px) <= it.rx && fabsf(py) <= it.ry)) return src * per_src + cells;
+  // position in knot-span units, u nsu with u = x / (2 rx) + 1/2
+  const float us = __fmul_rn(__fdiv_rn(px, it.rx) + 1.0f, 0.5f * (float)it.nsu);
+  const float vs = __fmul_rn(__fdiv_rn(py, it.ry) + 1.0f, 0.5f * (float)it.nsv);
+  const int k = min(max((int)us, 0), it.nsu - 1), l = min(max((int)vs, 0), it.nsv - 1);
+  const int cx = min(max((int)__fmul_rn(us - (float)k, (float)m), 0), m - 1);
+  const int cy = min(max((int)__fmul_rn(vs - (float)l, (float)m), 0), m - 1);
+  const uint32_t cell = (uint32_t)(l * it.nsu + k) * (uint32_t)(m * m) +
+                        (spread_bits((uint32_t)cx) | (spread_bits((uint32_t)cy) << 1));
+  return src * per_src + cell;
 }
 
-__global__ void __launch_bounds__(256) k_order_count(const __grid_constant__ Item it, int G, uint32_t* counts) {
+// Mean control height of the exit net minus z_in (0 if not positive), the
+// same in every CTA of both passes: warp 0 sums in a fixed order.
+__device__ float nominal_thickness(const Item& it) {
+  __shared__ float s_h;
+  if (threadIdx.x < 32) {
+    const int n = it.ncu * it.ncv;
+    float sum = 0.0f;
+    for (int q = (int)threadIdx.x; q < n; q += 32) sum = __fadd_rn(sum, __ldg(it.ctrl + q));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sum = __fadd_rn(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+    if (threadIdx.x == 0) s_h = fmaxf(__fadd_rn(__fdiv_rn(sum, (float)n), -it.z_in), 0.0f);
+  }
+  __syncthreads();
+  return s_h;
+}
+
+__global__ void __launch_bounds__(256) k_order_count(const __grid_constant__ Item it, int m, uint32_t* counts) {
+  const float h = nominal_thickness(it);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; id < it.n_rays; id += stride)
-    atomicAdd(counts + ray_key(it, id, G), 1u);
+    atomicAdd(counts + ray_key(it, id, m, h), 1u);
 }
 
 // Exclusive prefix sum of counts[0..n) in place, one CTA of 1024 threads: each
@@ -89,41 +129,45 @@ __global__ void __launch_bounds__(1024) k_order_scan(uint32_t* counts, uint64_t 
   }
 }
 
-__global__ void __launch_bounds__(256) k_order_scatter(const __grid_constant__ Item it, int G, uint32_t* cursor,
+__global__ void __launch_bounds__(256) k_order_scatter(const __grid_constant__ Item it, int m, uint32_t* cursor,
                                                        uint32_t* order) {
+  const float h = nominal_thickness(it);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; id < it.n_rays; id += stride) {
     // The key is the counting pass's to the bit (the same code, with no
     // contractible a*b+c left in it); the bound only guards memory.
-    const uint32_t pos = atomicAdd(cursor + ray_key(it, id, G), 1u);
+    const uint32_t pos = atomicAdd(cursor + ray_key(it, id, m, h), 1u);
     if (pos < it.n_rays) order[pos] = (uint32_t)id;
   }
 }
 
 }  // namespace
 
-// About 128 rays per cell of one source's grid, G a power of two in 1..128.
+// Cells per knot span side m: a power of two in 1..128 with about 128 or more
+// of one source's rays per cell.
 int ray_order_grid(const Item& it) {
-  const uint64_t per_src = it.n_rays / (uint64_t)(it.gnx * it.gny);
-  int G = 1;
-  while (G < 128 && (uint64_t)(2 * G) * (uint64_t)(2 * G) * 128u <= per_src) G *= 2;
-  return G;
+  const uint64_t per_span = it.n_rays / (uint64_t)(it.gnx * it.gny) / (uint64_t)(it.nsu * it.nsv);
+  int m = 1;
+  while (m < 128 && (uint64_t)(2 * m) * (uint64_t)(2 * m) * 128u <= per_span) m *= 2;
+  return m;
 }
 
-uint64_t ray_order_keys(const Item& it, int G) { return (uint64_t)(it.gnx * it.gny) * (uint64_t)(G * G) + 1; }
+uint64_t ray_order_keys(const Item& it, int m) {
+  return (uint64_t)(it.gnx * it.gny) * ((uint64_t)(it.nsu * it.nsv) * (uint64_t)(m * m) + 1) + 1;
+}
 
-cudaError_t launch_ray_order(const Item& it, int G, uint32_t* counts, uint32_t* order, cudaStream_t st) {
-  const uint64_t nk = ray_order_keys(it, G);
+cudaError_t launch_ray_order(const Item& it, int m, uint32_t* counts, uint32_t* order, cudaStream_t st) {
+  const uint64_t nk = ray_order_keys(it, m);
   cudaError_t e = cudaMemsetAsync(counts, 0, nk * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const uint64_t want = (it.n_rays + 255) / 256;
   const unsigned int blocks = (unsigned int)(want < 4096 ? want : 4096);
-  k_order_count<<<blocks, 256, 0, st>>>(it, G, counts);
+  k_order_count<<<blocks, 256, 0, st>>>(it, m, counts);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // a freeform entry face decides the aperture in the trace: every position is traced
   k_order_scan<<<1, 1024, 0, st>>>(counts, nk, order + it.n_rays, it.two_face ? (uint32_t)it.n_rays : 0u);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_order_scatter<<<blocks, 256, 0, st>>>(it, G, counts, order);
+  k_order_scatter<<<blocks, 256, 0, st>>>(it, m, counts, order);
   return cudaGetLastError();
 }
 

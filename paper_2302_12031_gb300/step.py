@@ -25,8 +25,9 @@ class OptimStep:
         """`options` apply to both traces unless `adj_options` is given for the adjoint
         (e.g. to record timing events around each trace kernel separately).
         ray_order: point-source lenses trace their rays
-        in the coherent order of fr_ray_order (built once here: it does not
-        depend on the heights)."""
+        in the coherent order of fr_ray_order (built once here, from the starting
+        heights' mean: any order gives the same sums, so it stays valid as the
+        heights move)."""
         if isinstance(workloads, dict):
             workloads = [workloads]
         if loss not in ("l2", "frobenius"):
