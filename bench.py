@@ -42,7 +42,7 @@ FLOPS_ADJ_COLLIMATED = 290
 # from one ncu capture of the collimated 2048x2048 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of each trace kernel launch).
 # Set to None whenever the kernel changes after that capture.
-PROFILED_DRAM_BYTES = {"forward": 130560, "adjoint": 139008}
+PROFILED_DRAM_BYTES = {"forward": 116224, "adjoint": 137728}
 
 
 # Per-ray work of each trace kernel on the cases of counting_cases(), from one
@@ -55,19 +55,23 @@ PROFILED_DRAM_BYTES = {"forward": 130560, "adjoint": 139008}
 COUNTS_PER_RAY = {
     "collimated_2048x2048": {
         "forward": {"warp": 8.919, "fp32": 139.2, "xu": 19.87, "satom": 0.257},
-        "adjoint": {"warp": 14.673, "fp32": 280.3, "xu": 16.88, "satom": 0.153},
+        "adjoint": {"warp": 14.070, "fp32": 289.1, "xu": 17.86, "satom": 0.153},
+    },
+    "plain_256x256": {
+        "forward": {"warp": 10.591, "fp32": 147.6, "xu": 22.45, "satom": 0.244},
+        "adjoint": {"warp": 21.593, "fp32": 334.2, "xu": 19.53, "satom": 1.002},
     },
     "point_4M": {
-        "forward": {"warp": 23.321, "fp32": 405.5, "xu": 39.05, "satom": 0.225},
-        "adjoint": {"warp": 48.029, "fp32": 716.4, "xu": 38.92, "satom": 0.554},
+        "forward": {"warp": 24.560, "fp32": 405.2, "xu": 37.83, "satom": 0.235},
+        "adjoint": {"warp": 32.539, "fp32": 721.8, "xu": 39.15, "satom": 0.302},
     },
     "grid_8x8_4M": {
-        "forward": {"warp": 28.072, "fp32": 403.6, "xu": 43.93, "satom": 0.250},
-        "adjoint": {"warp": 43.074, "fp32": 716.0, "xu": 43.28, "satom": 0.808},
+        "forward": {"warp": 26.892, "fp32": 403.8, "xu": 43.85, "satom": 0.236},
+        "adjoint": {"warp": 38.965, "fp32": 721.1, "xu": 43.52, "satom": 1.041},
     },
     "sweep_32_lenses_scaled": {
-        "forward": {"warp": 23.340, "fp32": 348.8, "xu": 33.98, "satom": 0.235},
-        "adjoint": {"warp": 40.370, "fp32": 607.5, "xu": 32.95, "satom": 0.550},
+        "forward": {"warp": 24.818, "fp32": 350.5, "xu": 35.17, "satom": 0.233},
+        "adjoint": {"warp": 29.756, "fp32": 612.8, "xu": 33.12, "satom": 0.368},
     },
 }
 
@@ -80,6 +84,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--table", action="store_true",
+                   help="also time the oracle on a sample of each of the five workloads (about a minute)")
     p.add_argument("--tune", action="store_true", help="autotune the trace kernels' schedule first")
     p.add_argument("--point-kernels", action="store_true",
                    help="time only the point-source trace kernels (16M rays), in id order and in the ray order")
@@ -240,6 +246,37 @@ def oracle_rays_per_s(wl, n_sample, begin):
     O.trace_gradient(wl, d, begin=begin, count=n_sample)
     dt = time.perf_counter() - t0
     return n_sample / dt, dt
+
+
+def oracle_table():
+    """The FP64 oracle (forward + gradient, all host cores) on a sample of each of the five
+    workloads: all of the 256x256 grid; 2^20 consecutive rays from the middle of the 2048x2048
+    grid; 2^14 consecutive ids from the middle of the point-source workloads (the oracle's
+    first-root scan of the whole slab makes a point ray about a millisecond of one core);
+    2^10 ids from the middle of each lens of the sweep."""
+    from oracle import oracle as O
+    from paper_2302_12031_gb300 import workloads as W
+    out = {}
+    for k in range(1, 6):
+        wls = W.config(k)
+        wls = wls if isinstance(wls, list) else [wls]
+        if k == 1:
+            samples, desc = [(wls[0], 0, wls[0]["n_rays"])], "all rays"
+        elif k == 2:
+            n = 1 << 20
+            samples, desc = [(wls[0], wls[0]["n_rays"] // 2 - n // 2, n)], "2^20 consecutive rays, middle of the grid"
+        elif k == 5:
+            n = 1 << 10
+            samples = [(w, w["n_rays"] // 2 - n // 2, n) for w in wls]
+            desc = "2^10 consecutive ids from the middle of each of the 32 lenses"
+        else:
+            n = 1 << 14
+            samples, desc = [(wls[0], wls[0]["n_rays"] // 2 - n // 2, n)], "2^14 consecutive ids, middle of the ids"
+        rays = sum(c for _, _, c in samples)
+        dt = sum(oracle_rays_per_s(w, c, b)[1] for w, b, c in samples)
+        out["config_%d" % k] = {"rays_per_s": rays / dt, "rays": rays, "seconds": dt,
+                                "cores": O.default_threads(), "sample": desc}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -444,6 +481,8 @@ def run_ours(args, rank, world, local):
 
     if not args.no_extra:
         line["extra"] = extra_workloads(args, flush, world, (sm_count, mhz, ceil))
+    if rank == 0 and world == 1 and args.table:
+        line["oracle_by_config"] = oracle_table()
 
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -453,10 +492,11 @@ def run_ours(args, rank, world, local):
 
 
 def extra_workloads(args, flush, world, roof):
-    """Point source (16M rays) and the batched graph steps, fewer steps each; for the first
-    three, the trace kernels' durations (library events in a second graph of the same step),
-    forward-only rays/s from the forward kernel and each kernel's roofline (`roof`: SMs, clock,
-    measured ceilings)."""
+    """The 256x256-ray collimated lens, the point source (16M rays) and the batched graph steps,
+    fewer steps each; for these four, the trace kernels' durations (library events in a second
+    graph of the same step), forward-only rays/s from the forward kernel and each kernel's
+    roofline (`roof`: SMs, clock, measured ceilings); then the mesh, two-face, loss and
+    derivative-map variants."""
     import torch
     from paper_2302_12031_gb300 import api, step
     from paper_2302_12031_gb300 import dist as D
@@ -464,8 +504,8 @@ def extra_workloads(args, flush, world, roof):
     out = {}
     k = max(3, args.steps // 4)
     autotune_fields = ("warps_per_cta", "rays_per_lane", "ctas_per_sm", "batch_waves")
-    for name, wls in (("point_16M", W.config(3)), ("grid_8x8_64M_batched_graph", W.config(4)),
-                      ("sweep_32_lenses_batched_graph", W.config(5))):
+    for name, wls in (("plain_256x256", W.config(1)), ("point_16M", W.config(3)),
+                      ("grid_8x8_64M_batched_graph", W.config(4)), ("sweep_32_lenses_batched_graph", W.config(5))):
         opts = {}
         if name.startswith("sweep"):
             # the batch's schedule (waves of CTAs, warps, rays per lane) from the autotuner,
@@ -653,22 +693,23 @@ def run_point_kernels(args):
 
 
 # The counting case whose per-ray counts stand for each secondary workload.
-COUNTED_AS = {"point_16M": "point_4M", "grid_8x8_64M_batched_graph": "grid_8x8_4M",
+COUNTED_AS = {"plain_256x256": "plain_256x256", "point_16M": "point_4M", "grid_8x8_64M_batched_graph": "grid_8x8_4M",
               "sweep_32_lenses_batched_graph": "sweep_32_lenses_scaled"}
 
 
 def counting_cases():
     """The cases whose trace kernels the per-ray counts are taken on: the headline collimated
-    workload, and the point-source, grid-of-sources and sweep workloads with fewer rays (the
-    same lenses, screens and schedules; the counts are per ray). Each entry: (name, workloads,
-    ray-order flag)."""
+    workload, the 256x256-ray one, and the point-source, grid-of-sources and sweep workloads
+    with fewer rays (the same lenses, screens and schedules; the counts are per ray). Each
+    entry: (name, workloads, ray-order flag)."""
     from paper_2302_12031_gb300 import workloads as W
     w3 = W.config(3)
     w3["n_rays"] = 1 << 22
     w4 = W.config(4)
     w4["n_rays"] = 64 << 16
     sweep = W.design_sweep(32, seed=6, min_rays=1 << 16, max_rays=1 << 20)
-    return [("collimated_2048x2048", [W.config(2)], False), ("point_4M", [w3], True),
+    return [("collimated_2048x2048", [W.config(2)], False), ("plain_256x256", [W.config(1)], False),
+            ("point_4M", [w3], True),
             ("grid_8x8_4M", [w4], True), ("sweep_32_lenses_scaled", sweep, True)]
 
 

@@ -363,7 +363,7 @@ fr_status fr_zero_list(fr_handle* h, void* const* ptrs, const uint64_t* bytes, i
  * net minus z_in, at the call; 0 if negative), where each knot span of the
  * exit net (in x, y) is cut into m x m cells, the spans taken in row order and
  * the cells of a span in Z order (m the largest power of two up to 128 that
- * leaves 128 or more of a source's rays per cell, else 1), and after the
+ * leaves 16 or more of a source's rays per cell, else 1), and after the
  * cells the rays whose point there lies outside the aperture; positions
  * H..n_rays-1 hold rays that miss the aperture (the test has a 1e-5 relative
  * margin toward "meets", so a ray placed among the misses misses in the trace
