@@ -487,9 +487,12 @@ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t
 template <int CAP, bool DET, int NU, int KINDS>
 __global__ void __launch_bounds__(CAP == 1 && !DET && KINDS == 1 && NU <= 3 ? 320 : 256, 2)
     k_adjoint(const __grid_constant__ Launch<CAP> L) {
+  // One lens: item 0 by a constant index (its fields are then operands of the
+  // parameter bank, not loads); a batch: the item whose CTA range holds this CTA.
   int ii = 0;
-  while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
-  const Item& it = L.items[ii];
+  if constexpr (CAP > 1)
+    while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
+  const Item& it = L.items[CAP > 1 ? ii : 0];
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_exit(smem, it);
   const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;

@@ -318,9 +318,12 @@ __global__ void __launch_bounds__(KINDS == 1 ? (NU <= 3 ? 384 : (DET ? 256 : 384
                                   (KINDS & 7) == 2 ? 1 : 2)
     k_forward(const __grid_constant__ Launch<CAP> L) {
   pdl_trigger();   // the loss kernel may start launching; it waits for this one to end
+  // One lens: item 0 by a constant index (its fields are then operands of the
+  // parameter bank, not loads); a batch: the item whose CTA range holds this CTA.
   int ii = 0;
-  while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
-  const Item& it = L.items[ii];
+  if constexpr (CAP > 1)
+    while (ii + 1 < L.n_items && (int)blockIdx.x >= L.items[ii].cta_end) ++ii;
+  const Item& it = L.items[CAP > 1 ? ii : 0];
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_exit(smem, it);
   const LensSmem li = (KINDS & 4) && it.two_face ? carve_entry(smem, it) : ls;
