@@ -31,7 +31,10 @@
  *    traces at most 2^32 - 1 rays.
  *  - A handle is not thread-safe; use one handle per host thread.
  *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported;
- *    control nets from 4x4 to 32x32; filter sizes nu_x = nu_y in {1, 3, 5}.
+ *    control nets from 4x4 to 32x32; filter sizes nu_x = nu_y odd, 1 to 11.
+ *    Sizes 7 to 11 run in the wide-filter trace kernels: one single-face lens
+ *    per call (FR_ERR_UNSUPPORTED for a batch or a freeform entry face), not
+ *    in fr_trace_forward_static.
  *
  * Layouts:
  *  - Control heights: float32, (n1+1) x (n2+1), row-major with the u index i
@@ -120,7 +123,7 @@ typedef struct fr_target_desc {
   float z_screen;        /* screen plane, above the lens */
   float Rx, Ry;          /* screen half-widths; pixel size w = 2R/n */
   int32_t nx, ny;        /* interior pixels, 1..4096 */
-  int32_t nu_x, nu_y;    /* filter sizes (odd, equal, in {1,3,5}) */
+  int32_t nu_x, nu_y;    /* filter sizes (odd, equal, 1..11) */
   float alpha;           /* Gaussian coefficient in pixel units: exp(-alpha ((x-c)/w)^2) */
 } fr_target_desc;
 

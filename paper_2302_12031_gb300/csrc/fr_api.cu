@@ -95,7 +95,10 @@ struct ItemWs {
 
 // Whether the hot trace kernels may defer an item's rays (single-face point
 // sources intersected by Newton).
-bool may_defer(const Item& it) { return it.kind == FR_SOURCE_POINT && !it.two_face && it.mesh_nu == 0; }
+// The wide-filter kernels (nu > 5) march in the kernel: no deferred list.
+bool may_defer(const Item& it) {
+  return it.kind == FR_SOURCE_POINT && !it.two_face && it.mesh_nu == 0 && it.nu <= 5;
+}
 
 ItemWs plan(const Item& it, size_t at, bool det_fwd, bool det_adj) {
   ItemWs w;
@@ -309,7 +312,8 @@ void schedule_item(Item* it, int warps, const fr_options& o) {
 // took 1040 us in the ray order against 1005 us at 8.)
 int pick_warps(const fr_options& o, bool adjoint, int kind, bool det, int nu) {
   int cap = 8;
-  if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = nu <= 3 ? 12 : (det ? 8 : 12);
+  if (nu > 5) cap = 8;   // the wide-filter kernels: 256 threads
+  else if (!adjoint && kind == FR_SOURCE_COLLIMATED) cap = nu <= 3 ? 12 : (det ? 8 : 12);
   else if (adjoint && kind == FR_SOURCE_COLLIMATED && !det && nu <= 3) cap = 10;
   return o.warps_per_cta > 0 ? std::min(o.warps_per_cta, cap) : cap;
 }
@@ -333,7 +337,7 @@ bool want_smem_hist(const Item& it, const fr_options& o, bool det) {
 // (collimated items too), sized so that a CTA needs at most `budget` bytes:
 // two CTAs of the batch kernel share an SM.
 bool plan_window(Item* it, const fr_options& o, int smem_optin, size_t budget = 0) {
-  if (o.deterministic || it->two_face) return false;
+  if (o.deterministic || it->two_face || it->nu > 5) return false;
   if (budget == 0 && it->kind != FR_SOURCE_POINT) return false;
   if (o.hist_mode == 1 || o.hist_mode == 2) return false;
   if (o.hist_mode == 0 && want_smem_hist(*it, o, false)) return false;
@@ -385,9 +389,8 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   if (o.ray_order && items.size() > 1)
     return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to one lens, not to a batch");
   for (auto& it : items)
-    if (it.nu > 5)
-      return set_error(h, FR_ERR_UNSUPPORTED, "the forward and adjoint traces take filter sizes 1, 3, 5 "
-                                              "(derivative maps up to 11)");
+    if (it.nu > 5 && (CAP > 1 || items.size() > 1 || it.two_face))
+      return set_error(h, FR_ERR_UNSUPPORTED, "filter sizes 7, 9, 11: one single-face lens per call");
   bool det = o.deterministic != 0;
   // A point-source forward privatises a window of its grid (plan_window); in a
   // batch every item whose grid does not fit does (two CTAs per SM).

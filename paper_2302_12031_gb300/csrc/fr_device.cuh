@@ -1468,6 +1468,62 @@ __device__ __forceinline__ bool footprint_scalar(const Item& it, float X, float 
   return NU >= 3 || (f.rsx > 0.0f && f.rsy > 0.0f);   // nu = 1 exactly on a pixel edge: all f = 0
 }
 
+// Filter sizes 7, 9, 11 with the size a runtime value (the wide-filter
+// traces): the values of axis_footprint, in loops that are not unrolled.
+constexpr int kWideNu = 11;
+struct FootDyn {
+  int ie, je;
+  float dx0, dy0;
+  float fx[kWideNu], fy[kWideNu];
+  float rsx, rsy;
+};
+
+__device__ __forceinline__ void axis_footprint_dyn(float g, int n, int nu, float a2, float cut, int* first, float* d0,
+                                                   float* f, float* rs) {
+  const int h = (nu - 1) / 2;
+  const float fl = fminf(fmaxf(floorf(g), (float)h), (float)(n + h - 1));
+  *first = (int)fl - h;
+  const float dfirst = g - fl + ((float)h - 0.5f);
+  *d0 = dfirst;
+  float sum = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a < nu; ++a) {
+    const float d = dfirst - (float)a;
+    f[a] = fmaxf(ex2_approx(-a2 * d * d) - cut, 0.0f);
+    sum += f[a];
+  }
+  *rs = fast_rcp(sum);   // nu >= 7: the hit's own pixel is inside the support
+}
+
+__device__ __forceinline__ void footprint_dyn(const Item& it, float X, float Y, FootDyn& f) {
+  axis_footprint_dyn(fmaf(X, it.inv_wx, it.gx_off), it.nx, it.nu, it.ax, it.cut, &f.ie, &f.dx0, f.fx, &f.rsx);
+  axis_footprint_dyn(fmaf(Y, it.inv_wy, it.gy_off), it.ny, it.nu, it.ay, it.cut, &f.je, &f.dy0, f.fy, &f.rsy);
+}
+
+// filter_grad for a FootDyn: F = f / S and dF/dX (dF/dY) per axis.
+__device__ __forceinline__ void filter_grad_dyn(const Item& it, const FootDyn& f, float* Fx, float* Fy, float* gxa,
+                                                float* gya) {
+  const float ln2 = 0.69314718055994531f;
+  const float kx = -2.0f * (it.ax * ln2) * it.inv_wx, ky = -2.0f * (it.ay * ln2) * it.inv_wy;
+  float Spx = 0.0f, Spy = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a < it.nu; ++a) {
+    const float gx = kx * (f.dx0 - (float)a) * (f.fx[a] + it.cut);
+    const float gy = ky * (f.dy0 - (float)a) * (f.fy[a] + it.cut);
+    gxa[a] = f.fx[a] != 0.0f ? gx : 0.0f;
+    gya[a] = f.fy[a] != 0.0f ? gy : 0.0f;
+    Spx += gxa[a];
+    Spy += gya[a];
+    Fx[a] = f.fx[a] * f.rsx;
+    Fy[a] = f.fy[a] * f.rsy;
+  }
+#pragma unroll 1
+  for (int a = 0; a < it.nu; ++a) {
+    gxa[a] = fmaf(-Fx[a], Spx, gxa[a]) * f.rsx;
+    gya[a] = fmaf(-Fy[a], Spy, gya[a]) * f.rsy;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Reverse mode of one ray (a9). Input: G[b][a] = dL/dE on the footprint (row b,
 // column a). Output: the adjoint zeta of the hit height and of the surface
@@ -1508,6 +1564,10 @@ __device__ __forceinline__ void filter_grad(const Item& it, const Foot<NU>& f, f
   }
 }
 
+template <bool COLL>
+__device__ __forceinline__ void ray_reverse_tail(const Item& it, const LensSmem& ls, const RayFwd& r, float W,
+                                                 float Xs, float Ys, float* zeta, float* Zs_bar, float* Zt_bar);
+
 template <int NU, bool COLL>
 __device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, const RayFwd& r, const Foot<NU>& f,
                                             const float (&G)[NU][NU], float* zeta, float* Zs_bar, float* Zt_bar) {
@@ -1524,8 +1584,16 @@ __device__ __forceinline__ void ray_reverse(const Item& it, const LensSmem& ls, 
     WX = __ffma2_rn(make_float2(AB.x, AB.x), make_float2(Fx[a], gxa[a]), WX);
     Ys = fmaf(AB.y, Fx[a], Ys);
   }
-  float wbar = WX.x;
-  const float Xs = WX.y;
+  ray_reverse_tail<COLL>(it, ls, r, WX.x, WX.y, Ys, zeta, Zs_bar, Zt_bar);
+}
+
+// The chain of ray_reverse after the footprint contraction: from
+// W = sum G F_x F_y, Xs = sum G F'_x F_y and Ys = sum G F_x F'_y to the
+// adjoints of the hit height and slopes.
+template <bool COLL>
+__device__ __forceinline__ void ray_reverse_tail(const Item& it, const LensSmem& ls, const RayFwd& r, float W,
+                                                 float Xs, float Ys, float* zeta, float* Zs_bar, float* Zt_bar) {
+  float wbar = W;
   const float K = r.w * it.inv_area;
   wbar *= it.inv_area;
   const float2 XYbar = __fmul2_rn(make_float2(K, K), make_float2(Xs, Ys));

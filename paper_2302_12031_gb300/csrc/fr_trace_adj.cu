@@ -98,22 +98,14 @@ struct GCache {
   float G[NU][NU];
 };
 
-template <int NU, bool DET, bool COLL>
-__device__ __forceinline__ void adjoint_ray(const Item& it, const LensSmem& ls, const RayFwd& r, GCache<NU>& gc,
-                                            const float (&Nv)[4], const float (&dNv)[4], GradAcc<DET>& acc,
-                                            const GradOut& go) {
-  Foot<NU> f;
-  if (!footprint_scalar<NU>(it, r.X, r.Y, f)) return;
-  if (f.ie != gc.ie || f.je != gc.je) {
-#pragma unroll
-    for (int b = 0; b < NU; ++b)
-#pragma unroll
-      for (int a = 0; a < NU; ++a) gc.G[b][a] = __ldg(it.dLdE + (size_t)(f.je + b) * it.ncol + f.ie + a);
-    gc.ie = f.ie;
-    gc.je = f.je;
-  }
-  float zeta, Zsb, Ztb;
-  ray_reverse<NU, COLL>(it, ls, r, f, gc.G, &zeta, &Zsb, &Ztb);
+// dL/dP += zeta N_a N_b + Zs_bar N'_a N_b + Zt_bar N_a N'_b for a ray on
+// patch (k, l) (N_b, N'_b at the ray's t in Nv, dNv), summed in `acc` while the
+// patch does not change; on the triangle mesh the height term follows the
+// triangle's vertices.
+template <bool DET, bool COLL>
+__device__ __forceinline__ void add_ray_grad(const Item& it, const LensSmem& ls, const RayFwd& r, float zeta,
+                                             float Zsb, float Ztb, const float (&Nv)[4], const float (&dNv)[4],
+                                             GradAcc<DET>& acc, const GradOut& go) {
   float Nu[4], dNu[4];
   basis_eval(ls.bu + r.k * 4, r.s, Nu, dNu);
   if (r.k != acc.k || r.l != acc.l) {
@@ -166,6 +158,25 @@ __device__ __forceinline__ void adjoint_ray(const Item& it, const LensSmem& ls, 
       else acc.g[a][b] += c;
     }
   }
+}
+
+template <int NU, bool DET, bool COLL>
+__device__ __forceinline__ void adjoint_ray(const Item& it, const LensSmem& ls, const RayFwd& r, GCache<NU>& gc,
+                                            const float (&Nv)[4], const float (&dNv)[4], GradAcc<DET>& acc,
+                                            const GradOut& go) {
+  Foot<NU> f;
+  if (!footprint_scalar<NU>(it, r.X, r.Y, f)) return;
+  if (f.ie != gc.ie || f.je != gc.je) {
+#pragma unroll
+    for (int b = 0; b < NU; ++b)
+#pragma unroll
+      for (int a = 0; a < NU; ++a) gc.G[b][a] = __ldg(it.dLdE + (size_t)(f.je + b) * it.ncol + f.ie + a);
+    gc.ie = f.ie;
+    gc.je = f.je;
+  }
+  float zeta, Zsb, Ztb;
+  ray_reverse<NU, COLL>(it, ls, r, f, gc.G, &zeta, &Zsb, &Ztb);
+  add_ray_grad<DET, COLL>(it, ls, r, zeta, Zsb, Ztb, Nv, dNv, acc, go);
 }
 
 // Along one grid row of a collimated source t, N_b(t) and N'_b(t) are fixed, so
@@ -617,6 +628,104 @@ __global__ void __launch_bounds__(256) k_adjoint_deferred(const __grid_constant_
 
 // Deterministic mode: int64 fixed point -> float gradient, with the scale the
 // adjoint kernel used (recomputed from the same device value).
+// Adjoint for filter sizes 7, 9 and 11 (one single-face lens per launch, the
+// size a runtime value): each lane traces its run of rays (of ordered
+// positions for a point source in the ray order), point sources with the
+// march in the kernel; per ray the footprint's dL/dE is read from global
+// memory inside the contraction (W = sum G F_x F_y, Xs = sum G F'_x F_y,
+// Ys = sum G F_x F'_y), ray_reverse_tail gives the adjoints of the hit, and
+// add_ray_grad sums the 16 terms as in the other kernels.
+template <bool DET>
+__global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ Launch<1> L) {
+  const Item& it = L.items[0];
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LensSmem ls = carve_exit(smem, it);
+  unsigned char* grad_raw = smem + tables_bytes(it);
+  GradOut go;
+  go.s_group = nullptr;
+  go.sg_f = reinterpret_cast<float*>(grad_raw);
+  go.sg_q = reinterpret_cast<unsigned long long*>(grad_raw);
+  const int nctrl = it.nparam;
+  for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
+    if constexpr (DET) go.sg_q[q] = 0ull;
+    else go.sg_f[q] = 0.0f;
+  }
+  __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  build_lens_tables(it, ls);   // ends with __syncthreads
+  go.fixP = 0.0f;
+  if constexpr (DET) {   // the scale of k_adjoint
+    const float unit = *it.gmax * it.fixP_unit;
+    int e = 0;
+    if (unit > 0.0f) frexpf(unit, &e);
+    go.fixP = unit > 0.0f ? ldexpf(1.0f, 40 - e) : 1.0f;
+  }
+  float zmin = 0.0f, zmax = 0.0f;
+  const bool coll = it.kind == FR_SOURCE_COLLIMATED;
+  if (!coll) zbounds(ls, &zmin, &zmax);
+  const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+  uint64_t a, b;
+  lane_range(it, L.warps, &a, &b);
+  RayCount cnt;
+  cnt.on_screen = 0u;
+  unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+  GradAcc<DET> acc;
+  acc.k = -1;
+  for (uint64_t p = a; p < b; ++p) {
+    RayFwd r;
+    if (coll) {
+      const uint32_t row = (uint32_t)(p / (uint64_t)it.cols), col = (uint32_t)(p % (uint64_t)it.cols);
+      trace_collimated(it, ls, row, col, p, inv_cols, inv_rows, r);
+    } else {
+      trace_point<true>(it, ls, it.order ? (uint64_t)__ldg(it.order + p) : p, zmin, zmax, r);
+    }
+    cnt.add(r.status, cnt_dst);
+    if (r.status != FR_RAY_ON_SCREEN) continue;
+    FootDyn f;
+    footprint_dyn(it, r.X, r.Y, f);
+    float Fx[kWideNu], Fy[kWideNu], gxa[kWideNu], gya[kWideNu];
+    filter_grad_dyn(it, f, Fx, Fy, gxa, gya);
+    float W = 0.0f, Xs = 0.0f, Ys = 0.0f;
+#pragma unroll 1
+    for (int ca = 0; ca < it.nu; ++ca) {
+      float A = 0.0f, B = 0.0f;
+      const float* col = it.dLdE + (size_t)f.je * it.ncol + f.ie + ca;
+#pragma unroll 1
+      for (int rb = 0; rb < it.nu; ++rb) {
+        const float g = __ldg(col + (size_t)rb * it.ncol);
+        A = fmaf(g, Fy[rb], A);
+        B = fmaf(g, gya[rb], B);
+      }
+      W = fmaf(A, Fx[ca], W);
+      Xs = fmaf(A, gxa[ca], Xs);
+      Ys = fmaf(B, Fx[ca], Ys);
+    }
+    float zeta, Zsb, Ztb, Nv[4], dNv[4];
+    basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
+    if (coll) {
+      ray_reverse_tail<true>(it, ls, r, W, Xs, Ys, &zeta, &Zsb, &Ztb);
+      add_ray_grad<DET, true>(it, ls, r, zeta, Zsb, Ztb, Nv, dNv, acc, go);
+    } else {
+      ray_reverse_tail<false>(it, ls, r, W, Xs, Ys, &zeta, &Zsb, &Ztb);
+      add_ray_grad<DET, false>(it, ls, r, zeta, Zsb, Ztb, Nv, dNv, acc, go);
+    }
+  }
+  grad_flush<DET>(acc, it.ncv, go.sg_f, go.sg_q);
+  cnt.reduce_into(cnt_dst);
+  ordered_misses_into(it, cnt_dst);
+  __syncthreads();
+  for (int q = threadIdx.x; q < nctrl; q += blockDim.x) {
+    if constexpr (DET) {
+      const unsigned long long v = go.sg_q[q];
+      if (v) atomicAdd(it.Pfix + q, v);
+    } else {
+      const float v = go.sg_f[q];
+      if (v != 0.0f) atomicAdd(it.dLdP + q, v);
+    }
+  }
+  RayCount::publish(s_cnt, it.stats);
+}
+
 __global__ void k_grad_fix_to_float(const __grid_constant__ Item it, int accumulate) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= it.nparam) return;
@@ -646,6 +755,7 @@ template <int CAP>
 AdjKernel<CAP> pick_adjoint(bool det, int nu, int kinds);
 template <>
 AdjKernel<1> pick_adjoint<1>(bool det, int nu, int kinds) {
+  if (nu > 5) return det ? k_adjoint_wide<true> : k_adjoint_wide<false>;   // filter sizes 7, 9, 11
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
   if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
   return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
@@ -713,6 +823,8 @@ cudaError_t configure_adjoint(int optin) {
       if ((e = allow_max_smem(pick_adjoint_deferred<1>(det != 0, nu), optin))) return e;
       if ((e = allow_max_smem(pick_adjoint_deferred<kMaxItems>(det != 0, nu), optin))) return e;
     }
+  if ((e = allow_max_smem(k_adjoint_wide<false>, optin))) return e;
+  if ((e = allow_max_smem(k_adjoint_wide<true>, optin))) return e;
   return cudaSuccess;
 }
 

@@ -514,6 +514,110 @@ __global__ void __launch_bounds__(256) k_forward_deferred(const __grid_constant_
 }
 
 // The full record of every ray of [ray_begin, ray_end), one thread per ray.
+// Forward trace for filter sizes 7, 9 and 11 (one single-face lens per
+// launch, the size a runtime value): each lane traces its run of rays (of
+// ordered positions for a point source in the ray order), point sources with
+// the march in the kernel, and adds every ray's nu x nu footprint straight to
+// the privatised histogram (float or, deterministic, int64 fixed point) when
+// the grid fits in shared memory, else to global memory. The per-ray terms are
+// those of `deposit`: kx_a ky_b with kx_a = w/(w_x w_y) f_a / S_x and
+// ky_b = f_b / S_y.
+template <bool DET>
+__global__ void __launch_bounds__(256) k_forward_wide(const __grid_constant__ Launch<1> L) {
+  const Item& it = L.items[0];
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LensSmem ls = carve_exit(smem, it);
+  const bool sh = it.smem_hist == 1;
+  float* sh_f = reinterpret_cast<float*>(smem + tables_bytes(it));
+  unsigned long long* sh_q = reinterpret_cast<unsigned long long*>(smem + tables_bytes(it));
+  const int ncell = it.ncol * it.nrow;
+  __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  __shared__ int s_bb[4];
+  if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  if (threadIdx.x < 4) s_bb[threadIdx.x] = (threadIdx.x & 1) ? -1 : 0x7fffffff;
+  if (sh)
+    for (int q = threadIdx.x; q < ncell; q += blockDim.x) {
+      if constexpr (DET) sh_q[q] = 0ull;
+      else sh_f[q] = 0.0f;
+    }
+  build_lens_tables(it, ls);   // ends with __syncthreads
+  float zmin = 0.0f, zmax = 0.0f;
+  if (it.kind == FR_SOURCE_POINT) zbounds(ls, &zmin, &zmax);
+  const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+  uint64_t a, b;
+  lane_range(it, L.warps, &a, &b);
+  RayCount cnt;
+  cnt.on_screen = 0u;
+  unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+  Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
+  for (uint64_t p = a; p < b; ++p) {
+    RayFwd r;
+    if (it.kind == FR_SOURCE_COLLIMATED) {
+      const uint32_t row = (uint32_t)(p / (uint64_t)it.cols), col = (uint32_t)(p % (uint64_t)it.cols);
+      trace_collimated(it, ls, row, col, p, inv_cols, inv_rows, r);
+    } else {
+      trace_point<true>(it, ls, it.order ? (uint64_t)__ldg(it.order + p) : p, zmin, zmax, r);
+    }
+    cnt.add(r.status, cnt_dst);
+    if (r.status != FR_RAY_ON_SCREEN) continue;
+    FootDyn f;
+    footprint_dyn(it, r.X, r.Y, f);
+    bb.imin = min(bb.imin, f.ie);
+    bb.imax = max(bb.imax, f.ie);
+    bb.jmin = min(bb.jmin, f.je);
+    bb.jmax = max(bb.jmax, f.je);
+    const float Kx = r.w * it.inv_area * f.rsx;
+#pragma unroll 1
+    for (int rb = 0; rb < it.nu; ++rb) {
+      const float ky = f.fy[rb] * f.rsy;
+      if (ky == 0.0f) continue;
+      const int row0 = (f.je + rb) * it.ncol + f.ie;
+#pragma unroll 1
+      for (int ca = 0; ca < it.nu; ++ca) {
+        const float kx = f.fx[ca] * Kx;
+        if (kx == 0.0f) continue;
+        if constexpr (DET) {
+          const unsigned long long v = (unsigned long long)__float2ll_rn(kx * ky * it.fixE);
+          if (sh) atomicAdd(sh_q + row0 + ca, v);
+          else atomicAdd(it.Efix + row0 + ca, v);
+        } else {
+          if (sh) atomicAdd(sh_f + row0 + ca, kx * ky);
+          else atomicAdd(it.E + row0 + ca, kx * ky);
+        }
+      }
+    }
+  }
+  cnt.reduce_into(cnt_dst);
+  ordered_misses_into(it, cnt_dst);
+  if (sh) {
+    const int i0 = __reduce_min_sync(0xffffffffu, bb.imin), i1 = __reduce_max_sync(0xffffffffu, bb.imax);
+    const int j0 = __reduce_min_sync(0xffffffffu, bb.jmin), j1 = __reduce_max_sync(0xffffffffu, bb.jmax);
+    if ((threadIdx.x & 31) == 0 && i1 >= 0) {
+      atomicMin(&s_bb[0], i0);
+      atomicMax(&s_bb[1], i1);
+      atomicMin(&s_bb[2], j0);
+      atomicMax(&s_bb[3], j1);
+    }
+  }
+  __syncthreads();
+  if (sh && s_bb[1] >= 0) {
+    // the touched window of the privatised histogram
+    const int c0 = s_bb[0], c1 = s_bb[1] + it.nu - 1, r0 = s_bb[2], r1 = s_bb[3] + it.nu - 1;
+    const int wcols = c1 - c0 + 1, n = wcols * (r1 - r0 + 1);
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int idx = (r0 + q / wcols) * it.ncol + c0 + q % wcols;
+      if constexpr (DET) {
+        const unsigned long long v = sh_q[idx];
+        if (v) atomicAdd(it.Efix + idx, v);
+      } else {
+        const float v = sh_f[idx];
+        if (v != 0.0f) atomicAdd(it.E + idx, v);
+      }
+    }
+  }
+  RayCount::publish(s_cnt, it.stats);
+}
+
 __global__ void __launch_bounds__(128) k_debug(const __grid_constant__ Item it, fr_ray_record* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_exit(smem, it);
@@ -589,6 +693,7 @@ template <int CAP>
 FwdKernel<CAP> pick_forward(bool det, int nu, int kinds);
 template <>
 FwdKernel<1> pick_forward<1>(bool det, int nu, int kinds) {
+  if (nu > 5) return det ? k_forward_wide<true> : k_forward_wide<false>;   // filter sizes 7, 9, 11
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
   if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
   if (kinds == 8) return det ? pick_nu<1, true, 10>(nu) : pick_nu<1, false, 10>(nu);  // point, march in the kernel
@@ -665,6 +770,8 @@ cudaError_t configure_forward(int optin) {
       if ((e = allow_max_smem(pick_forward_deferred<1>(det != 0, nu), optin))) return e;
       if ((e = allow_max_smem(pick_forward_deferred<kMaxItems>(det != 0, nu), optin))) return e;
     }
+  if ((e = allow_max_smem(k_forward_wide<false>, optin))) return e;
+  if ((e = allow_max_smem(k_forward_wide<true>, optin))) return e;
   return cudaSuccess;
 }
 

@@ -183,7 +183,7 @@ def test_invalid_arguments_return_error_codes():
     assert fwd(begin=pb.n_rays + 1) == api.FR_ERR_INVALID_ARG
     assert fwd(begin=10, count=pb.n_rays) == api.FR_ERR_INVALID_ARG
     assert fwd(E_ptr=False) == api.FR_ERR_INVALID_ARG
-    bt = api.TargetDesc.from_buffer_copy(pb.target); bt.nu_x = bt.nu_y = 7
+    bt = api.TargetDesc.from_buffer_copy(pb.target); bt.nu_x = bt.nu_y = 13
     assert fwd(tgt=bt) == api.FR_ERR_UNSUPPORTED
     bt = api.TargetDesc.from_buffer_copy(pb.target); bt.nx = 0
     assert fwd(tgt=bt) == api.FR_ERR_INVALID_ARG

@@ -146,13 +146,3 @@ def test_flat_lens_maps_sum_to_zero_for_both_filter_sizes():
         # zero up to FP32 rounding of the float-atomic sums: the map's terms
         # cancel to ~1e-5 of their absolute sum
         assert abs(float(t.sum())) < 5e-5 * float(t.abs().sum())
-
-
-def test_traces_refuse_wide_filters():
-    wl = W.collimated("c", 64, 8, 16, 1, 2, with_target=False)
-    wl["target"]["nu_x"] = wl["target"]["nu_y"] = 7
-    pb = api.Problem(wl)
-    with pytest.raises(api.FreerayError):
-        pb.forward()
-    with pytest.raises(api.FreerayError):
-        pb.adjoint(torch.zeros(pb.ext_shape, device="cuda"))
