@@ -381,8 +381,8 @@ fr_status fr_zero_list(fr_handle* h, void* const* ptrs, const uint64_t* bytes, i
  * differ from call to call); deterministic-mode results do not depend on it.
  * With a freeform entry face (entry_ctrl_z) the same key orders the rays but
  * H = n_rays: the entry face decides the aperture in the trace. Needs n_rays
- * < 2^32; uses the handle's workspace (4 bytes per cell); asynchronous on
- * `stream`. FR_ERR_UNSUPPORTED for collimated sources. */
+ * < 2^32; uses the handle's workspace (4 bytes per cell and per ray);
+ * asynchronous on `stream`. FR_ERR_UNSUPPORTED for collimated sources. */
 fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source, uint64_t n_rays,
                        uint64_t seed, uint32_t* order_out, void* stream);
 

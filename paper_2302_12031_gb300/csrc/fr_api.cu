@@ -887,9 +887,13 @@ fr_status fr_ray_order(fr_handle* h, const fr_lens_desc* lens, const fr_source_d
   const int m = fr::ray_order_grid(it);
   const uint64_t nk = fr::ray_order_keys(it, m);
   cudaStream_t st = as_stream(stream);
-  s = ensure_workspace(h, kHeaderBytes + nk * sizeof(uint32_t), st);
+  const size_t keys_at = align_up(kHeaderBytes + nk * sizeof(uint32_t));
+  const size_t partial_at = align_up(keys_at + n_rays * sizeof(uint32_t));
+  s = ensure_workspace(h, partial_at + fr::ray_order_scratch_words(it, m) * sizeof(uint32_t), st);
   if (s != FR_OK) return s;
-  cudaError_t e = fr::launch_ray_order(it, m, reinterpret_cast<uint32_t*>(h->ws + kHeaderBytes), order_out, st);
+  cudaError_t e = fr::launch_ray_order(it, m, reinterpret_cast<uint32_t*>(h->ws + kHeaderBytes),
+                                       reinterpret_cast<uint32_t*>(h->ws + keys_at),
+                                       reinterpret_cast<uint32_t*>(h->ws + partial_at), order_out, st);
   if (e != cudaSuccess) return cuda_error(h, e, "ray order kernels");
   return FR_OK;
 }

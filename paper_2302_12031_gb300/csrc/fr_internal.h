@@ -156,11 +156,13 @@ cudaError_t launch_adam_tanh(float* theta, float* m, float* v, const float* dLdP
 cudaError_t launch_offset_spherical(int n1, int n2, int p, int q, double rx, double ry, double c, double R,
                                     float* out, cudaStream_t st);
 // Coherent ray order (fr_ray_order): counting sort of the ray ids by source
-// and entry-plane cell (m x m cells per knot span). `counts` holds n_keys
-// words of scratch.
+// and cell (m x m cells per knot span). Scratch: `counts` n_keys words,
+// `keys` n_rays words, `partial` ray_order_scratch_words words.
 int ray_order_grid(const Item& it);
 uint64_t ray_order_keys(const Item& it, int m);
-cudaError_t launch_ray_order(const Item& it, int m, uint32_t* counts, uint32_t* order, cudaStream_t st);
+uint64_t ray_order_scratch_words(const Item& it, int m);
+cudaError_t launch_ray_order(const Item& it, int m, uint32_t* counts, uint32_t* keys, uint32_t* partial,
+                             uint32_t* order, cudaStream_t st);
 size_t tan_smem_bytes(const Item& it);
 cudaError_t launch_tangent(const Item& it, int warps, int grid, size_t smem, const float* dP, int n_dirs, float* dE,
                            cudaStream_t st);

@@ -83,17 +83,22 @@ __device__ float nominal_thickness(const Item& it) {
   return s_h;
 }
 
-__global__ void __launch_bounds__(256) k_order_count(const __grid_constant__ Item it, int m, uint32_t* counts) {
+// Counts the rays per key and keeps each ray's key for the scatter pass.
+__global__ void __launch_bounds__(256) k_order_count(const __grid_constant__ Item it, int m, uint32_t* counts,
+                                                     uint32_t* keys) {
   const float h = nominal_thickness(it);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; id < it.n_rays; id += stride)
-    atomicAdd(counts + ray_key(it, id, m, h), 1u);
+  for (uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; id < it.n_rays; id += stride) {
+    const uint32_t k = ray_key(it, id, m, h);
+    keys[id] = k;
+    atomicAdd(counts + k, 1u);
+  }
 }
 
 // Exclusive prefix sum of counts[0..n) in place, one CTA of 1024 threads: each
 // thread sums a contiguous chunk, the CTA scans the chunk sums, each thread
 // writes its chunk's prefixes. The prefix of the last key (the misses) is the
-// number of rays that meet the aperture: it goes to *hits.
+// number of rays that meet the aperture: it goes to *hits (when given).
 __global__ void __launch_bounds__(1024) k_order_scan(uint32_t* counts, uint64_t n, uint32_t* hits, uint32_t all) {
   __shared__ uint32_t s_warp[32];
   const uint64_t chunk = (n + blockDim.x - 1) / blockDim.x;
@@ -124,19 +129,90 @@ __global__ void __launch_bounds__(1024) k_order_scan(uint32_t* counts, uint64_t 
   for (uint64_t i = lo; i < hi; ++i) {
     const uint32_t c = counts[i];
     counts[i] = run;
-    if (i == n - 1) *hits = all ? all : run;
+    if (i == n - 1 && hits) *hits = all ? all : run;
     run += c;
   }
 }
 
-__global__ void __launch_bounds__(256) k_order_scatter(const __grid_constant__ Item it, int m, uint32_t* cursor,
-                                                       uint32_t* order) {
-  const float h = nominal_thickness(it);
+// The same scan for many keys, in three launches: the sum of every tile of
+// kScanTile counts (k_scan_partial), the scan of those sums (k_order_scan on
+// one CTA), then each tile's own scan from its offset (k_scan_apply).
+constexpr uint64_t kScanTile = 8192;   // 1024 threads x 8 counts
+
+__device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* s_warp) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t t = 0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? s_warp[threadIdx.x] : 0u;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;   // in thread 0
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partial(const uint32_t* counts, uint64_t n, uint32_t* partial) {
+  __shared__ uint32_t s_warp[32];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  uint32_t v = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t i = base + threadIdx.x + 1024u * j;
+    if (i < n) v += counts[i];
+  }
+  const uint32_t t = block_sum_1024(v, s_warp);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(uint32_t* counts, uint64_t n, const uint32_t* partial,
+                                                     uint32_t* hits, uint32_t all) {
+  __shared__ uint32_t s_warp[32];
+  const uint64_t lo = min(n, (uint64_t)blockIdx.x * kScanTile + 8u * threadIdx.x), hi = min(n, lo + 8);
+  uint32_t c[8], sum = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    c[j] = lo + j < hi ? counts[lo + j] : 0u;
+    sum += c[j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;   // inclusive over warps 0..lane
+  }
+  __syncthreads();
+  uint32_t run = partial[blockIdx.x] + incl - sum + (warp > 0 ? s_warp[warp - 1] : 0u);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t i = lo + j;
+    if (i < hi) {
+      counts[i] = run;
+      if (i == n - 1) *hits = all ? all : run;
+      run += c[j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(const __grid_constant__ Item it, const uint32_t* keys,
+                                                       uint32_t* cursor, uint32_t* order) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t id = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; id < it.n_rays; id += stride) {
-    // The key is the counting pass's to the bit (the same code, with no
-    // contractible a*b+c left in it); the bound only guards memory.
-    const uint32_t pos = atomicAdd(cursor + ray_key(it, id, m, h), 1u);
+    // the counting pass's key; the bound only guards memory
+    const uint32_t pos = atomicAdd(cursor + keys[id], 1u);
     if (pos < it.n_rays) order[pos] = (uint32_t)id;
   }
 }
@@ -158,18 +234,33 @@ uint64_t ray_order_keys(const Item& it, int m) {
   return (uint64_t)(it.gnx * it.gny) * ((uint64_t)(it.nsu * it.nsv) * (uint64_t)(m * m) + 1) + 1;
 }
 
-cudaError_t launch_ray_order(const Item& it, int m, uint32_t* counts, uint32_t* order, cudaStream_t st) {
+uint64_t ray_order_scratch_words(const Item& it, int m) {
+  return (ray_order_keys(it, m) + kScanTile - 1) / kScanTile;
+}
+
+cudaError_t launch_ray_order(const Item& it, int m, uint32_t* counts, uint32_t* keys, uint32_t* partial,
+                             uint32_t* order, cudaStream_t st) {
   const uint64_t nk = ray_order_keys(it, m);
   cudaError_t e = cudaMemsetAsync(counts, 0, nk * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const uint64_t want = (it.n_rays + 255) / 256;
   const unsigned int blocks = (unsigned int)(want < 4096 ? want : 4096);
-  k_order_count<<<blocks, 256, 0, st>>>(it, m, counts);
+  k_order_count<<<blocks, 256, 0, st>>>(it, m, counts, keys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // a freeform entry face decides the aperture in the trace: every position is traced
-  k_order_scan<<<1, 1024, 0, st>>>(counts, nk, order + it.n_rays, it.two_face ? (uint32_t)it.n_rays : 0u);
+  const uint32_t all = it.two_face ? (uint32_t)it.n_rays : 0u;
+  const uint64_t tiles = (nk + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    k_order_scan<<<1, 1024, 0, st>>>(counts, nk, order + it.n_rays, all);
+  } else {
+    k_scan_partial<<<(unsigned int)tiles, 1024, 0, st>>>(counts, nk, partial);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_order_scan<<<1, 1024, 0, st>>>(partial, tiles, nullptr, 0u);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan_apply<<<(unsigned int)tiles, 1024, 0, st>>>(counts, nk, partial, order + it.n_rays, all);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_order_scatter<<<blocks, 256, 0, st>>>(it, m, counts, order);
+  k_order_scatter<<<blocks, 256, 0, st>>>(it, keys, counts, order);
   return cudaGetLastError();
 }
 
