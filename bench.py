@@ -42,7 +42,7 @@ FLOPS_ADJ_COLLIMATED = 290
 # from one ncu capture of the collimated 2048x2048 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of each trace kernel launch).
 # Set to None whenever the kernel changes after that capture.
-PROFILED_DRAM_BYTES = {"forward": 116224, "adjoint": 137728}
+PROFILED_DRAM_BYTES = {"forward": 115712, "adjoint": 136960}
 
 
 # Per-ray work of each trace kernel on the cases of counting_cases(), from one
@@ -54,24 +54,24 @@ PROFILED_DRAM_BYTES = {"forward": 116224, "adjoint": 137728}
 #   changed after that capture.
 COUNTS_PER_RAY = {
     "collimated_2048x2048": {
-        "forward": {"warp": 8.919, "fp32": 139.2, "xu": 19.87, "satom": 0.257},
-        "adjoint": {"warp": 14.070, "fp32": 289.1, "xu": 17.86, "satom": 0.153},
+        "forward": {"warp": 8.543, "fp32": 139.2, "xu": 19.87, "satom": 0.257},
+        "adjoint": {"warp": 13.948, "fp32": 289.1, "xu": 17.86, "satom": 0.154},
     },
     "plain_256x256": {
-        "forward": {"warp": 10.591, "fp32": 147.6, "xu": 22.45, "satom": 0.244},
-        "adjoint": {"warp": 21.593, "fp32": 334.2, "xu": 19.53, "satom": 1.002},
+        "forward": {"warp": 10.229, "fp32": 147.6, "xu": 22.45, "satom": 0.244},
+        "adjoint": {"warp": 21.341, "fp32": 334.2, "xu": 19.53, "satom": 1.014},
     },
     "point_4M": {
-        "forward": {"warp": 24.560, "fp32": 405.2, "xu": 37.83, "satom": 0.235},
-        "adjoint": {"warp": 32.539, "fp32": 721.8, "xu": 39.15, "satom": 0.302},
+        "forward": {"warp": 24.746, "fp32": 402.8, "xu": 37.83, "satom": 0.235},
+        "adjoint": {"warp": 32.935, "fp32": 719.4, "xu": 39.15, "satom": 0.304},
     },
     "grid_8x8_4M": {
-        "forward": {"warp": 26.892, "fp32": 403.8, "xu": 43.85, "satom": 0.236},
-        "adjoint": {"warp": 38.965, "fp32": 721.1, "xu": 43.52, "satom": 1.041},
+        "forward": {"warp": 27.175, "fp32": 401.4, "xu": 43.85, "satom": 0.236},
+        "adjoint": {"warp": 39.513, "fp32": 718.8, "xu": 43.52, "satom": 1.041},
     },
     "sweep_32_lenses_scaled": {
-        "forward": {"warp": 24.818, "fp32": 350.5, "xu": 35.17, "satom": 0.233},
-        "adjoint": {"warp": 29.756, "fp32": 612.8, "xu": 33.12, "satom": 0.368},
+        "forward": {"warp": 24.821, "fp32": 350.5, "xu": 35.16, "satom": 0.233},
+        "adjoint": {"warp": 29.767, "fp32": 612.8, "xu": 33.12, "satom": 0.369},
     },
 }
 
