@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(256) k_adjoint_deferred(const __grid_constant_
 // add_ray_grad sums the 16 terms as in the other kernels.
 template <bool DET>
 __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ Launch<1> L) {
+  pdl_wait();   // launched early after a kernel that triggers: nothing before it ends
   const Item& it = L.items[0];
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_exit(smem, it);

@@ -524,6 +524,7 @@ __global__ void __launch_bounds__(256) k_forward_deferred(const __grid_constant_
 // ky_b = f_b / S_y.
 template <bool DET>
 __global__ void __launch_bounds__(256) k_forward_wide(const __grid_constant__ Launch<1> L) {
+  pdl_wait();   // launched early after a kernel that triggers: nothing before it ends
   const Item& it = L.items[0];
   extern __shared__ __align__(16) unsigned char smem[];
   const LensSmem ls = carve_exit(smem, it);

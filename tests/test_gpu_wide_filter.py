@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2302_12031_gb300 import api
+from paper_2302_12031_gb300 import api, step
 from paper_2302_12031_gb300 import workloads as W
 from oracle import oracle as O
 from tests.gpu_helpers import (TOL_E, TOL_GRAD, adjoint_both, ambiguous_rays, forward_both, options_for, random_dLdE,
@@ -110,3 +110,20 @@ def test_wide_filter_refusals():
     E = [torch.zeros(p.ext_shape, device="cuda") for p in pbs]
     with pytest.raises(api.FreerayError):
         api.fr_trace_batch_forward(api.default_handle(), [p.batch_item(E=e) for p, e in zip(pbs, E)], None)
+
+
+@pytest.mark.parametrize("kind", ["coll", "point"])
+def test_wide_filter_graph_step_with_programmatic_launch(kind):
+    # the optimisation step launches the traces programmatically after the
+    # clearing and loss kernels; the wide-filter kernels wait for them, so the
+    # steps agree with the same graph launched without that overlap
+    wl = W.config(1) if kind == "coll" else W.point("p", 1 << 15, 8, 24, 3, 4, 5)
+    wl["target"]["nu_x"] = wl["target"]["nu_y"] = 9
+    a = step.OptimStep(wl, lr=1e-3, graph=True, pdl=True)
+    b = step.OptimStep(wl, lr=1e-3, graph=True, pdl=False)
+    for _ in range(3):
+        a.step()
+        b.step()
+    torch.cuda.synchronize()
+    assert torch.allclose(a.P, b.P, rtol=0, atol=1e-6)
+    assert torch.allclose(a.losses(), b.losses(), rtol=1e-5, atol=0)
