@@ -65,7 +65,7 @@ __device__ __forceinline__ void grad_flush_warp(GradAcc<false>& acc, int ncv, fl
   const bool mine = key == key0;
   float v[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {   // round 1: halves of the 16 terms over lane bit 4
+  for (int i = 0; i < 8; ++i) {   // first exchange: halves of the 16 terms over lane bit 4
     const bool hi = (lane & 16u) != 0;
     const float lo_t = mine ? acc.g[i >> 2][i & 3] : 0.0f;
     const float hi_t = mine ? acc.g[(i + 8) >> 2][(i + 8) & 3] : 0.0f;
