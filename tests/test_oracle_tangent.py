@@ -48,6 +48,15 @@ def test_collimated_tangent_matches_central_differences(oracle, n_ctrl):
     _check_fd(oracle, wl, seed=n_ctrl)
 
 
+@pytest.mark.parametrize("p,q", [(5, 3), (2, 4)])
+def test_other_degree_tangent_matches_central_differences(oracle, p, q):
+    # Sec. 3.1 shows derivative maps of a degree (5, 3) net beside (3, 3)
+    wl = W.collimated("c", 20, 9, 8, 1, 2)
+    wl["lens"]["p"], wl["lens"]["q"] = p, q
+    wl["lens"]["P"] = W.control_heights(9, 9, 0.02, 40 + p)
+    _check_fd(oracle, wl, seed=p)
+
+
 def test_jittered_collimated_tangent_matches_central_differences(oracle):
     wl = W.collimated("c", 24, 6, 10, 3, 4, jitter=1)
     wl["lens"]["P"] = W.control_heights(6, 6, 0.03, 98)
