@@ -30,7 +30,8 @@
  *    call of the same size must run once before capture. A point-source call
  *    traces at most 2^32 - 1 rays.
  *  - A handle is not thread-safe; use one handle per host thread.
- *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported;
+ *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported
+ *    (fr_trace_tangent of a collimated lens: degrees 1 to 5);
  *    control nets from 4x4 to 32x32; filter sizes nu_x = nu_y odd, 1 to 11.
  *    Sizes 7 to 11 run in the wide-filter trace kernels: one single-face lens
  *    per call (FR_ERR_UNSUPPORTED for a batch or a freeform entry face), not
@@ -242,7 +243,11 @@ fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_sour
  * n_dirs extended grids, grid k at dE_out + k*(nx+nu_x-1)*(ny+nu_y-1)). The
  * derivative map of one control point is dP = its unit vector. Same lens,
  * source, screen and rays as fr_trace_forward; deposits use float atomics
- * (not bit-reproducible; options.deterministic is ignored). */
+ * (not bit-reproducible; options.deterministic is ignored). For a collimated
+ * source the lens may also have degrees p, q from 1 to 5 (at least p + 1 and
+ * q + 1 control points; the Sec. 3.1 figure shows (5,3) beside (3,3)): a
+ * second kernel evaluates each ray's basis functions by the Cox-de Boor
+ * recursion; other degrees with a point source: FR_ERR_UNSUPPORTED. */
 fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_source_desc* source,
                            const fr_target_desc* target, uint64_t n_rays, uint64_t seed,
                            uint64_t ray_begin, uint64_t ray_count, const fr_options* options,

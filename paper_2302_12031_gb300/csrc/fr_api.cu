@@ -136,13 +136,21 @@ fr_status ensure_workspace(fr_handle* h, size_t bytes, cudaStream_t st) {
 }
 
 // Checks the public descriptors and fills the device view.
+// any_degree: degrees 1..5 (the general-degree derivative maps); else p = q = 3.
 fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S, const fr_target_desc* T,
                     uint64_t n_rays, uint64_t seed, uint64_t begin, uint64_t count, const fr_options& o,
-                    Item* it) {
+                    Item* it, bool any_degree = false) {
   if (!L || !S || !T) return set_error(h, FR_ERR_INVALID_ARG, "null descriptor");
   std::memset(it, 0, sizeof *it);
   if (!L->ctrl_z) return set_error(h, FR_ERR_INVALID_ARG, "lens.ctrl_z is null");
-  if (L->p != 3 || L->q != 3) return set_error(h, FR_ERR_UNSUPPORTED, "only degrees p = q = 3 are implemented");
+  if (any_degree) {
+    if (L->p < 1 || L->q < 1 || L->p > 5 || L->q > 5)
+      return set_error(h, FR_ERR_UNSUPPORTED, "derivative maps take degrees 1 to 5");
+    if (L->n1 < L->p || L->n2 < L->q)
+      return set_error(h, FR_ERR_INVALID_ARG, "a degree-p net needs at least p + 1 control points");
+  } else if (L->p != 3 || L->q != 3) {
+    return set_error(h, FR_ERR_UNSUPPORTED, "only degrees p = q = 3 are implemented");
+  }
   if (L->n1 < 3 || L->n2 < 3 || L->n1 + 1 > fr::kMaxCtrl || L->n2 + 1 > fr::kMaxCtrl)
     return set_error(h, FR_ERR_UNSUPPORTED, "control net must be between 4x4 and %dx%d", fr::kMaxCtrl,
                      fr::kMaxCtrl);
@@ -167,8 +175,10 @@ fr_status make_item(fr_handle* h, const fr_lens_desc* L, const fr_source_desc* S
   it->ctrl = L->ctrl_z;
   it->ncu = L->n1 + 1;
   it->ncv = L->n2 + 1;
-  it->nsu = it->ncu - 3;
-  it->nsv = it->ncv - 3;
+  it->p = L->p;
+  it->q = L->q;
+  it->nsu = it->ncu - L->p;
+  it->nsv = it->ncv - L->q;
   it->rx = L->rx;
   it->ry = L->ry;
   it->z_in = L->z_in;
@@ -637,13 +647,26 @@ fr_status fr_trace_tangent(fr_handle* h, const fr_lens_desc* lens, const fr_sour
   if (!dP || !dE_out) return set_error(h, FR_ERR_INVALID_ARG, "dP or dE_out is null");
   if (n_dirs < 1 || n_dirs > 32) return set_error(h, FR_ERR_INVALID_ARG, "n_dirs must be 1..32");
   Item it;
-  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it);
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &it, true);
   if (s != FR_OK) return s;
   if (it.two_face) return set_error(h, FR_ERR_UNSUPPORTED, "derivative maps take a flat entry face");
+  const bool general = it.p != 3 || it.q != 3;
+  if (general && it.kind != FR_SOURCE_COLLIMATED)
+    return set_error(h, FR_ERR_UNSUPPORTED, "degrees other than 3: derivative maps of collimated lenses");
   it.stats = stats_out;
   const cudaStream_t st = as_stream(stream);
   if (!o.accumulate)
     FR_CUDA(h, cudaMemsetAsync(dE_out, 0, (size_t)n_dirs * it.ncol * it.nrow * sizeof(float), st), "memset");
+  if (general) {
+    const int warps = o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 8) : 8;
+    schedule_item(&it, warps, o);
+    it.cta_begin = 0;
+    it.cta_end = std::min(std::max(1, h->sm_count * 4), it.max_ctas);
+    if (it.cta_end <= 0) return FR_OK;   // no rays
+    cudaError_t e = fr::launch_tangent_general(it, warps, it.cta_end, dP, n_dirs, dE_out, st);
+    if (e != cudaSuccess) return cuda_error(h, e, "tangent kernel");
+    return FR_OK;
+  }
   const int warps = o.warps_per_cta > 0 ? std::min(o.warps_per_cta, 8) : 8;
   schedule_item(&it, warps, o);
   const size_t smem = fr::tan_smem_bytes(it);

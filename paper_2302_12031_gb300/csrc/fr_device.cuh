@@ -1468,8 +1468,9 @@ __device__ __forceinline__ bool footprint_scalar(const Item& it, float X, float 
   return NU >= 3 || (f.rsx > 0.0f && f.rsy > 0.0f);   // nu = 1 exactly on a pixel edge: all f = 0
 }
 
-// Filter sizes 7, 9, 11 with the size a runtime value (the wide-filter
-// traces): the values of axis_footprint, in loops that are not unrolled.
+// Filter sizes 1 to 11 with the size a runtime value (the wide-filter traces,
+// the general-degree derivative maps): the values of axis_footprint, in loops
+// that are not unrolled.
 constexpr int kWideNu = 11;
 struct FootDyn {
   int ie, je;
@@ -1492,12 +1493,14 @@ __device__ __forceinline__ void axis_footprint_dyn(float g, int n, int nu, float
     f[a] = fmaxf(ex2_approx(-a2 * d * d) - cut, 0.0f);
     sum += f[a];
   }
-  *rs = fast_rcp(sum);   // nu >= 7: the hit's own pixel is inside the support
+  *rs = sum > 0.0f ? fast_rcp(sum) : 0.0f;   // 0 only for nu = 1 exactly on a pixel edge
 }
 
-__device__ __forceinline__ void footprint_dyn(const Item& it, float X, float Y, FootDyn& f) {
+// False when the footprint is empty (nu = 1 exactly on a pixel edge).
+__device__ __forceinline__ bool footprint_dyn(const Item& it, float X, float Y, FootDyn& f) {
   axis_footprint_dyn(fmaf(X, it.inv_wx, it.gx_off), it.nx, it.nu, it.ax, it.cut, &f.ie, &f.dx0, f.fx, &f.rsx);
   axis_footprint_dyn(fmaf(Y, it.inv_wy, it.gy_off), it.ny, it.nu, it.ay, it.cut, &f.je, &f.dy0, f.fy, &f.rsy);
+  return f.rsx > 0.0f && f.rsy > 0.0f;
 }
 
 // filter_grad for a FootDyn: F = f / S and dF/dX (dF/dY) per axis.
@@ -1519,8 +1522,9 @@ __device__ __forceinline__ void filter_grad_dyn(const Item& it, const FootDyn& f
   }
 #pragma unroll 1
   for (int a = 0; a < it.nu; ++a) {
-    gxa[a] = fmaf(-Fx[a], Spx, gxa[a]) * f.rsx;
-    gya[a] = fmaf(-Fy[a], Spy, gya[a]) * f.rsy;
+    // nu = 1: the normalised filter is 1 on its pixel, its derivative 0
+    gxa[a] = it.nu == 1 ? 0.0f : fmaf(-Fx[a], Spx, gxa[a]) * f.rsx;
+    gya[a] = it.nu == 1 ? 0.0f : fmaf(-Fy[a], Spy, gya[a]) * f.rsy;
   }
 }
 

@@ -17,9 +17,11 @@ constexpr int kMaxItems = 64;             // lenses per batched launch
 // Built on the host by the C ABI from the public descriptors.
 struct Item {
   // Lens (Sec. 2.1). Spans are the non-empty knot spans of the clamped uniform
-  // knot vector: nsu = ncu - 3 along u, nsv = ncv - 3 along v.
+  // knot vector: nsu = ncu - p along u, nsv = ncv - q along v (p = q = 3 in
+  // every kernel but the general-degree derivative maps).
   const float* ctrl;
   int ncu, ncv, nsu, nsv;
+  int p, q;
   float rx, ry, z_in, n_glass;
   float ku, kv;                 // d(span coordinate)/dx = nsu/(2 rx), likewise kv
   float R0;                     // ((n-1)/(n+1))^2
@@ -166,6 +168,10 @@ cudaError_t launch_ray_order(const Item& it, int m, uint32_t* counts, uint32_t* 
 size_t tan_smem_bytes(const Item& it);
 cudaError_t launch_tangent(const Item& it, int warps, int grid, size_t smem, const float* dP, int n_dirs, float* dE,
                            cudaStream_t st);
+// Derivative maps of a collimated lens of any degrees 1..5 (p, q of the Item).
+size_t tan_general_smem_bytes(const Item& it);
+cudaError_t launch_tangent_general(const Item& it, int warps, int grid, const float* dP, int n_dirs, float* dE,
+                                   cudaStream_t st);
 int tangent_occupancy(int threads, size_t smem, int nu);
 cudaError_t configure_tangent(int optin);
 cudaError_t configure_forward(int optin);

@@ -248,6 +248,150 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
   RayCount::publish(s_cnt, it.stats);
 }
 
+// Clamped uniform knot vector of degree p with ns non-empty spans:
+// t_j = clamp((j - p) / ns, 0, 1).
+__device__ __forceinline__ float knot_cu(int j, int p, int ns) {
+  return fminf(fmaxf((float)(j - p) / (float)ns, 0.0f), 1.0f);
+}
+
+// The p + 1 basis functions of degree p (p <= 5) that are non-zero on the span
+// of u, N_{k+a,p}(u) for a = 0..p, and their u-derivatives (Sec. 2.1): the
+// Cox-de Boor recursion raised one degree at a time on the span's knots, and
+// N'_{j,p} = p N_{j,p-1} / (t_{j+p} - t_j) - p N_{j+1,p-1} / (t_{j+p+1} - t_{j+1})
+// from the degree p - 1 values. k: the span's first control index.
+__device__ __forceinline__ void basis_general(int p, int ns, float u, int* k_out, float (&N)[6], float (&dN)[6]) {
+  const int k = min((int)(u * (float)ns), ns - 1);
+  const int i = k + p;   // the span is [t_i, t_{i+1})
+  float left[6], right[6], M[6];
+  N[0] = 1.0f;
+  M[0] = 1.0f;
+#pragma unroll 1
+  for (int d = 1; d <= p; ++d) {
+    left[d] = u - knot_cu(i + 1 - d, p, ns);
+    right[d] = knot_cu(i + d, p, ns) - u;
+    float saved = 0.0f;
+#pragma unroll 1
+    for (int r = 0; r < d; ++r) {
+      const float den = right[r + 1] + left[d - r];
+      const float tmp = den != 0.0f ? N[r] / den : 0.0f;
+      N[r] = saved + right[r + 1] * tmp;
+      saved = left[d - r] * tmp;
+    }
+    N[d] = saved;
+    if (d == p - 1)
+#pragma unroll 1
+      for (int r = 0; r < p; ++r) M[r] = N[r];   // degree p - 1: N_{k+1+r,p-1}
+  }
+#pragma unroll 1
+  for (int a = 0; a <= p; ++a) {
+    float v = 0.0f;
+    if (a >= 1) {
+      const float den = knot_cu(i + a, p, ns) - knot_cu(i - p + a, p, ns);
+      if (den != 0.0f) v += M[a - 1] / den;
+    }
+    if (a <= p - 1) {
+      const float den = knot_cu(i + a + 1, p, ns) - knot_cu(i - p + a + 1, p, ns);
+      if (den != 0.0f) v -= M[a] / den;
+    }
+    dN[a] = (float)p * v;
+  }
+  *k_out = k;
+}
+
+// Z and its u- and v-derivatives from a net in `P` (row-major, ncv columns).
+__device__ __forceinline__ void surface_general(const float* P, int ncv, int k, int l, int p, int q,
+                                                const float (&Nu)[6], const float (&dNu)[6], const float (&Nv)[6],
+                                                const float (&dNv)[6], float* Z, float* Zu, float* Zv) {
+  float z = 0.0f, zu = 0.0f, zv = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a <= p; ++a) {
+    float c = 0.0f, cv = 0.0f;
+#pragma unroll 1
+    for (int b = 0; b <= q; ++b) {
+      const float w = P[(k + a) * ncv + l + b];
+      c = fmaf(Nv[b], w, c);
+      cv = fmaf(dNv[b], w, cv);
+    }
+    z = fmaf(Nu[a], c, z);
+    zu = fmaf(dNu[a], c, zu);
+    zv = fmaf(Nu[a], cv, zv);
+  }
+  *Z = z;
+  *Zu = zu;
+  *Zv = zv;
+}
+
+// Derivative maps of a collimated lens of degrees (p, q), 1 <= p, q <= 5 (the
+// Sec. 3.1 figure shows (5, 3) beside (3, 3)), filter sizes 1 to 11: each lane
+// traces its run of cells with the basis functions of the ray's span computed
+// by the recursion (no power-form tables), and adds
+//   dE_ij += (dw F_ij + w (dF_ij/dX dX + dF_ij/dY dY)) / (w_x w_y)
+// for every direction with global atomics, as k_tangent.
+__global__ void __launch_bounds__(256) k_tangent_general(const __grid_constant__ Item it, int warps,
+                                                         const float* __restrict__ dP, int n_dirs,
+                                                         float* __restrict__ dE) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* s_P = reinterpret_cast<float*>(smem);   // the heights
+  __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
+  const int nctrl = it.ncu * it.ncv;
+  for (int q = threadIdx.x; q < nctrl; q += blockDim.x) s_P[q] = __ldg(it.ctrl + q);
+  if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const size_t cells = (size_t)it.ncol * it.nrow;
+  const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
+  const float inv_nsu = 1.0f / (float)it.nsu, inv_nsv = 1.0f / (float)it.nsv;
+  RayCount cnt{0u};
+  unsigned int* cnt_dst = it.stats ? s_cnt : nullptr;
+  uint64_t a0, a1;
+  lane_range(it, warps, &a0, &a1);
+  for (uint64_t id = a0; id < a1; ++id) {
+    const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
+    float ja = 0.5f, jb = 0.5f;
+    if (it.jitter) {
+      const uint2 w = philox_ray_words(it.seed, id);
+      ja = unit23(w.x);
+      jb = unit23(w.y);
+    }
+    const float u = ((float)col + ja) * inv_cols, v = ((float)row + jb) * inv_rows;
+    float Nu[6], dNu[6], Nv[6], dNv[6];
+    int k, l;
+    basis_general(it.p, it.nsu, u, &k, Nu, dNu);
+    basis_general(it.q, it.nsv, v, &l, Nv, dNv);
+    float Z, Zu, Zv;
+    surface_general(s_P, it.ncv, k, l, it.p, it.q, Nu, dNu, Nv, dNv, &Z, &Zu, &Zv);
+    RayFwd r;
+    // slopes per unit of span coordinate s = u nsu - k, as the cubic kernels
+    collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zu * inv_nsu, Zv * inv_nsv, r);
+    cnt.add(r.status, cnt_dst);
+    if (r.status != FR_RAY_ON_SCREEN) continue;
+    FootDyn f;
+    if (!footprint_dyn(it, r.X, r.Y, f)) continue;
+    float Fx[kWideNu], Fy[kWideNu], gx[kWideNu], gy[kWideNu];
+    filter_grad_dyn(it, f, Fx, Fy, gx, gy);
+    const float K = r.w * it.inv_area;
+#pragma unroll 1
+    for (int q = 0; q < n_dirs; ++q) {
+      float dZ, dZu, dZv;
+      surface_general(dP + (size_t)q * nctrl, it.ncv, k, l, it.p, it.q, Nu, dNu, Nv, dNv, &dZ, &dZu, &dZv);
+      const RayTan tg = ray_tangent<true>(it, r, 0.0f, 0.0f, dZ, dZu * inv_nsu, dZv * inv_nsv);
+      const float cw = tg.dw * it.inv_area, cx = K * tg.dX, cy = K * tg.dY;
+      float* base = dE + (size_t)q * cells + (size_t)f.je * it.ncol + f.ie;
+#pragma unroll 1
+      for (int b = 0; b < it.nu; ++b) {
+        const float rb = cw * Fy[b], sb = cx * Fy[b], tb = cy * gy[b];
+#pragma unroll 1
+        for (int a = 0; a < it.nu; ++a) {
+          const float val = fmaf(rb, Fx[a], fmaf(sb, gx[a], tb * Fx[a]));
+          if (val != 0.0f) atomicAdd(base + b * it.ncol + a, val);
+        }
+      }
+    }
+  }
+  cnt.reduce_into(cnt_dst);
+  __syncthreads();
+  RayCount::publish(s_cnt, it.stats);
+}
+
 using TanKernel = void (*)(Item, int, const float*, int, float*);
 
 TanKernel pick_tangent(int nu) {
@@ -262,6 +406,14 @@ TanKernel pick_tangent(int nu) {
 }
 
 }  // namespace
+
+size_t tan_general_smem_bytes(const Item& it) { return (size_t)it.ncu * it.ncv * sizeof(float); }
+
+cudaError_t launch_tangent_general(const Item& it, int warps, int grid, const float* dP, int n_dirs, float* dE,
+                                   cudaStream_t st) {
+  k_tangent_general<<<grid, warps * 32, tan_general_smem_bytes(it), st>>>(it, warps, dP, n_dirs, dE);
+  return cudaGetLastError();
+}
 
 size_t tan_smem_bytes(const Item& it) {
   return ((lens_smem_bytes(it.nsu, it.nsv, needs_hull(it)) + 15) & ~(size_t)15) + (size_t)it.nsu * it.nsv * 4;

@@ -146,3 +146,47 @@ def test_flat_lens_maps_sum_to_zero_for_both_filter_sizes():
         # zero up to FP32 rounding of the float-atomic sums: the map's terms
         # cancel to ~1e-5 of their absolute sum
         assert abs(float(t.sum())) < 5e-5 * float(t.abs().sum())
+
+
+@pytest.mark.parametrize("p,q,nu", [(5, 3, 3), (5, 3, 11), (2, 4, 1), (3, 5, 5)])
+def test_other_degree_maps_match_oracle(p, q, nu):
+    # Sec. 3.1 shows derivative maps of a degree (5, 3) net beside (3, 3): the
+    # general-degree kernel against the oracle's maps (which take any degree)
+    wl = W.collimated("c", 192, 9, 24, 1, 2, with_target=False, jitter=1 if q == 5 else 0)
+    wl["lens"]["p"], wl["lens"]["q"] = p, q
+    wl["target"]["nu_x"] = wl["target"]["nu_y"] = nu
+    rng = np.random.default_rng(p * 10 + q)
+    dP = np.stack([rng.normal(size=wl["lens"]["P"].shape), _unit(wl, 4, 3), _unit(wl, 0, 8)])
+    pb = api.Problem(wl)
+    g = pb.tangent(dP).cpu().numpy().astype(np.float64)
+    o = O.trace_tangent(wl, dP)
+    # the rays within rounding of a pixel edge or of the screen's edge (the
+    # debug kernel behind ambiguous_rays takes degree 3 only), out of both sides
+    rec = O.trace_records(wl)
+    t = wl["target"]
+    wx, wy = 2 * t["Rx"] / t["nx"], 2 * t["Ry"] / t["ny"]
+    fx = (rec["X"] + t["Rx"] + (nu - 1) / 2 * wx) / wx
+    fy = (rec["Y"] + t["Ry"] + (nu - 1) / 2 * wy) / wy
+    near = lambda f: np.minimum(f - np.floor(f), np.ceil(f) - f) < 1e-4
+    rim = (np.abs(np.abs(rec["X"]) - t["Rx"]) < 1e-4 * wx) | (np.abs(np.abs(rec["Y"]) - t["Ry"]) < 1e-4 * wy)
+    amb = np.nonzero(((rec["status"] == 0) & (near(fx) | near(fy))) | rim)[0]
+    assert len(amb) <= max(3, 2e-3 * wl["n_rays"]), len(amb)
+    for rid in amb:
+        g -= pb.tangent(dP, ray_begin=int(rid), ray_count=1).cpu().numpy()
+        o -= O.trace_tangent(wl, dP, begin=int(rid), count=1)
+    for k in range(3):
+        assert rel_l2(g[k], o[k]) < TOL_GRAD, (k, rel_l2(g[k], o[k]))
+
+
+def test_other_degrees_refused_elsewhere():
+    wl = W.collimated("c", 64, 8, 16, 1, 2, with_target=False)
+    wl["lens"]["p"] = 5
+    pb = api.Problem(wl)
+    with pytest.raises(api.FreerayError):
+        pb.forward()
+    with pytest.raises(api.FreerayError):
+        pb.adjoint(torch.zeros(pb.ext_shape, device="cuda"))
+    wp = W.point("p", 4096, 8, 16, 3, 4, 5, with_target=False)
+    wp["lens"]["p"] = 5
+    with pytest.raises(api.FreerayError):
+        api.Problem(wp).tangent(_unit(wp, 3, 3))
