@@ -30,8 +30,11 @@
  *    call of the same size must run once before capture. A point-source call
  *    traces at most 2^32 - 1 rays.
  *  - A handle is not thread-safe; use one handle per host thread.
- *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported
- *    (fr_trace_tangent of a collimated lens: degrees 1 to 5);
+ *  - Only clamped uniform knot vectors and degrees p = q = 3 are supported,
+ *    except that a collimated single-face lens may have degrees p, q from 1
+ *    to 5 in fr_trace_forward, fr_trace_adjoint and fr_trace_tangent (one
+ *    lens per call; general-degree kernels evaluate each ray's basis
+ *    functions by the Cox-de Boor recursion);
  *    control nets from 4x4 to 32x32; filter sizes nu_x = nu_y odd, 1 to 11.
  *    Sizes 7 to 11 run in the wide-filter trace kernels: one single-face lens
  *    per call (FR_ERR_UNSUPPORTED for a batch or a freeform entry face), not

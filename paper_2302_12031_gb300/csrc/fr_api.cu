@@ -398,9 +398,12 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
                     cudaStream_t st) {
   if (o.ray_order && items.size() > 1)
     return set_error(h, FR_ERR_INVALID_ARG, "ray_order applies to one lens, not to a batch");
-  for (auto& it : items)
+  for (auto& it : items) {
     if (it.nu > 5 && (CAP > 1 || items.size() > 1 || it.two_face))
       return set_error(h, FR_ERR_UNSUPPORTED, "filter sizes 7, 9, 11: one single-face lens per call");
+    if ((it.p != 3 || it.q != 3) && (CAP > 1 || items.size() > 1 || it.two_face || it.kind != FR_SOURCE_COLLIMATED))
+      return set_error(h, FR_ERR_UNSUPPORTED, "degrees other than 3: one collimated single-face lens per call");
+  }
   bool det = o.deterministic != 0;
   // A point-source forward privatises a window of its grid (plan_window); in a
   // batch every item whose grid does not fit does (two CTAs per SM).
@@ -428,9 +431,10 @@ fr_status run_trace(fr_handle* h, std::vector<Item>& items, const fr_options& o,
   // The one CTA per SM of the window form: 20 warps with filter sizes 1 and 3
   // (the kernel's launch bounds allow 640 threads there), 16 with 5; else pick_warps.
   const int win_cap = items[0].nu <= 3 ? 20 : 16;
-  const int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, win_cap) : win_cap)
-                           : pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind : -1,
-                                        det, items[0].nu);
+  int warps = window ? (o.warps_per_cta > 0 ? std::min(o.warps_per_cta, win_cap) : win_cap)
+                     : pick_warps(o, adjoint, items.size() == 1 && !items[0].two_face ? items[0].kind : -1,
+                                  det, items[0].nu);
+  if (items[0].p != 3 || items[0].q != 3) warps = std::min(warps, 8);   // the general-degree kernels: 256 threads
   // Workspace.
   size_t at = kHeaderBytes;
   std::vector<ItemWs> ws(items.size());
@@ -611,7 +615,7 @@ fr_status fr_trace_forward(fr_handle* h, const fr_lens_desc* lens, const fr_sour
   const fr_options o = defaults(options);
   if (!E_out) return set_error(h, FR_ERR_INVALID_ARG, "E_out is null");
   std::vector<Item> items(1);
-  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &items[0]);
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &items[0], true);
   if (s != FR_OK) return s;
   items[0].E = E_out;
   items[0].stats = stats_out;
@@ -628,7 +632,7 @@ fr_status fr_trace_adjoint(fr_handle* h, const fr_lens_desc* lens, const fr_sour
   const fr_options o = defaults(options);
   if (!dLdE || !dLdP_out) return set_error(h, FR_ERR_INVALID_ARG, "dLdE or dLdP_out is null");
   std::vector<Item> items(1);
-  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &items[0]);
+  fr_status s = make_item(h, lens, source, target, n_rays, seed, ray_begin, ray_count, o, &items[0], true);
   if (s != FR_OK) return s;
   items[0].dLdE = dLdE;
   items[0].dLdP = dLdP_out;

@@ -168,6 +168,8 @@ __host__ __device__ inline bool needs_hull(const Item& it) { return it.kind == F
 
 // Bytes of all lens tables of an item (the exit net's, then the entry net's).
 __host__ __device__ inline size_t tables_bytes(const Item& it) {
+  // a lens of other degrees (collimated, general-degree kernels): its heights
+  if (it.p != 3 || it.q != 3) return ((size_t)it.ncu * it.ncv * sizeof(float) + 15) & ~(size_t)15;
   const bool h = needs_hull(it);
   size_t b = (lens_smem_bytes(it.nsu, it.nsv, h) + 15) & ~(size_t)15;
   if (it.two_face) b += (lens_smem_bytes(it.nsu_in, it.nsv_in, h) + 15) & ~(size_t)15;
@@ -1466,6 +1468,107 @@ __device__ __forceinline__ bool footprint_scalar(const Item& it, float X, float 
   axis_footprint<NU>(gx, it.nx, it.ax, it.cut, &f.ie, &f.dx0, f.fx, &f.rsx);
   axis_footprint<NU>(gy, it.ny, it.ay, it.cut, &f.je, &f.dy0, f.fy, &f.rsy);
   return NU >= 3 || (f.rsx > 0.0f && f.rsy > 0.0f);   // nu = 1 exactly on a pixel edge: all f = 0
+}
+
+// ---------------------------------------------------------------------------
+// Lenses of degrees p, q from 1 to 5 (collimated sources only): the basis
+// functions of each ray's span by the recursion, the heights in shared memory.
+// ---------------------------------------------------------------------------
+// Clamped uniform knot vector of degree p with ns non-empty spans:
+// t_j = clamp((j - p) / ns, 0, 1).
+__device__ __forceinline__ float knot_cu(int j, int p, int ns) {
+  return fminf(fmaxf((float)(j - p) / (float)ns, 0.0f), 1.0f);
+}
+
+// The p + 1 basis functions of degree p (p <= 5) that are non-zero on the span
+// of u, N_{k+a,p}(u) for a = 0..p, and their u-derivatives (Sec. 2.1): the
+// Cox-de Boor recursion raised one degree at a time on the span's knots, and
+// N'_{j,p} = p N_{j,p-1} / (t_{j+p} - t_j) - p N_{j+1,p-1} / (t_{j+p+1} - t_{j+1})
+// from the degree p - 1 values. k: the span's first control index.
+__device__ __forceinline__ void basis_general(int p, int ns, float u, int* k_out, float (&N)[6], float (&dN)[6]) {
+  const int k = min((int)(u * (float)ns), ns - 1);
+  const int i = k + p;   // the span is [t_i, t_{i+1})
+  float left[6], right[6], M[6];
+  N[0] = 1.0f;
+  M[0] = 1.0f;
+#pragma unroll 1
+  for (int d = 1; d <= p; ++d) {
+    left[d] = u - knot_cu(i + 1 - d, p, ns);
+    right[d] = knot_cu(i + d, p, ns) - u;
+    float saved = 0.0f;
+#pragma unroll 1
+    for (int r = 0; r < d; ++r) {
+      const float den = right[r + 1] + left[d - r];
+      const float tmp = den != 0.0f ? N[r] / den : 0.0f;
+      N[r] = saved + right[r + 1] * tmp;
+      saved = left[d - r] * tmp;
+    }
+    N[d] = saved;
+    if (d == p - 1)
+#pragma unroll 1
+      for (int r = 0; r < p; ++r) M[r] = N[r];   // degree p - 1: N_{k+1+r,p-1}
+  }
+#pragma unroll 1
+  for (int a = 0; a <= p; ++a) {
+    float v = 0.0f;
+    if (a >= 1) {
+      const float den = knot_cu(i + a, p, ns) - knot_cu(i - p + a, p, ns);
+      if (den != 0.0f) v += M[a - 1] / den;
+    }
+    if (a <= p - 1) {
+      const float den = knot_cu(i + a + 1, p, ns) - knot_cu(i - p + a + 1, p, ns);
+      if (den != 0.0f) v -= M[a] / den;
+    }
+    dN[a] = (float)p * v;
+  }
+  *k_out = k;
+}
+
+// Z and its u- and v-derivatives from a net in `P` (row-major, ncv columns).
+__device__ __forceinline__ void surface_general(const float* P, int ncv, int k, int l, int p, int q,
+                                                const float (&Nu)[6], const float (&dNu)[6], const float (&Nv)[6],
+                                                const float (&dNv)[6], float* Z, float* Zu, float* Zv) {
+  float z = 0.0f, zu = 0.0f, zv = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a <= p; ++a) {
+    float c = 0.0f, cv = 0.0f;
+#pragma unroll 1
+    for (int b = 0; b <= q; ++b) {
+      const float w = P[(k + a) * ncv + l + b];
+      c = fmaf(Nv[b], w, c);
+      cv = fmaf(dNv[b], w, cv);
+    }
+    z = fmaf(Nu[a], c, z);
+    zu = fmaf(dNu[a], c, zu);
+    zv = fmaf(Nu[a], cv, zv);
+  }
+  *Z = z;
+  *Zu = zu;
+  *Zv = zv;
+}
+
+// Collimated ray `id` (cell centre or jittered) through a general-degree lens
+// whose heights are in sP: its span (k, l), the basis functions and their
+// u- and v-derivatives, and the traced ray. The slopes passed on are per unit
+// of span coordinate (s = u nsu - k), as the bicubic kernels'.
+__device__ __forceinline__ void trace_collimated_general(const Item& it, const float* sP, uint64_t id, float inv_cols,
+                                                         float inv_rows, RayFwd& r, int* k, int* l, float (&Nu)[6],
+                                                         float (&dNu)[6], float (&Nv)[6], float (&dNv)[6]) {
+  const uint32_t row = (uint32_t)(id / (uint64_t)it.cols), col = (uint32_t)(id % (uint64_t)it.cols);
+  float ja = 0.5f, jb = 0.5f;
+  if (it.jitter) {
+    const uint2 w = philox_ray_words(it.seed, id);
+    ja = unit23(w.x);
+    jb = unit23(w.y);
+  }
+  const float u = ((float)col + ja) * inv_cols, v = ((float)row + jb) * inv_rows;
+  basis_general(it.p, it.nsu, u, k, Nu, dNu);
+  basis_general(it.q, it.nsv, v, l, Nv, dNv);
+  float Z, Zu, Zv;
+  surface_general(sP, it.ncv, *k, *l, it.p, it.q, Nu, dNu, Nv, dNv, &Z, &Zu, &Zv);
+  collimated_at(it, u, v, fmaf(2.0f, v, -1.0f) * it.ry, Z, Zu / (float)it.nsu, Zv / (float)it.nsv, r);
+  r.k = *k;
+  r.l = *l;
 }
 
 // Filter sizes 1 to 11 with the size a runtime value (the wide-filter traces,

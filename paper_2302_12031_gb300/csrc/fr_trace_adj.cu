@@ -629,18 +629,23 @@ __global__ void __launch_bounds__(256) k_adjoint_deferred(const __grid_constant_
 // Deterministic mode: int64 fixed point -> float gradient, with the scale the
 // adjoint kernel used (recomputed from the same device value).
 // Adjoint for filter sizes 7, 9 and 11 (one single-face lens per launch, the
-// size a runtime value): each lane traces its run of rays (of ordered
-// positions for a point source in the ray order), point sources with the
-// march in the kernel; per ray the footprint's dL/dE is read from global
-// memory inside the contraction (W = sum G F_x F_y, Xs = sum G F'_x F_y,
-// Ys = sum G F_x F'_y), ray_reverse_tail gives the adjoints of the hit, and
-// add_ray_grad sums the 16 terms as in the other kernels.
-template <bool DET>
+// size a runtime value) and, GEN, for a collimated lens of other degrees (any
+// filter size): each lane traces its run of rays (of ordered positions for a
+// point source in the ray order), point sources with the march in the
+// kernel, GEN lenses by the basis recursion on the heights in shared memory;
+// per ray the footprint's dL/dE is read from global memory inside the
+// contraction (W = sum G F_x F_y, Xs = sum G F'_x F_y, Ys = sum G F_x F'_y),
+// ray_reverse_tail gives the adjoints of the hit, and add_ray_grad sums the 16
+// terms as in the other kernels (GEN: the (p+1)(q+1) terms
+// zeta N_a N_b + Zs_bar dN_a/ds N_b + Zt_bar N_a dN_b/dt go to the CTA's copy
+// of dL/dP ray by ray).
+template <bool DET, bool GEN>
 __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ Launch<1> L) {
   pdl_wait();   // launched early after a kernel that triggers: nothing before it ends
   const Item& it = L.items[0];
   extern __shared__ __align__(16) unsigned char smem[];
-  const LensSmem ls = carve_exit(smem, it);
+  const LensSmem ls = GEN ? LensSmem{} : carve_exit(smem, it);
+  float* sP = reinterpret_cast<float*>(smem);
   unsigned char* grad_raw = smem + tables_bytes(it);
   GradOut go;
   go.s_group = nullptr;
@@ -653,7 +658,12 @@ __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ La
   }
   __shared__ unsigned int s_cnt[FR_RAY_NCAUSES];
   if (threadIdx.x < FR_RAY_NCAUSES) s_cnt[threadIdx.x] = 0u;
-  build_lens_tables(it, ls);   // ends with __syncthreads
+  if constexpr (GEN) {
+    for (int q = threadIdx.x; q < it.ncu * it.ncv; q += blockDim.x) sP[q] = __ldg(it.ctrl + q);
+    __syncthreads();
+  } else {
+    build_lens_tables(it, ls);   // ends with __syncthreads
+  }
   go.fixP = 0.0f;
   if constexpr (DET) {   // the scale of k_adjoint
     const float unit = *it.gmax * it.fixP_unit;
@@ -663,7 +673,7 @@ __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ La
   }
   float zmin = 0.0f, zmax = 0.0f;
   const bool coll = it.kind == FR_SOURCE_COLLIMATED;
-  if (!coll) zbounds(ls, &zmin, &zmax);
+  if (!GEN && !coll) zbounds(ls, &zmin, &zmax);
   const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
   uint64_t a, b;
   lane_range(it, L.warps, &a, &b);
@@ -674,7 +684,11 @@ __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ La
   acc.k = -1;
   for (uint64_t p = a; p < b; ++p) {
     RayFwd r;
-    if (coll) {
+    int gk = 0, gl = 0;
+    float gNu[6], gdNu[6], gNv[6], gdNv[6];
+    if constexpr (GEN) {
+      trace_collimated_general(it, sP, p, inv_cols, inv_rows, r, &gk, &gl, gNu, gdNu, gNv, gdNv);
+    } else if (coll) {
       const uint32_t row = (uint32_t)(p / (uint64_t)it.cols), col = (uint32_t)(p % (uint64_t)it.cols);
       trace_collimated(it, ls, row, col, p, inv_cols, inv_rows, r);
     } else {
@@ -683,7 +697,7 @@ __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ La
     cnt.add(r.status, cnt_dst);
     if (r.status != FR_RAY_ON_SCREEN) continue;
     FootDyn f;
-    footprint_dyn(it, r.X, r.Y, f);
+    if (!footprint_dyn(it, r.X, r.Y, f)) continue;
     float Fx[kWideNu], Fy[kWideNu], gxa[kWideNu], gya[kWideNu];
     filter_grad_dyn(it, f, Fx, Fy, gxa, gya);
     float W = 0.0f, Xs = 0.0f, Ys = 0.0f;
@@ -702,6 +716,22 @@ __global__ void __launch_bounds__(256) k_adjoint_wide(const __grid_constant__ La
       Ys = fmaf(B, Fx[ca], Ys);
     }
     float zeta, Zsb, Ztb, Nv[4], dNv[4];
+    if constexpr (GEN) {
+      ray_reverse_tail<true>(it, ls, r, W, Xs, Ys, &zeta, &Zsb, &Ztb);
+      const float isu = 1.0f / (float)it.nsu, isv = 1.0f / (float)it.nsv;
+#pragma unroll 1
+      for (int ca = 0; ca <= it.p; ++ca) {
+        const float A = fmaf(zeta, gNu[ca], Zsb * gdNu[ca] * isu), B = Ztb * gNu[ca] * isv;
+#pragma unroll 1
+        for (int cb = 0; cb <= it.q; ++cb) {
+          const float c = fmaf(A, gNv[cb], B * gdNv[cb]);
+          const int idx = (gk + ca) * it.ncv + gl + cb;
+          if constexpr (DET) atomicAdd(go.sg_q + idx, (unsigned long long)__float2ll_rn(c * go.fixP));
+          else if (c != 0.0f) atomicAdd(go.sg_f + idx, c);
+        }
+      }
+      continue;
+    }
     basis_eval(ls.bv + r.l * 4, r.t, Nv, dNv);
     if (coll) {
       ray_reverse_tail<true>(it, ls, r, W, Xs, Ys, &zeta, &Zsb, &Ztb);
@@ -756,7 +786,7 @@ template <int CAP>
 AdjKernel<CAP> pick_adjoint(bool det, int nu, int kinds);
 template <>
 AdjKernel<1> pick_adjoint<1>(bool det, int nu, int kinds) {
-  if (nu > 5) return det ? k_adjoint_wide<true> : k_adjoint_wide<false>;   // filter sizes 7, 9, 11
+  if (nu > 5) return det ? k_adjoint_wide<true, false> : k_adjoint_wide<false, false>;   // filter sizes 7, 9, 11
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
   if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
   return det ? pick_nu<1, true, 2>(nu) : pick_nu<1, false, 2>(nu);
@@ -769,6 +799,11 @@ AdjKernel<kMaxItems> pick_adjoint<kMaxItems>(bool det, int nu, int) {
 template <int CAP>
 cudaError_t launch_adjoint(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl) {
   const int threads = 32 * L.warps;
+  if constexpr (CAP == 1) {
+    if (L.items[0].p != 3 || L.items[0].q != 3)   // a collimated lens of other degrees
+      return launch_k(det ? k_adjoint_wide<true, true> : k_adjoint_wide<false, true>, dim3(grid), dim3(threads),
+                      smem, st, pdl, L);
+  }
   const int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
   return launch_k(pick_adjoint<CAP>(det, L.items[0].nu, kinds), dim3(grid), dim3(threads), smem, st, pdl, L);
 }
@@ -824,8 +859,10 @@ cudaError_t configure_adjoint(int optin) {
       if ((e = allow_max_smem(pick_adjoint_deferred<1>(det != 0, nu), optin))) return e;
       if ((e = allow_max_smem(pick_adjoint_deferred<kMaxItems>(det != 0, nu), optin))) return e;
     }
-  if ((e = allow_max_smem(k_adjoint_wide<false>, optin))) return e;
-  if ((e = allow_max_smem(k_adjoint_wide<true>, optin))) return e;
+  if ((e = allow_max_smem(k_adjoint_wide<false, false>, optin))) return e;
+  if ((e = allow_max_smem(k_adjoint_wide<true, false>, optin))) return e;
+  if ((e = allow_max_smem(k_adjoint_wide<false, true>, optin))) return e;
+  if ((e = allow_max_smem(k_adjoint_wide<true, true>, optin))) return e;
   return cudaSuccess;
 }
 

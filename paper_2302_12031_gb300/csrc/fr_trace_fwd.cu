@@ -515,19 +515,22 @@ __global__ void __launch_bounds__(256) k_forward_deferred(const __grid_constant_
 
 // The full record of every ray of [ray_begin, ray_end), one thread per ray.
 // Forward trace for filter sizes 7, 9 and 11 (one single-face lens per
-// launch, the size a runtime value): each lane traces its run of rays (of
-// ordered positions for a point source in the ray order), point sources with
-// the march in the kernel, and adds every ray's nu x nu footprint straight to
-// the privatised histogram (float or, deterministic, int64 fixed point) when
-// the grid fits in shared memory, else to global memory. The per-ray terms are
+// launch, the size a runtime value) and, GEN, for a collimated lens of other
+// degrees (any filter size): each lane traces its run of rays (of ordered
+// positions for a point source in the ray order), point sources with the
+// march in the kernel, GEN lenses by the basis recursion on the heights in
+// shared memory, and adds every ray's nu x nu footprint straight to the
+// privatised histogram (float or, deterministic, int64 fixed point) when the
+// grid fits in shared memory, else to global memory. The per-ray terms are
 // those of `deposit`: kx_a ky_b with kx_a = w/(w_x w_y) f_a / S_x and
 // ky_b = f_b / S_y.
-template <bool DET>
+template <bool DET, bool GEN>
 __global__ void __launch_bounds__(256) k_forward_wide(const __grid_constant__ Launch<1> L) {
   pdl_wait();   // launched early after a kernel that triggers: nothing before it ends
   const Item& it = L.items[0];
   extern __shared__ __align__(16) unsigned char smem[];
-  const LensSmem ls = carve_exit(smem, it);
+  const LensSmem ls = GEN ? LensSmem{} : carve_exit(smem, it);
+  float* sP = reinterpret_cast<float*>(smem);
   const bool sh = it.smem_hist == 1;
   float* sh_f = reinterpret_cast<float*>(smem + tables_bytes(it));
   unsigned long long* sh_q = reinterpret_cast<unsigned long long*>(smem + tables_bytes(it));
@@ -541,9 +544,14 @@ __global__ void __launch_bounds__(256) k_forward_wide(const __grid_constant__ La
       if constexpr (DET) sh_q[q] = 0ull;
       else sh_f[q] = 0.0f;
     }
-  build_lens_tables(it, ls);   // ends with __syncthreads
+  if constexpr (GEN) {
+    for (int q = threadIdx.x; q < it.ncu * it.ncv; q += blockDim.x) sP[q] = __ldg(it.ctrl + q);
+    __syncthreads();
+  } else {
+    build_lens_tables(it, ls);   // ends with __syncthreads
+  }
   float zmin = 0.0f, zmax = 0.0f;
-  if (it.kind == FR_SOURCE_POINT) zbounds(ls, &zmin, &zmax);
+  if (!GEN && it.kind == FR_SOURCE_POINT) zbounds(ls, &zmin, &zmax);
   const float inv_cols = 1.0f / (float)it.cols, inv_rows = 1.0f / (float)it.rows;
   uint64_t a, b;
   lane_range(it, L.warps, &a, &b);
@@ -553,7 +561,11 @@ __global__ void __launch_bounds__(256) k_forward_wide(const __grid_constant__ La
   Bbox bb{0x7fffffff, -1, 0x7fffffff, -1};
   for (uint64_t p = a; p < b; ++p) {
     RayFwd r;
-    if (it.kind == FR_SOURCE_COLLIMATED) {
+    if constexpr (GEN) {
+      int k, l;
+      float Nu[6], dNu[6], Nv[6], dNv[6];
+      trace_collimated_general(it, sP, p, inv_cols, inv_rows, r, &k, &l, Nu, dNu, Nv, dNv);
+    } else if (it.kind == FR_SOURCE_COLLIMATED) {
       const uint32_t row = (uint32_t)(p / (uint64_t)it.cols), col = (uint32_t)(p % (uint64_t)it.cols);
       trace_collimated(it, ls, row, col, p, inv_cols, inv_rows, r);
     } else {
@@ -562,7 +574,7 @@ __global__ void __launch_bounds__(256) k_forward_wide(const __grid_constant__ La
     cnt.add(r.status, cnt_dst);
     if (r.status != FR_RAY_ON_SCREEN) continue;
     FootDyn f;
-    footprint_dyn(it, r.X, r.Y, f);
+    if (!footprint_dyn(it, r.X, r.Y, f)) continue;
     bb.imin = min(bb.imin, f.ie);
     bb.imax = max(bb.imax, f.ie);
     bb.jmin = min(bb.jmin, f.je);
@@ -694,7 +706,7 @@ template <int CAP>
 FwdKernel<CAP> pick_forward(bool det, int nu, int kinds);
 template <>
 FwdKernel<1> pick_forward<1>(bool det, int nu, int kinds) {
-  if (nu > 5) return det ? k_forward_wide<true> : k_forward_wide<false>;   // filter sizes 7, 9, 11
+  if (nu > 5) return det ? k_forward_wide<true, false> : k_forward_wide<false, false>;   // filter sizes 7, 9, 11
   if (kinds == 1) return det ? pick_nu<1, true, 1>(nu) : pick_nu<1, false, 1>(nu);
   if (kinds == 4) return det ? pick_nu<1, true, 7>(nu) : pick_nu<1, false, 7>(nu);   // two-face lens
   if (kinds == 8) return det ? pick_nu<1, true, 10>(nu) : pick_nu<1, false, 10>(nu);  // point, march in the kernel
@@ -709,6 +721,11 @@ template <int CAP>
 cudaError_t launch_forward(const Launch<CAP>& L, int grid, size_t smem, bool det, cudaStream_t st, bool pdl,
                            bool march) {
   const int threads = 32 * L.warps;
+  if constexpr (CAP == 1) {
+    if (L.items[0].p != 3 || L.items[0].q != 3)   // a collimated lens of other degrees
+      return launch_k(det ? k_forward_wide<true, true> : k_forward_wide<false, true>, dim3(grid), dim3(threads),
+                      smem, st, pdl, L);
+  }
   int kinds = L.items[0].two_face ? 4 : (L.items[0].kind == FR_SOURCE_COLLIMATED ? 1 : 2);
   if (march && kinds == 2) kinds = 8;
   return launch_k(pick_forward<CAP>(det, L.items[0].nu, kinds), dim3(grid), dim3(threads), smem, st, pdl, L);
@@ -771,8 +788,10 @@ cudaError_t configure_forward(int optin) {
       if ((e = allow_max_smem(pick_forward_deferred<1>(det != 0, nu), optin))) return e;
       if ((e = allow_max_smem(pick_forward_deferred<kMaxItems>(det != 0, nu), optin))) return e;
     }
-  if ((e = allow_max_smem(k_forward_wide<false>, optin))) return e;
-  if ((e = allow_max_smem(k_forward_wide<true>, optin))) return e;
+  if ((e = allow_max_smem(k_forward_wide<false, false>, optin))) return e;
+  if ((e = allow_max_smem(k_forward_wide<true, false>, optin))) return e;
+  if ((e = allow_max_smem(k_forward_wide<false, true>, optin))) return e;
+  if ((e = allow_max_smem(k_forward_wide<true, true>, optin))) return e;
   return cudaSuccess;
 }
 

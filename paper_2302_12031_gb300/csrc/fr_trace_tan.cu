@@ -248,79 +248,6 @@ __global__ void __launch_bounds__(256, 2) k_tangent(const __grid_constant__ Item
   RayCount::publish(s_cnt, it.stats);
 }
 
-// Clamped uniform knot vector of degree p with ns non-empty spans:
-// t_j = clamp((j - p) / ns, 0, 1).
-__device__ __forceinline__ float knot_cu(int j, int p, int ns) {
-  return fminf(fmaxf((float)(j - p) / (float)ns, 0.0f), 1.0f);
-}
-
-// The p + 1 basis functions of degree p (p <= 5) that are non-zero on the span
-// of u, N_{k+a,p}(u) for a = 0..p, and their u-derivatives (Sec. 2.1): the
-// Cox-de Boor recursion raised one degree at a time on the span's knots, and
-// N'_{j,p} = p N_{j,p-1} / (t_{j+p} - t_j) - p N_{j+1,p-1} / (t_{j+p+1} - t_{j+1})
-// from the degree p - 1 values. k: the span's first control index.
-__device__ __forceinline__ void basis_general(int p, int ns, float u, int* k_out, float (&N)[6], float (&dN)[6]) {
-  const int k = min((int)(u * (float)ns), ns - 1);
-  const int i = k + p;   // the span is [t_i, t_{i+1})
-  float left[6], right[6], M[6];
-  N[0] = 1.0f;
-  M[0] = 1.0f;
-#pragma unroll 1
-  for (int d = 1; d <= p; ++d) {
-    left[d] = u - knot_cu(i + 1 - d, p, ns);
-    right[d] = knot_cu(i + d, p, ns) - u;
-    float saved = 0.0f;
-#pragma unroll 1
-    for (int r = 0; r < d; ++r) {
-      const float den = right[r + 1] + left[d - r];
-      const float tmp = den != 0.0f ? N[r] / den : 0.0f;
-      N[r] = saved + right[r + 1] * tmp;
-      saved = left[d - r] * tmp;
-    }
-    N[d] = saved;
-    if (d == p - 1)
-#pragma unroll 1
-      for (int r = 0; r < p; ++r) M[r] = N[r];   // degree p - 1: N_{k+1+r,p-1}
-  }
-#pragma unroll 1
-  for (int a = 0; a <= p; ++a) {
-    float v = 0.0f;
-    if (a >= 1) {
-      const float den = knot_cu(i + a, p, ns) - knot_cu(i - p + a, p, ns);
-      if (den != 0.0f) v += M[a - 1] / den;
-    }
-    if (a <= p - 1) {
-      const float den = knot_cu(i + a + 1, p, ns) - knot_cu(i - p + a + 1, p, ns);
-      if (den != 0.0f) v -= M[a] / den;
-    }
-    dN[a] = (float)p * v;
-  }
-  *k_out = k;
-}
-
-// Z and its u- and v-derivatives from a net in `P` (row-major, ncv columns).
-__device__ __forceinline__ void surface_general(const float* P, int ncv, int k, int l, int p, int q,
-                                                const float (&Nu)[6], const float (&dNu)[6], const float (&Nv)[6],
-                                                const float (&dNv)[6], float* Z, float* Zu, float* Zv) {
-  float z = 0.0f, zu = 0.0f, zv = 0.0f;
-#pragma unroll 1
-  for (int a = 0; a <= p; ++a) {
-    float c = 0.0f, cv = 0.0f;
-#pragma unroll 1
-    for (int b = 0; b <= q; ++b) {
-      const float w = P[(k + a) * ncv + l + b];
-      c = fmaf(Nv[b], w, c);
-      cv = fmaf(dNv[b], w, cv);
-    }
-    z = fmaf(Nu[a], c, z);
-    zu = fmaf(dNu[a], c, zu);
-    zv = fmaf(Nu[a], cv, zv);
-  }
-  *Z = z;
-  *Zu = zu;
-  *Zv = zv;
-}
-
 // Derivative maps of a collimated lens of degrees (p, q), 1 <= p, q <= 5 (the
 // Sec. 3.1 figure shows (5, 3) beside (3, 3)), filter sizes 1 to 11: each lane
 // traces its run of cells with the basis functions of the ray's span computed

@@ -171,7 +171,7 @@ def test_invalid_arguments_return_error_codes():
                                   C.c_void_p(E.data_ptr()) if E_ptr else None, None, None)
 
     assert fwd() == api.FR_OK
-    bad = api.LensDesc.from_buffer_copy(pb.lens); bad.p = 2
+    bad = api.LensDesc.from_buffer_copy(pb.lens); bad.p = 6
     assert fwd(lens=bad) == api.FR_ERR_UNSUPPORTED
     bad = api.LensDesc.from_buffer_copy(pb.lens); bad.n1 = 40
     assert fwd(lens=bad) == api.FR_ERR_UNSUPPORTED

@@ -176,17 +176,3 @@ def test_other_degree_maps_match_oracle(p, q, nu):
         o -= O.trace_tangent(wl, dP, begin=int(rid), count=1)
     for k in range(3):
         assert rel_l2(g[k], o[k]) < TOL_GRAD, (k, rel_l2(g[k], o[k]))
-
-
-def test_other_degrees_refused_elsewhere():
-    wl = W.collimated("c", 64, 8, 16, 1, 2, with_target=False)
-    wl["lens"]["p"] = 5
-    pb = api.Problem(wl)
-    with pytest.raises(api.FreerayError):
-        pb.forward()
-    with pytest.raises(api.FreerayError):
-        pb.adjoint(torch.zeros(pb.ext_shape, device="cuda"))
-    wp = W.point("p", 4096, 8, 16, 3, 4, 5, with_target=False)
-    wp["lens"]["p"] = 5
-    with pytest.raises(api.FreerayError):
-        api.Problem(wp).tangent(_unit(wp, 3, 3))
